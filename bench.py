@@ -1,0 +1,360 @@
+"""Benchmark: ERQLP factorizations/s on one GB300 (and sketch TFLOP/s).
+
+Workload (the 8192 x 8192 ERQLP case): A = X diag(10^(-j/100)) Y^T with
+X, Y orthonormal from the QR of seeded N(0,1) matrices, m = n = 8192,
+k = 100, p = 10 (l = 110), q = 1 power step, d = 2 inner QRs (Algorithm 2.2
+plus one power step), Omega seeded N(0,1).  A step is one whole
+factorization A ~= Q L P^T through the C ABI with A resident in HBM (A is
+537 MB in FP64, larger than the 129 MB L2, so no flush is needed between
+steps).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--prec fp64|bf16x3|bf16]
+Prints ONE JSON line (rank 0).  With N > 1 (torchrun), each rank factors
+its own matrix (independent problems, no collective on the data path), and
+the value is the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M = N_ = 8192
+K_RANK, P_OVER, Q_POW, D_INNER = 100, 10, 1, 2
+WORKLOAD = "erqlp_8192x8192_k100_p10_q1_d2_expdecay"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA-core and DMMA) nominal rate
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _sketch_flops(m, n, l, q):
+    """Algorithmic flops of the products with A: 2q + 2 passes of 2 m n l."""
+    return (2 * q + 2) * 2.0 * m * n * l
+
+
+def _oracle_run(A_np, Om_np, prec_forms_out, budget_s=25.0):
+    """Times the FP64 CPU oracle on the same factorization (bounded sample)."""
+    from oracle import rqlp_ref as O
+    times = []
+    ref = None
+    t_start = time.time()
+    while True:
+        t0 = time.time()
+        ref = O.rqlp(A_np, K_RANK, P_OVER, Om_np, q=Q_POW, d=D_INNER, pivot2=False)
+        times.append(time.time() - t0)
+        if time.time() - t_start + times[-1] > budget_s or len(times) >= 3:
+            break
+    return ref, times
+
+
+def _lvalue_err(gpu_out, ref):
+    import numpy as np
+    lg = gpu_out["Lvalues"].double().cpu().numpy()
+    lr = ref["Lvalues"]
+    rel = np.abs(lg - lr) / np.abs(lr)
+    keep = np.abs(lr) >= 1e-3 * np.abs(lr).max()
+    piv_ok = bool((gpu_out["piv0"].cpu().numpy()[:len(lr)] == ref["piv0"][:len(lr)]).all())
+    return {"max_rel": float(rel[keep].max()), "median_rel": float(np.median(rel[keep])),
+            "pivots_match": piv_ok}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import rqlp_ref as O
+    from paper_1811_09334_gb300 import workloads as W
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else None
+    except ImportError:
+        dev = None
+    pr = W.c2(device=dev)
+    A = pr.A.cpu().numpy() if dev else pr.A
+    Om = W.omega(pr.n, pr.l, 0)
+    for _ in range(args.warmup):
+        O.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False)
+    t0 = time.time()
+    for _ in range(args.steps):
+        O.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False)
+    dt = time.time() - t0
+    value = args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": "erqlp_factorizations_per_s", "value": value,
+            "unit": "factorizations/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N_, "k": K_RANK, "p": P_OVER,
+                       "q": Q_POW, "d": D_INNER, "prec": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%d whole factorizations of the workload" % args.steps},
+            "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_1811_09334_gb300 import rqlp as R
+    from paper_1811_09334_gb300 import workloads as W
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    __graft_entry__.build() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    R.lib()
+    dev = torch.device("cuda", local)
+    pr = W.c2(device=str(dev))
+    A = pr.A
+    Om_np = W.omega(pr.n, pr.l, 0)
+    Om = torch.from_numpy(Om_np).to(dev)
+    forms = [args.prec] + (["fp64"] if args.prec != "fp64" else [])
+    stream = torch.cuda.current_stream()
+    results = {}
+    outs = {}
+    for form in forms:
+        out = R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form)
+        ws = out["ws"]
+        buf = {k: out[k] for k in ("Q", "L", "P", "Lvalues", "piv0", "piv1")}
+        steps = args.steps if form == args.prec else max(3, min(args.steps, 5))
+        for _ in range(args.warmup):
+            R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form, ws=ws, out=buf,
+                   check=False)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        if form == args.prec:
+            clocks.start()
+        n0 = R.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form, ws=ws, out=buf,
+                   check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = R.launch_count() - n0
+        clk = clocks.stop() if form == args.prec else None
+        ms = e0.elapsed_time(e1)
+        status = R.read_status(ws)
+        if status < 0:
+            raise SystemExit("device status %d during the timed region" % status)
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        # per-kernel-class timing over the same number of steps (events on the launch stream)
+        R.profile_begin()
+        for _ in range(steps):
+            R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form, ws=ws, out=buf,
+                   check=False)
+        prof = R.profile_end()
+        results[form] = dict(ms_total=ms_max, steps=steps, launches=launches, clocks=clk,
+                             prof=prof, status=status)
+        outs[form] = {k: v.clone() for k, v in buf.items()}
+
+    main = results[args.prec]
+    value = world * main["steps"] / (main["ms_total"] / 1e3)
+    flops = _sketch_flops(pr.m, pr.n, pr.l, Q_POW)
+    forms_out = {}
+    for form, r in results.items():
+        prod_ms, prod_cnt = r["prof"]["products_with_A"]
+        forms_out[form] = {
+            "factorizations_per_s": r["steps"] / (r["ms_total"] / 1e3),
+            "ms_per_step": r["ms_total"] / r["steps"],
+            "sketch_tflops": flops * r["steps"] / (prod_ms / 1e3) / 1e12 if prod_ms > 0 else None,
+            "stage_ms_per_step": {k: v[0] / r["steps"] for k, v in r["prof"].items()},
+            "status": r["status"],
+        }
+
+    # dominant kernel class of the headline form and its roofline
+    peaks, peak_src = _peaks()
+    prof = main["prof"]
+    dom = max(prof, key=lambda c: prof[c][0])
+    dom_ms, dom_cnt = prof[dom]
+    roof = None
+    if dom == "products_with_A":
+        per_launch_flops = flops / (2 * Q_POW + 2)
+        achieved = per_launch_flops * dom_cnt / (dom_ms / 1e3) / 1e12
+        if args.prec == "fp64":
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                    "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
+        else:
+            bytes_per = 4.0 * pr.m * pr.n if args.prec == "bf16x3" else 2.0 * pr.m * pr.n
+            gbs = bytes_per * dom_cnt / (dom_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_src}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "peak_source": "nominal FP64"}
+    roof["kernel_class"] = dom
+    roof["traffic"] = None
+    roof["time_share"] = dom_ms / sum(v[0] for v in prof.values()) if prof else None
+
+    # end to end through the host-pointer entry point (pinned buffers)
+    e2e = None
+    if rank == 0 or world > 1:
+        A_h = A.cpu().pin_memory()
+        Om_h = torch.from_numpy(Om_np).pin_memory()
+        ho = R.rqlp_host(A_h, pr.k, pr.p, Om_h, q=Q_POW, d=D_INNER, pivot2=False, prec=args.prec)
+        hsteps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(hsteps):
+            ho = R.rqlp_host(A_h, pr.k, pr.p, Om_h, q=Q_POW, d=D_INNER, pivot2=False,
+                             prec=args.prec, ws=ho["ws"], out={k: ho[k] for k in
+                                                              ("Q", "L", "P", "Lvalues", "piv0", "piv1")})
+        dt = time.perf_counter() - t0
+        l = pr.l
+        h2d = A_h.numel() * A_h.element_size() + Om_h.numel() * 8
+        d2h = (pr.m * l + l * l + pr.n * l + l) * 8 + (pr.n + l) * 4
+        e2e = {"value": world * hsteps / dt, "unit": "factorizations/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # CPU baseline (oracle) on rank 0 at N = 1; L-value error of each form against it
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_np = A.cpu().numpy()
+        ref, times = _oracle_run(A_np, Om_np, forms_out)
+        cpu = {"value": 1.0 / statistics.mean(times), "unit": "factorizations/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d whole factorization(s) of the workload (numpy FP64, all host cores)"
+                         % len(times)}
+        for form in forms_out:
+            forms_out[form]["lvalue_err_vs_oracle"] = _lvalue_err(outs[form], ref)
+
+    if rank == 0:
+        line = {
+            "metric": "erqlp_factorizations_per_s", "value": value, "unit": "factorizations/s",
+            "n_gpus": world, "steps": main["steps"], "warmup": args.warmup,
+            "ms_per_step": main["ms_total"] / main["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else args.prec + "+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": pr.m, "n": pr.n, "k": pr.k, "p": pr.p,
+                       "q": Q_POW, "d": D_INNER, "prec": args.prec, "l2": "inputs larger than L2"},
+            "sketch_tflops": forms_out[args.prec]["sketch_tflops"],
+            "forms": forms_out,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(main["launches"]),
+            "clocks": main["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

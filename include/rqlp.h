@@ -1,0 +1,184 @@
+/*
+ * rqlp.h - C ABI of the GB300 (sm_103a) randomized QLP library.
+ *
+ * The library computes the randomized QLP factorization A ~= Q L P^T of
+ * Wu & Xiang, "Randomized QLP algorithm and error analysis" (arXiv
+ * 1811.09334): RQLP (Algorithm 2.1), the enhanced ERQLP with d inner QR
+ * iterations (Algorithm 2.2) and the blocked BRQLP (Algorithm 4.1), plus
+ * q power steps Y = (A A^T)^q A Omega in the range finder.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are dense, row-major, with an explicit leading dimension
+ *   (ld >= number of columns), FP64 unless stated.
+ * - l = k + p is the sketch width; 1 <= l <= min(m, n) and l <= 256.
+ * - All pointers are DEVICE pointers except in rqlp_host().  The caller
+ *   owns every buffer, including the workspace; the library never
+ *   allocates device memory.  Buffers must not overlap unless stated.
+ * - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *   the legacy default stream).  Argument errors are returned at once and
+ *   enqueue nothing.  Errors found on the device (non-finite data, a
+ *   device-side wait that ran out of time) are written to a status word in
+ *   the workspace; read it with rqlp_read_status() after the work is done.
+ * - Every QR inside returns R with a non-negative diagonal, so Q, L and P
+ *   are unique for full-rank inputs.  Column pivoting compares exact
+ *   trailing column norms; exact ties go to the lowest original column
+ *   index; columns never chosen as pivots keep their original order.
+ * - Workspaces may be reused between calls on the same stream; two calls
+ *   that run concurrently need two workspaces.
+ */
+#ifndef RQLP_H
+#define RQLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rqlp_stream_t; /* a cudaStream_t */
+
+/* Status codes.  Negative: error (outputs are invalid).  Positive: warning
+ * (outputs are valid). */
+typedef enum {
+  RQLP_OK = 0,
+  RQLP_WARN_SHIFTED_CHOLQR = 1,  /* a Gram matrix was numerically singular; a shifted CholeskyQR pass was added */
+  RQLP_ERR_INVALID_ARG = -1,     /* bad size, pointer, leading dimension or option */
+  RQLP_ERR_NONFINITE = -2,       /* NaN or Inf met in A, Omega or an intermediate */
+  RQLP_ERR_RANK_DEFICIENT = -3,  /* a Gram matrix stayed singular after the shift */
+  RQLP_ERR_TIMEOUT = -4,         /* a device-side wait gave up (see spin_limit_ns) */
+  RQLP_ERR_CUDA = -5,            /* a CUDA runtime call failed */
+  RQLP_ERR_WORKSPACE = -6,       /* workspace too small or misaligned (needs 256-byte alignment) */
+  RQLP_ERR_UNSUPPORTED = -7      /* option not available in this build */
+} rqlp_status;
+
+/* Precision of the products with A (sketch, power steps, projection).
+ * The QR factorizations and the QLP of B always run in FP64. */
+typedef enum {
+  RQLP_PREC_FP64 = 0,   /* FP64 CUDA-core products (A in FP64 or FP32) */
+  RQLP_PREC_BF16X3 = 1, /* tcgen05 BF16 tensor cores, split A = Ah + Al and W = Wh + Wl,
+                           three products Ah Wh + Ah Wl + Al Wh accumulated in FP32 */
+  RQLP_PREC_BF16 = 2    /* tcgen05 BF16 tensor cores, one product, FP32 accumulation */
+} rqlp_prec;
+
+/* Element type of A. */
+typedef enum { RQLP_F64 = 0, RQLP_F32 = 1 } rqlp_dtype;
+
+typedef struct {
+  int32_t q;            /* power steps, q >= 0 (Y = (A A^T)^q A Omega, QR after every product) */
+  int32_t d;            /* inner QR iterations of Algorithm 2.2, d >= 1 (used when pivot2 == 0) */
+  int32_t pivot2;       /* 1: Algorithm 2.1, second QR column-pivoted; 0: Algorithm 2.2 */
+  int32_t prec;         /* rqlp_prec */
+  int32_t block_b;      /* 0: unblocked; b > 0: Algorithm 4.1 with blocks of b columns (b divides l) */
+  int32_t debug_flags;  /* 0 in normal use; bit 0: the first device-side grid barrier waits for one
+                           arrival too many, so that it runs out of time (tests of the timeout path) */
+  int64_t spin_limit_ns;/* bound on every device-side wait in ns; 0 selects 2 s */
+} rqlp_opts;
+
+/* Human-readable name of a status code. */
+const char *rqlp_status_string(int status);
+
+/* Library ABI version (major * 100 + minor). */
+int rqlp_version(void);
+
+/* Bytes of device workspace rqlp() needs for these sizes and options
+ * (0 if the arguments are invalid). */
+size_t rqlp_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts);
+
+/*
+ * Randomized QLP of A (Algorithms 2.1, 2.2 and 4.1; the problem statement of
+ * Section 1, eq. 1.1).
+ *
+ *  A       [in]  m x n, element type a_dtype, leading dimension lda.
+ *  Omega   [in]  n x l Gaussian sketch (FP64, ld ldo); the caller draws it so
+ *                that other implementations can be fed the same sketch.
+ *  Q       [out] m x l, column-orthonormal (ld l).
+ *  L       [out] l x l middle factor (ld l): lower triangular, except for
+ *                ERQLP with even d, where the exact middle factor of
+ *                B = Q_B R(d) P_B^T is upper triangular.  BRQLP: blkdiag(L_j).
+ *  P       [out] n x l (ld l); column-orthonormal (within each block for BRQLP).
+ *  Lvalues [out] l values diag(L) (>= 0); may be NULL.
+ *  piv0    [out] n int32 column pivots of the CPQR of B (position i holds the
+ *                original column index); may be NULL.  BRQLP: first block.
+ *  piv1    [out] l int32 pivots of the second CPQR (identity for ERQLP); may be NULL.
+ *  ws      [in]  device workspace of ws_bytes >= rqlp_workspace_size(), 256-byte aligned.
+ * Returns RQLP_OK once the work is enqueued, or an argument error.
+ */
+int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t p,
+         const double *Omega, int64_t ldo, const rqlp_opts *opts, double *Q, double *L, double *P,
+         double *Lvalues, int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
+         rqlp_stream_t stream);
+
+/* Synchronizes `stream` and returns the device status word of the last call
+ * that used `ws` (RQLP_OK, a warning or an error). */
+int rqlp_read_status(const void *ws, rqlp_stream_t stream);
+
+/* Bytes of device workspace rqlp_host() needs (inputs and outputs are staged in it). */
+size_t rqlp_host_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts,
+                                int32_t a_dtype);
+
+/*
+ * rqlp() on HOST buffers: copies A (m x n, dense, lda = n) and Omega (n x l)
+ * to the device workspace, factors, copies Q, L, P, Lvalues, piv0, piv1 back
+ * and synchronizes the stream.  Host buffers should be page-locked for full
+ * copy speed.  Returns the final status (argument, CUDA or device status).
+ */
+int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k, int32_t p,
+              const double *Omega_host, const rqlp_opts *opts, double *Q_host, double *L_host,
+              double *P_host, double *Lvalues_host, int32_t *piv0_host, int32_t *piv1_host,
+              void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points (each one a step of Algorithm 2.1 / 2.2).  They use the
+ * same workspace rules; rqlp_stage_workspace_size() covers all of them.
+ * ---------------------------------------------------------------------- */
+size_t rqlp_stage_workspace_size(int64_t rows, int64_t cols, int32_t l, int32_t prec);
+
+/* Y = A W (Algorithm 2.1, step 2 with W = Omega; also the second half of a
+ * power step).  A m x n (a_dtype, lda), W n x l (ldw), Y m x l (ldy). */
+int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, const double *W,
+                int64_t ldw, int32_t l, int32_t prec, double *Y, int64_t ldy, void *ws,
+                size_t ws_bytes, rqlp_stream_t stream);
+
+/* Z = A^T V (n x l, ldz), i.e. B^T for B = V^T A (Algorithm 2.1, step 4;
+ * also the first half of a power step).  A m x n, V m x l (ldv). */
+int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, const double *V,
+                 int64_t ldv, int32_t l, int32_t prec, double *Z, int64_t ldz, void *ws,
+                 size_t ws_bytes, rqlp_stream_t stream);
+
+/* Thin QR X = Qx R of a rows x l matrix (Algorithm 2.1, step 3) by
+ * CholeskyQR2 in FP64, with a shifted first pass and a third pass when a
+ * Gram matrix is numerically singular.  X is read (ldx); Qx (rows x l, ldq)
+ * and, if R != NULL, R (l x l upper, ld l, non-negative diagonal) are written. */
+int rqlp_orth(const double *X, int64_t rows, int32_t l, int64_t ldx, double *Qx, int64_t ldq,
+              double *R, void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
+/* Column-pivoted Householder QR of the l x n matrix B (Algorithm 2.1, step 5),
+ * B given as Bt = B^T (n x l row-major, ld ldb; each row one column of B).
+ * Writes R0t = R0^T (n x l, ld l; row i is column i of R0 in pivot order),
+ * piv0 (n) and Q0 (l x l, ld l) with B[:, piv0] = Q0 R0. */
+int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, int32_t *piv0,
+              double *Q0, void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation.
+ * ---------------------------------------------------------------------- */
+/* Number of CUDA kernels this library has launched in this process. */
+long long rqlp_launch_count(void);
+
+/* Starts timing kernel classes: from now on rqlp() records a CUDA event pair
+ * on its stream around (0) every product with A, (1) every column-pivoted QR
+ * of B, (2) every CholeskyQR and (3) the explicit Q0 of the first CPQR. */
+int rqlp_profile_begin(void);
+
+/* Stops timing; waits for the recorded events and writes, per class c <
+ * nclass, the summed device time in ms (ms[c]) and the number of timed
+ * regions (count[c]).  Either array may be NULL. */
+int rqlp_profile_end(double *ms, long long *count, int nclass);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQLP_H */

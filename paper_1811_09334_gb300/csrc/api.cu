@@ -1,0 +1,480 @@
+// C ABI driver: enqueues the stages of RQLP / ERQLP / BRQLP on one stream.
+//
+// Algorithm 2.1 / 2.2 (Section 2) as launched here:
+//   range finder   Y = A Omega; q times { V = qr(Y); Z = A^T V; W = qr(Z); Y = A W }; V = qr(Y)
+//   projection     B^T = A^T V                     (n x l; column-major B)
+//   first CPQR     B Pi0 = Q0 R0                    (cooperative kernel)
+//   second stage   X = R0^T:  RQLP  X = Qa Ra, Ra Pi1 = Qc R1   => L = R1^T, P = Pi0 Qa Qc
+//                             ERQLP X = Q(1) R(1), R(i-1)^T = Q(i) R(i), i = 2..d
+//   assembly       Q = V Q_B,  P = Pi0 (Q(1) Q(3) ...),  L-values = diag(L)
+// Every thin QR is CholeskyQR2 in FP64; with column pivoting compared on
+// exact norms the CPQR of the tall X equals the CPQR of its R factor Ra,
+// which is why the second CPQR runs on the l x l matrix Ra.
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+#include "mixed.cuh"
+
+using namespace rqk;
+
+namespace {
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return RQLP_ERR_CUDA;  \
+  } while (0)
+
+// Scratch for CholeskyQR2 on rows x l data.
+struct OrthBufs {
+  double *part;  // split-K partials
+  double *G, *Rp, *Rinv, *Racc, *Rtmp;
+  double *tmp;   // rows x l ping-pong
+};
+
+size_t part_doubles(int64_t m, int64_t n, int l) {
+  const int64_t big = std::max(m, n);
+  size_t b = 0;
+  auto upd = [&](int64_t M, int64_t N, int64_t K) {
+    b = std::max(b, gemm_f64_part_bytes(M, N, K) / sizeof(double));
+  };
+  upd(m, l, n);
+  upd(n, l, m);
+  upd(l, l, m);
+  upd(l, l, n);
+  upd(l, l, l);
+  upd(big, l, l);
+  b = std::max(b, (size_t)4 * big * l);  // products with K = l (<= 4 splits) and the scatter
+  return b;
+}
+
+void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBufs &o,
+                double *shared_part) {
+  o.part = shared_part ? shared_part : a.take<double>(part_doubles(m, n, l));
+  o.G = a.take<double>((size_t)l * l);
+  o.Rp = a.take<double>((size_t)l * l);
+  o.Rinv = a.take<double>((size_t)l * l);
+  o.Racc = a.take<double>((size_t)l * l);
+  o.Rtmp = a.take<double>((size_t)l * l);
+  o.tmp = a.take<double>((size_t)rows_max * l);
+}
+
+// CholeskyQR2 (+ a third pass iff a pass needed the shift): Xq = X R^{-1}.
+int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
+         const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
+  site %= kShiftSites;
+  const int *flag = &ctrl->shift_flag[site];
+  // pass 1: X -> tmp
+  CK(gemm_f64(true, RQLP_F64, X, ldx, X, ldx, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
+              nullptr, st));
+  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, nullptr, st));
+  CK(trinv_upper(o.Rp, l, o.Rinv, nullptr, st));
+  CK(gemm_f64(false, RQLP_F64, X, ldx, o.Rinv, l, o.tmp, l, rows, l, l, 1.0, 0.0, o.part, nullptr,
+              nullptr, st));
+  if (R) CK(copy2d(o.Rp, l, l, l, o.Racc, l, nullptr, st));
+  // pass 2: tmp -> Xq
+  CK(gemm_f64(true, RQLP_F64, o.tmp, l, o.tmp, l, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
+              nullptr, st));
+  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, nullptr, st));
+  CK(trinv_upper(o.Rp, l, o.Rinv, nullptr, st));
+  CK(gemm_f64(false, RQLP_F64, o.tmp, l, o.Rinv, l, Xq, ldq, rows, l, l, 1.0, 0.0, o.part, nullptr,
+              nullptr, st));
+  if (R) {
+    CK(gemm_f64(false, RQLP_F64, o.Rp, l, o.Racc, l, o.Rtmp, l, l, l, l, 1.0, 0.0, o.part, nullptr,
+                nullptr, st));
+    CK(copy2d(o.Rtmp, l, l, l, o.Racc, l, nullptr, st));
+  }
+  // pass 3, only when the device raised the shift flag: Xq -> tmp -> Xq
+  CK(gemm_f64(true, RQLP_F64, Xq, ldq, Xq, ldq, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr, flag,
+              st));
+  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, flag, st));
+  CK(trinv_upper(o.Rp, l, o.Rinv, flag, st));
+  CK(gemm_f64(false, RQLP_F64, Xq, ldq, o.Rinv, l, o.tmp, l, rows, l, l, 1.0, 0.0, o.part, nullptr,
+              flag, st));
+  CK(copy2d(o.tmp, rows, l, l, Xq, ldq, flag, st));
+  if (R) {
+    CK(gemm_f64(false, RQLP_F64, o.Rp, l, o.Racc, l, o.Rtmp, l, l, l, l, 1.0, 0.0, o.part, nullptr,
+                flag, st));
+    CK(copy2d(o.Rtmp, l, l, l, o.Racc, l, flag, st));
+    CK(copy2d(o.Racc, l, l, l, R, l, nullptr, st));
+  }
+  return RQLP_OK;
+}
+
+int orth(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
+         const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
+  const int ev = prof_start(kProfOrth, st);
+  const int r = orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, st);
+  prof_stop(kProfOrth, ev, st);
+  return r;
+}
+
+// Everything rqlp() carves from its workspace.
+struct Plan {
+  Ctrl *ctrl;
+  OrthBufs ob;
+  double *Y, *V, *Z, *W, *X, *R0t;
+  double *Q0, *QB, *Macc, *Racc, *Rt, *Tl, *Vh, *tau, *Qi, *Rprev, *Xs, *sm1;
+  int32_t *piv0, *piv1;
+  void *cpqr_scratch;
+  MixedBufs mx;
+  size_t bytes;
+};
+
+Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
+  Plan p;
+  Arena a(ws);
+  p.ctrl = a.take<Ctrl>(1);
+  const int64_t big = std::max(m, n);
+  carve_orth(a, big, l, m, n, p.ob, nullptr);
+  p.Y = a.take<double>((size_t)m * l);
+  p.V = a.take<double>((size_t)m * l);
+  p.Z = a.take<double>((size_t)n * l);
+  p.W = a.take<double>((size_t)n * l);
+  p.X = a.take<double>((size_t)n * l);
+  p.R0t = a.take<double>((size_t)n * l);
+  const size_t ll = (size_t)l * l;
+  p.Q0 = a.take<double>(ll);
+  p.QB = a.take<double>(ll);
+  p.Macc = a.take<double>(ll);
+  p.Racc = a.take<double>(ll);
+  p.Rt = a.take<double>(ll);
+  p.Tl = a.take<double>(ll);
+  p.Vh = a.take<double>(ll);
+  p.tau = a.take<double>((size_t)l);
+  p.Qi = a.take<double>(ll);
+  p.Rprev = a.take<double>(ll);
+  p.Xs = a.take<double>(ll);
+  p.sm1 = a.take<double>(ll);
+  p.piv0 = a.take<int32_t>((size_t)n);
+  p.piv1 = a.take<int32_t>((size_t)l);
+  p.cpqr_scratch = a.take<char>(cpqr_ws_bytes(std::max<int64_t>(n, l), l));
+  carve_mixed(a, m, n, l, o.prec, p.mx);
+  p.bytes = a.off;
+  return p;
+}
+
+bool valid_opts(const rqlp_opts *o) {
+  if (!o) return false;
+  if (o->q < 0 || o->q > 16) return false;
+  if (o->pivot2 != 0 && o->pivot2 != 1) return false;
+  if (!o->pivot2 && (o->d < 1 || o->d > 64)) return false;
+  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_BF16) return false;
+  if (o->block_b < 0) return false;
+  if (o->spin_limit_ns < 0) return false;
+  return true;
+}
+
+bool valid_dims(int64_t m, int64_t n, int32_t k, int32_t p) {
+  if (m <= 0 || n <= 0 || k < 1 || p < 0) return false;
+  const int64_t l = (int64_t)k + p;
+  if (l > kMaxL || l > m || l > n) return false;
+  if (m > (1LL << 31) || n > (1LL << 31)) return false;
+  return true;
+}
+
+// Products with A in the requested precision.
+int prod_nn(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64_t m, int64_t n,
+            int64_t lda, const double *W, int64_t ldw, int l, double *Y, cudaStream_t st) {
+  const int ev = prof_start(kProfProducts, st);
+  int r;
+  if (o.prec == RQLP_PREC_FP64)
+    r = gemm_f64(false, a_dtype, A, lda, W, ldw, Y, l, m, l, n, 1.0, 0.0, P.ob.part, nullptr,
+                 nullptr, st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+  else
+    r = mixed_nn(P.mx, o.prec, m, n, W, ldw, l, Y, P.ctrl, o.spin_limit_ns, st);
+  prof_stop(kProfProducts, ev, st);
+  return r;
+}
+
+int prod_tn(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64_t m, int64_t n,
+            int64_t lda, const double *V, int64_t ldv, int l, double *Z, cudaStream_t st) {
+  const int ev = prof_start(kProfProducts, st);
+  int r;
+  if (o.prec == RQLP_PREC_FP64)
+    r = gemm_f64(true, a_dtype, A, lda, V, ldv, Z, l, n, l, m, 1.0, 0.0, P.ob.part, nullptr,
+                 nullptr, st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+  else
+    r = mixed_tn(P.mx, o.prec, m, n, V, ldv, l, Z, P.ctrl, o.spin_limit_ns, st);
+  prof_stop(kProfProducts, ev, st);
+  return r;
+}
+
+#define RET(x)                    \
+  do {                            \
+    int r_ = (x);                 \
+    if (r_ != RQLP_OK) return r_; \
+  } while (0)
+
+// The pivoted QLP of the small l x n matrix B, given as Bt = B^T (n x l),
+// followed by the assembly of Q and P (Algorithm 2.1 steps 5-7, Algorithm
+// 2.2 steps 5-9).  V is the m x l range basis.
+int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int l, const double *Vb,
+              const double *Bt, double *Q, double *L, double *Pout, double *Lvalues,
+              int32_t *piv0, int32_t *piv1, int site0, cudaStream_t st) {
+  Ctrl *ctrl = P.ctrl;
+  const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
+  const unsigned extra = (o.debug_flags & 1) ? 1u : 0u;
+  int ev = prof_start(kProfCpqr, st);
+  CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st));
+  prof_stop(kProfCpqr, ev, st);
+  ev = prof_start(kProfSmall, st);
+  CK(form_q(P.Vh, l, P.tau, l, l, P.Q0, l, st));
+  prof_stop(kProfSmall, ev, st);
+  if (o.pivot2) {
+    RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st));
+    CK(transpose(P.Racc, l, l, l, P.Rt, l, st));
+    CK(cpqr_wide(P.Rt, l, l, l, L, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
+    CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st));
+    CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
+    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, l, n, l, l, 1.0, 0.0, P.ob.part, piv0,
+                nullptr, st));
+  } else {
+    RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st));
+    CK(set_identity(P.QB, l, l, l, st));
+    CK(set_identity(P.Macc, l, l, l, st));
+    for (int i = 2; i <= o.d; ++i) {
+      CK(transpose(P.Rprev, l, l, l, P.Xs, l, st));
+      RET(orth(P.Xs, l, l, l, P.Qi, l, P.Rprev, P.ob, ctrl, site0 + i - 1, st));
+      double *acc = (i % 2 == 0) ? P.QB : P.Macc;
+      CK(gemm_f64(false, RQLP_F64, acc, l, P.Qi, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
+                  nullptr, st));
+      CK(copy2d(P.sm1, l, l, l, acc, l, nullptr, st));
+    }
+    CK(gemm_f64(false, RQLP_F64, P.Q0, l, P.QB, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
+                nullptr, st));
+    CK(copy2d(P.sm1, l, l, l, P.QB, l, nullptr, st));
+    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, l, n, l, l, 1.0, 0.0, P.ob.part, piv0,
+                nullptr, st));
+    if (o.d % 2 == 1) CK(transpose(P.Rprev, l, l, l, L, l, st));
+    else CK(copy2d(P.Rprev, l, l, l, L, l, nullptr, st));
+  }
+  CK(gemm_f64(false, RQLP_F64, Vb, l, P.QB, l, Q, l, m, l, l, 1.0, 0.0, P.ob.part, nullptr, nullptr,
+              st));
+  if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
+  return RQLP_OK;
+}
+
+int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+             int32_t p, const double *Omega, int64_t ldo, const rqlp_opts &o, double *Q, double *L,
+             double *Pout, double *Lvalues, int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
+             cudaStream_t st) {
+  const int l = k + p;
+  Plan P = carve(ws, m, n, l, o);
+  if (P.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
+  CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
+  int32_t *pv0 = piv0 ? piv0 : P.piv0;
+  int32_t *pv1 = piv1 ? piv1 : P.piv1;
+  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
+  int site = 0;
+  if (o.block_b > 0) return RQLP_ERR_UNSUPPORTED;
+  // range finder (Section 2) with q power steps
+  RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega, ldo, l, P.Y, st));
+  for (int i = 0; i < o.q; ++i) {
+    RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st));
+    RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
+    RET(orth(P.Z, n, l, l, P.W, l, nullptr, P.ob, P.ctrl, site++, st));
+    RET(prod_nn(P, o, A, a_dtype, m, n, lda, P.W, l, l, P.Y, st));
+  }
+  RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st));
+  // B^T = A^T V  (Algorithm 2.1 step 4)
+  RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
+  RET(qlp_stage(P, o, m, n, l, P.V, P.Z, Q, L, Pout, Lvalues, pv0, pv1, site, st));
+  if (!o.pivot2) CK(iota(pv1, l, st));
+  return RQLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rqlp_status_string(int s) {
+  switch (s) {
+    case RQLP_OK: return "ok";
+    case RQLP_WARN_SHIFTED_CHOLQR: return "warning: shifted CholeskyQR pass used";
+    case RQLP_ERR_INVALID_ARG: return "invalid argument";
+    case RQLP_ERR_NONFINITE: return "non-finite value in the data";
+    case RQLP_ERR_RANK_DEFICIENT: return "Gram matrix singular after the shift";
+    case RQLP_ERR_TIMEOUT: return "device-side wait timed out";
+    case RQLP_ERR_CUDA: return "CUDA runtime error";
+    case RQLP_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case RQLP_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+int rqlp_version(void) { return 100; }
+
+size_t rqlp_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts) {
+  if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return 0;
+  Plan P = carve(nullptr, m, n, k + p, *opts);
+  return P.bytes + 256;
+}
+
+int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t p,
+         const double *Omega, int64_t ldo, const rqlp_opts *opts, double *Q, double *L, double *P,
+         double *Lvalues, int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
+         rqlp_stream_t stream) {
+  if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
+  if (!A || !Omega || !Q || !L || !P || !ws) return RQLP_ERR_INVALID_ARG;
+  if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
+  const int l = k + p;
+  if (lda < n || ldo < l) return RQLP_ERR_INVALID_ARG;
+  if (opts->block_b > 0 && (l % opts->block_b != 0)) return RQLP_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  return run_rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, *opts, Q, L, P, Lvalues, piv0, piv1, ws,
+                  ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rqlp_read_status(const void *ws, rqlp_stream_t stream) {
+  if (!ws) return RQLP_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RQLP_ERR_CUDA;
+  int s = 0;
+  if (cudaMemcpy(&s, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RQLP_ERR_CUDA;
+  return s;
+}
+
+size_t rqlp_host_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts,
+                                int32_t a_dtype) {
+  const size_t base = rqlp_workspace_size(m, n, k, p, opts);
+  if (!base) return 0;
+  const int64_t l = k + p;
+  const size_t esz = a_dtype == RQLP_F32 ? 4 : 8;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up(base) + up((size_t)m * n * esz) + up((size_t)n * l * 8) + up((size_t)m * l * 8) +
+         up((size_t)l * l * 8) + up((size_t)n * l * 8) + up((size_t)l * 8) + up((size_t)n * 4) +
+         up((size_t)l * 4);
+}
+
+int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k, int32_t p,
+              const double *Omega_host, const rqlp_opts *opts, double *Q_host, double *L_host,
+              double *P_host, double *Lvalues_host, int32_t *piv0_host, int32_t *piv1_host,
+              void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
+  if (!A_host || !Omega_host || !Q_host || !L_host || !P_host || !ws) return RQLP_ERR_INVALID_ARG;
+  if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
+  const size_t need = rqlp_host_workspace_size(m, n, k, p, opts, a_dtype);
+  if (ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  const int64_t l = k + p;
+  const size_t esz = a_dtype == RQLP_F32 ? 4 : 8;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  char *c = reinterpret_cast<char *>(ws);
+  const size_t base = up(rqlp_workspace_size(m, n, k, p, opts));
+  char *dA = c + base;
+  double *dO = reinterpret_cast<double *>(dA + up((size_t)m * n * esz));
+  double *dQ = reinterpret_cast<double *>(reinterpret_cast<char *>(dO) + up((size_t)n * l * 8));
+  double *dL = reinterpret_cast<double *>(reinterpret_cast<char *>(dQ) + up((size_t)m * l * 8));
+  double *dP = reinterpret_cast<double *>(reinterpret_cast<char *>(dL) + up((size_t)l * l * 8));
+  double *dLv = reinterpret_cast<double *>(reinterpret_cast<char *>(dP) + up((size_t)n * l * 8));
+  int32_t *dp0 = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(dLv) + up((size_t)l * 8));
+  int32_t *dp1 = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(dp0) + up((size_t)n * 4));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(dA, A_host, (size_t)m * n * esz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dO, Omega_host, (size_t)n * l * 8, cudaMemcpyHostToDevice, st));
+  int r = rqlp(dA, a_dtype, m, n, n, k, p, dO, l, opts, dQ, dL, dP, dLv, dp0, dp1, c, base,
+               stream);
+  if (r != RQLP_OK) return r;
+  CK(cudaMemcpyAsync(Q_host, dQ, (size_t)m * l * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(L_host, dL, (size_t)l * l * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(P_host, dP, (size_t)n * l * 8, cudaMemcpyDeviceToHost, st));
+  if (Lvalues_host) CK(cudaMemcpyAsync(Lvalues_host, dLv, (size_t)l * 8, cudaMemcpyDeviceToHost, st));
+  if (piv0_host) CK(cudaMemcpyAsync(piv0_host, dp0, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+  if (piv1_host) CK(cudaMemcpyAsync(piv1_host, dp1, (size_t)l * 4, cudaMemcpyDeviceToHost, st));
+  return rqlp_read_status(c, stream);
+}
+
+// ---------------------------------------------------------------- stages
+size_t rqlp_stage_workspace_size(int64_t rows, int64_t cols, int32_t l, int32_t prec) {
+  if (rows <= 0 || cols <= 0 || l < 1 || l > kMaxL) return 0;
+  rqlp_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.prec = prec;
+  o.pivot2 = 1;
+  const int64_t m = rows, n = std::max<int64_t>(cols, l);
+  Plan P = carve(nullptr, std::max<int64_t>(m, l), n, l, o);
+  return P.bytes + 256;
+}
+
+int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, const double *W,
+                int64_t ldw, int32_t l, int32_t prec, double *Y, int64_t ldy, void *ws,
+                size_t ws_bytes, rqlp_stream_t stream) {
+  if (!A || !W || !Y || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldw < l ||
+      ldy < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
+    return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_BF16) return RQLP_ERR_INVALID_ARG;
+  rqlp_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.prec = prec;
+  Plan P = carve(ws, std::max<int64_t>(m, l), std::max<int64_t>(n, l), l, o);
+  if (P.bytes > ws_bytes || reinterpret_cast<uintptr_t>(ws) % 256) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
+  if (prec != RQLP_PREC_FP64) {
+    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, st));
+    double *tmpY = ldy == l ? Y : P.Y;
+    RET(mixed_nn(P.mx, prec, m, n, W, ldw, l, tmpY, P.ctrl, 0, st));
+    if (tmpY != Y) CK(copy2d(tmpY, m, l, l, Y, ldy, nullptr, st));
+    return RQLP_OK;
+  }
+  CK(gemm_f64(false, a_dtype, A, lda, W, ldw, Y, ldy, m, l, n, 1.0, 0.0, P.ob.part, nullptr,
+              nullptr, st));
+  return RQLP_OK;
+}
+
+int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, const double *V,
+                 int64_t ldv, int32_t l, int32_t prec, double *Z, int64_t ldz, void *ws,
+                 size_t ws_bytes, rqlp_stream_t stream) {
+  if (!A || !V || !Z || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldv < l ||
+      ldz < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
+    return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_BF16) return RQLP_ERR_INVALID_ARG;
+  rqlp_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.prec = prec;
+  Plan P = carve(ws, std::max<int64_t>(m, l), std::max<int64_t>(n, l), l, o);
+  if (P.bytes > ws_bytes || reinterpret_cast<uintptr_t>(ws) % 256) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
+  if (prec != RQLP_PREC_FP64) {
+    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, st));
+    double *tmpZ = ldz == l ? Z : P.Z;
+    RET(mixed_tn(P.mx, prec, m, n, V, ldv, l, tmpZ, P.ctrl, 0, st));
+    if (tmpZ != Z) CK(copy2d(tmpZ, n, l, l, Z, ldz, nullptr, st));
+    return RQLP_OK;
+  }
+  CK(gemm_f64(true, a_dtype, A, lda, V, ldv, Z, ldz, n, l, m, 1.0, 0.0, P.ob.part, nullptr,
+              nullptr, st));
+  return RQLP_OK;
+}
+
+int rqlp_orth(const double *X, int64_t rows, int32_t l, int64_t ldx, double *Qx, int64_t ldq,
+              double *R, void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  if (!X || !Qx || !ws || rows <= 0 || l < 1 || l > kMaxL || l > rows || ldx < l || ldq < l)
+    return RQLP_ERR_INVALID_ARG;
+  rqlp_opts o;
+  std::memset(&o, 0, sizeof(o));
+  Plan P = carve(ws, rows, l, l, o);
+  if (P.bytes > ws_bytes || reinterpret_cast<uintptr_t>(ws) % 256) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
+  return orth(X, rows, l, ldx, Qx, ldq, R, P.ob, P.ctrl, 0, st);
+}
+
+int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, int32_t *piv0,
+              double *Q0, void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  if (!Bt || !R0t || !piv0 || !ws || n <= 0 || l < 1 || l > kMaxL || l > n || ldb < l)
+    return RQLP_ERR_INVALID_ARG;
+  rqlp_opts o;
+  std::memset(&o, 0, sizeof(o));
+  Plan P = carve(ws, l, n, l, o);
+  if (P.bytes > ws_bytes || reinterpret_cast<uintptr_t>(ws) % 256) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
+  CK(cpqr_wide(Bt, n, l, ldb, R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, P.ctrl, 0, 0, st));
+  if (Q0) CK(form_q(P.Vh, l, P.tau, l, l, Q0, l, st));
+  return RQLP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Shared device-side helpers: the control block at the head of every
+// workspace, status reporting, bounded waits and the grid barrier used by
+// the cooperative kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rqlp.h"
+
+namespace rqk {
+
+// Control block at offset 0 of a workspace; zeroed at the start of each call.
+struct Ctrl {
+  int status;               // first error (< 0) or first warning (> 0)
+  int shift_flag[15];       // per CholeskyQR site: 1 when a pass needed the shift
+  unsigned bar_count;       // grid barrier: arrivals in the current generation
+  unsigned bar_gen;         // grid barrier: generation counter
+  int timeout_site;         // diagnostics: which wait gave up
+  int pad[13];
+};
+static_assert(sizeof(Ctrl) == 128, "Ctrl layout");
+
+constexpr int kMaxL = 256;               // widest sketch supported
+constexpr int kShiftSites = 15;
+constexpr unsigned long long kDefaultSpinNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p) {
+  return *reinterpret_cast<const volatile int *>(p);
+}
+
+// Record a status: errors override warnings, the first error wins.
+__device__ inline void set_status(Ctrl *c, int code) {
+  int old = ld_volatile_i32(&c->status);
+  while (true) {
+    if (old < 0) return;
+    if (code > 0 && old > 0) return;
+    int prev = atomicCAS(&c->status, old, code);
+    if (prev == old) return;
+    old = prev;
+  }
+}
+
+// Grid-wide barrier for a cooperative launch of `nblocks` CTAs.  Every wait
+// is bounded by `limit_ns`; on timeout the status becomes RQLP_ERR_TIMEOUT.
+// `extra` > 0 makes the barrier wait for arrivals that never come (used only
+// to test the timeout path).  Returns false if the caller must stop: the
+// wait timed out or an error is already recorded.
+__device__ inline bool grid_barrier(Ctrl *c, unsigned nblocks, unsigned long long limit_ns,
+                                    unsigned extra, int site) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned gen = ld_acquire_u32(&c->bar_gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+    if (arrived == nblocks + extra) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(&c->bar_gen) == gen) {
+        if (ld_volatile_i32(&c->status) < 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > limit_ns) {
+          set_status(c, RQLP_ERR_TIMEOUT);
+          atomicExch(&c->timeout_site, site);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ld_volatile_i32(&c->status) < 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the whole CTA; `red` is shared scratch of >= 32 doubles.  All
+// threads receive the result.
+__device__ inline double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+}  // namespace rqk

@@ -1,0 +1,284 @@
+// Small dense FP64 kernels around the l x l matrices of the method: the
+// Cholesky factor and triangular inverse of CholeskyQR, explicit Q from
+// Householder reflectors, transposes, gathers and diagonals.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace rqk {
+
+namespace {
+
+constexpr double kEps = 1.1102230246251565e-16;  // unit roundoff of binary64
+
+// One CTA.  Upper Cholesky G = R^T R, right-looking, on the upper triangle.
+// A pivot d_j <= l * eps * G_jj means the Gram matrix is numerically
+// singular; the factorization is then redone once on G + s I with the shift
+// s = 11 (rows l + l (l + 1)) u ||X||_F^2 of shifted CholeskyQR (Fukaya,
+// Kannan, Nakatsukasa, Yamamoto and Yanagisawa, SIAM J. Sci. Comput. 2020),
+// and ctrl->shift_flag[site] is raised so that the caller's extra pass runs.
+__global__ void __launch_bounds__(1024)
+k_chol_upper(const double *__restrict__ G, int l, double rows, double *__restrict__ R, Ctrl *ctrl,
+             int site, const int *skip_unless, int use_smem) {
+  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double *W = use_smem ? sm : R;
+  double tr = 0.0;
+  for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
+  tr = block_sum(tr, red);
+  int fail = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift = attempt ? 11.0 * (rows * l + (double)l * (l + 1)) * kEps * tr : 0.0;
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int i = e / l, j = e - i * l;
+      W[e] = G[e] + (i == j ? shift : 0.0);
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int j = 0; j < l; ++j) {
+      const double d = W[(int64_t)j * l + j];
+      const double g0 = G[(int64_t)j * l + j] + shift;
+      if (!isfinite(d) || !isfinite(g0)) { if (tid == 0) s_fail = 2; break; }
+      if (!(d > (double)l * 2.0 * kEps * g0) || !(d > 0.0)) { if (tid == 0) s_fail = 1; break; }
+      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      __syncthreads();
+      for (int c = j + 1 + tid; c < l; c += blockDim.x) W[(int64_t)j * l + c] *= inv;
+      if (tid == 0) W[(int64_t)j * l + j] = rjj;
+      __syncthreads();
+      for (int a = j + 1 + warp; a < l; a += nw) {
+        const double ra = W[(int64_t)j * l + a];
+        for (int c = a + lane; c < l; c += 32) W[(int64_t)a * l + c] -= ra * W[(int64_t)j * l + c];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    fail = s_fail;
+    __syncthreads();
+    if (fail == 0) break;
+    if (fail == 2) break;
+    if (attempt == 0 && tid == 0) {
+      ctrl->shift_flag[site] = 1;
+      set_status(ctrl, RQLP_WARN_SHIFTED_CHOLQR);
+    }
+  }
+  if (fail == 2) {
+    if (tid == 0) set_status(ctrl, RQLP_ERR_NONFINITE);
+  } else if (fail == 1) {
+    if (tid == 0) set_status(ctrl, RQLP_ERR_RANK_DEFICIENT);
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e - i * l;
+    R[e] = (j >= i) ? W[e] : 0.0;
+  }
+}
+
+// Rinv = R^{-1}, R upper triangular l x l.  One warp per column c: row i of
+// the column solves R(i, i:c) x(i:c) = e_c(i) from the bottom up.
+__global__ void __launch_bounds__(256)
+k_trinv_upper(const double *__restrict__ R, int l, double *__restrict__ Rinv,
+              const int *skip_unless) {
+  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  __shared__ double xs[8][kMaxL];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= l) return;
+  double *x = xs[warp];
+  for (int i = lane; i < l; i += 32) x[i] = 0.0;
+  __syncwarp();
+  if (lane == 0) x[c] = 1.0 / R[(int64_t)c * l + c];
+  __syncwarp();
+  for (int i = c - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int t = i + 1 + lane; t <= c; t += 32) s = fma(R[(int64_t)i * l + t], x[t], s);
+    s = warp_sum(s);
+    if (lane == 0) x[i] = -s / R[(int64_t)i * l + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < l; i += 32) Rinv[(int64_t)i * l + c] = x[i];
+}
+
+__global__ void k_transpose(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
+                            double *__restrict__ Y, int64_t ldy) {
+  __shared__ double t[32][33];
+  const int64_t bi = (int64_t)blockIdx.y * 32, bj = (int64_t)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = bi + k, j = bj + threadIdx.x;
+    if (i < r && j < c) t[k][threadIdx.x] = X[i * ldx + j];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t j = bj + k, i = bi + threadIdx.x;
+    if (i < r && j < c) Y[j * ldy + i] = t[threadIdx.x][k];
+  }
+}
+
+__global__ void k_copy2d(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
+                         double *__restrict__ Y, int64_t ldy, const int *skip_unless) {
+  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    Y[i * ldy + j] = X[i * ldx + j];
+  }
+}
+
+__global__ void k_set_identity(double *X, int64_t r, int64_t c, int64_t ld) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    X[i * ld + j] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_gather_cols(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
+                              const int32_t *__restrict__ perm, double *__restrict__ Y,
+                              int64_t ldy) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    const int32_t pj = perm[j];
+    Y[i * ldy + j] = (pj >= 0 && pj < c) ? X[i * ldx + pj] : 0.0;
+  }
+}
+
+__global__ void k_iota(int32_t *p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (int32_t)i;
+}
+
+__global__ void k_diag_of(const double *__restrict__ T, int l, int64_t ldt, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < l) out[i] = T[(int64_t)i * ldt + i];
+}
+
+__global__ void k_zero_triangle(double *T, int l, int64_t ld, int strict_lower) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
+    const int i = e / l, j = e - i * l;
+    if (strict_lower ? (i > j) : (j > i)) T[(int64_t)i * ld + j] = 0.0;
+  }
+}
+
+// Column c of Q = H_0 ... H_{t-1} e_c, applying H_s for s = min(c, t-1) .. 0
+// (H_s e_c = e_c for s > c).  One warp per column, rows <= kMaxL.
+__global__ void __launch_bounds__(256)
+k_form_q(const double *__restrict__ Vh, int64_t ldv, const double *__restrict__ tau, int rows,
+         int t, double *__restrict__ Q, int64_t ldq) {
+  __shared__ double xs[8][kMaxL];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= t) return;
+  double *x = xs[warp];
+  for (int i = lane; i < rows; i += 32) x[i] = (i == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int s = min(c, t - 1); s >= 0; --s) {
+    const double ts = tau[s];
+    if (ts == 0.0) continue;
+    double w = 0.0;
+    for (int i = s + lane; i < rows; i += 32) w = fma(Vh[(int64_t)i * ldv + s], x[i], w);
+    w = warp_sum(w) * ts;
+    for (int i = s + lane; i < rows; i += 32) x[i] -= w * Vh[(int64_t)i * ldv + s];
+    __syncwarp();
+  }
+  for (int i = lane; i < rows; i += 32) Q[(int64_t)i * ldq + c] = x[i];
+}
+
+inline int grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > 4LL * num_sms()) b = 4LL * num_sms();
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
+                       const int *skip_unless, cudaStream_t st) {
+  const size_t smem = (size_t)l * l * sizeof(double);
+  const bool use_smem = smem <= 200 * 1024;
+  if (use_smem) {
+    static size_t set_to = 0;
+    if (smem > 48 * 1024 && smem > set_to) {
+      cudaError_t e = cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(200 * 1024));
+      if (e != cudaSuccess) return e;
+      set_to = 200 * 1024;
+    }
+  }
+  k_chol_upper<<<1, 1024, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, ctrl, site,
+                                                      skip_unless, use_smem ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t trinv_upper(const double *R, int l, double *Rinv, const int *skip_unless,
+                        cudaStream_t st) {
+  k_trinv_upper<<<(l + 7) / 8, 256, 0, st>>>(R, l, Rinv, skip_unless);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t transpose(const double *X, int64_t r, int64_t c, int64_t ldx, double *Y, int64_t ldy,
+                      cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((c + 31) / 32), (unsigned)((r + 31) / 32));
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(X, r, c, ldx, Y, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t copy2d(const double *X, int64_t r, int64_t c, int64_t ldx, double *Y, int64_t ldy,
+                   const int *skip_unless, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_copy2d<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ldx, Y, ldy, skip_unless);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(double *X, int64_t r, int64_t c, int64_t ld, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_set_identity<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ld);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gather_cols(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                        double *Y, int64_t ldy, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_gather_cols<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ldx, perm, Y, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t iota(int32_t *p, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_iota<<<grid_for(n, 256), 256, 0, st>>>(p, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t diag_of(const double *T, int l, int64_t ldt, double *out, cudaStream_t st) {
+  k_diag_of<<<(l + 255) / 256, 256, 0, st>>>(T, l, ldt, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaStream_t st) {
+  k_zero_triangle<<<grid_for((int64_t)l * l, 256), 256, 0, st>>>(T, l, ld, strict_lower ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
+                   double *Q, int64_t ldq, cudaStream_t st) {
+  if (rows > kMaxL || t <= 0) return cudaErrorInvalidValue;
+  k_form_q<<<(t + 7) / 8, 256, 0, st>>>(Vh, ldv, tau, (int)rows, t, Q, ldq);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rqk

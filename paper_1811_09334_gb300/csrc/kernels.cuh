@@ -1,0 +1,89 @@
+// Host-side launchers shared by the translation units of the library.
+#pragma once
+
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rqk {
+
+int num_sms();
+
+// Launch counter (every launcher adds its launches) and event timing of
+// kernel classes (see prof.cu).
+void count_launch(int n = 1);
+long long launch_count();
+enum ProfClass { kProfProducts = 0, kProfCpqr = 1, kProfOrth = 2, kProfSmall = 3, kProfClasses = 4 };
+int prof_start(int cls, cudaStream_t st);
+void prof_stop(int cls, int idx, cudaStream_t st);
+
+// Carves a workspace in 256-byte aligned pieces; with a null base it only
+// measures.
+struct Arena {
+  char *base;
+  size_t off = 0;
+  explicit Arena(void *b) : base(reinterpret_cast<char *>(b)) {}
+  template <class T>
+  T *take(size_t count) {
+    const size_t bytes = (count * sizeof(T) + 255) / 256 * 256;
+    T *r = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += bytes;
+    return r;
+  }
+};
+
+// ---- gemm_f64.cu ---------------------------------------------------------
+int64_t gemm_f64_splits(int64_t M, int64_t N, int64_t K);
+size_t gemm_f64_part_bytes(int64_t M, int64_t N, int64_t K);
+// C = alpha op(A) B + beta C; op(A) = A (M x K) or A^T (A is K x M).
+// With rowmap, row i of the result goes to row rowmap[i] of C.  `part` is
+// split-K scratch of gemm_f64_part_bytes(M, N, K) bytes (M * N doubles at
+// least when rowmap is used).  skip_unless: the kernels return at once when
+// *skip_unless == 0 (device-side conditional passes); may be null.
+cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const double *B,
+                     int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                     double alpha, double beta, double *part, const int32_t *rowmap,
+                     const int *skip_unless, cudaStream_t st);
+
+// ---- dense_small.cu ------------------------------------------------------
+// Cholesky G = R^T R of an l x l SPD matrix (upper R, ld l), breakdown
+// detection, one shifted retry with Fukaya's shift for `rows` x l data.
+cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
+                       const int *skip_unless, cudaStream_t st);
+// Rinv = R^{-1} for upper triangular R (l x l, ld l).
+cudaError_t trinv_upper(const double *R, int l, double *Rinv, const int *skip_unless,
+                        cudaStream_t st);
+// Y = X^T for an r x c matrix (ld ldx) into c x r (ld ldy).
+cudaError_t transpose(const double *X, int64_t r, int64_t c, int64_t ldx, double *Y, int64_t ldy,
+                      cudaStream_t st);
+// Copy an r x c block (optionally only when *skip_unless != 0).
+cudaError_t copy2d(const double *X, int64_t r, int64_t c, int64_t ldx, double *Y, int64_t ldy,
+                   const int *skip_unless, cudaStream_t st);
+// Fill an r x c block with the identity pattern (1 on the diagonal).
+cudaError_t set_identity(double *X, int64_t r, int64_t c, int64_t ld, cudaStream_t st);
+// Y[:, j] = X[:, perm[j]] for an r x c matrix.
+cudaError_t gather_cols(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                        double *Y, int64_t ldy, cudaStream_t st);
+// p[i] = i (a valid permutation, written before a pivoting kernel that may abort)
+cudaError_t iota(int32_t *p, int64_t n, cudaStream_t st);
+// Lvalues[i] = T[i][i]
+cudaError_t diag_of(const double *T, int l, int64_t ldt, double *out, cudaStream_t st);
+// Zero the strict lower (lower_zero = 1) or strict upper part of an l x l matrix.
+cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaStream_t st);
+// Form Q = H_0 H_1 ... H_{t-1} [I; 0] (rows x t, ld ldq) from reflectors stored
+// as columns of Vh (rows x t, ld ldv; v_s[s] = 1 implicit, zeros above) and tau.
+cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
+                   double *Q, int64_t ldq, cudaStream_t st);
+
+// ---- cpqr.cu ---------------------------------------------------------------
+size_t cpqr_ws_bytes(int64_t n, int l);
+// Column-pivoted Householder QR of the l x n matrix whose columns are the
+// rows of Bt (n x l, ld ldb).  Writes R0t (n x l, ld ldr), piv (n), the
+// reflectors Vh (l x l, ld l) and tau (l).  Cooperative launch.
+cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
+                      int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
+                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st);
+
+}  // namespace rqk

@@ -1,0 +1,315 @@
+"""Python binding of the randomized QLP C ABI (include/rqlp.h).
+
+Argument marshalling only: every step of the factorization runs in the CUDA
+kernels of librqlp.so.  Device memory (outputs and workspace) comes from
+torch; the work is enqueued on torch's current CUDA stream.  There is no
+CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librqlp.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "rqlp.h")
+
+RQLP_OK = 0
+RQLP_WARN_SHIFTED_CHOLQR = 1
+STATUS = {0: "RQLP_OK", 1: "RQLP_WARN_SHIFTED_CHOLQR", -1: "RQLP_ERR_INVALID_ARG",
+          -2: "RQLP_ERR_NONFINITE", -3: "RQLP_ERR_RANK_DEFICIENT", -4: "RQLP_ERR_TIMEOUT",
+          -5: "RQLP_ERR_CUDA", -6: "RQLP_ERR_WORKSPACE", -7: "RQLP_ERR_UNSUPPORTED"}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16": 2}
+F64, F32 = 0, 1
+
+_c_i32, _c_i64, _c_sz, _c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("q", _c_i32), ("d", _c_i32), ("pivot2", _c_i32), ("prec", _c_i32),
+                ("block_b", _c_i32), ("debug_flags", _c_i32), ("spin_limit_ns", _c_i64)]
+
+
+class RqlpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, STATUS.get(code, "unknown"), code))
+
+
+_lib = None
+
+_SIGS = {
+    "rqlp_status_string": (ctypes.c_char_p, [_c_i32]),
+    "rqlp_version": (_c_i32, []),
+    "rqlp_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
+    "rqlp": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
+                      ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "rqlp_read_status": (_c_i32, [_c_p, _c_p]),
+    "rqlp_host_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts),
+                                         _c_i32]),
+    "rqlp_host": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i32, _c_i32, _c_p,
+                           ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz,
+                           _c_p]),
+    "rqlp_stage_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32]),
+    "rqlp_sketch": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_p, _c_i64, _c_i32, _c_i32,
+                             _c_p, _c_i64, _c_p, _c_sz, _c_p]),
+    "rqlp_project": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_p, _c_i64, _c_i32, _c_i32,
+                              _c_p, _c_i64, _c_p, _c_sz, _c_p]),
+    "rqlp_orth": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_i64, _c_p, _c_p, _c_sz, _c_p]),
+    "rqlp_cpqr": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "rqlp_launch_count": (ctypes.c_longlong, []),
+    "rqlp_profile_begin": (_c_i32, []),
+    "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
+}
+
+PROFILE_CLASSES = ("products_with_A", "cpqr_of_B", "cholesky_qr", "explicit_Q0")
+
+
+def launch_count() -> int:
+    return int(lib().rqlp_launch_count())
+
+
+def profile_begin():
+    _check(lib().rqlp_profile_begin(), "rqlp_profile_begin")
+
+
+def profile_end() -> dict:
+    n = len(PROFILE_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(lib().rqlp_profile_end(ctypes.cast(ms, _c_p), ctypes.cast(cnt, _c_p), n),
+           "rqlp_profile_end")
+    return {name: (ms[i], int(cnt[i])) for i, name in enumerate(PROFILE_CLASSES)}
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions include/rqlp.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rqlp\w*)\s*\(", text)))
+
+
+def lib():
+    """The loaded librqlp.so with its argument types declared (raises if not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librqlp.so is not built: run `python -m paper_1811_09334_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def opts(q=0, d=1, pivot2=True, prec="fp64", block_b=0, debug_flags=0, spin_limit_ns=0) -> Opts:
+    return Opts(int(q), int(d), 1 if pivot2 else 0, PREC[prec] if isinstance(prec, str) else int(prec),
+                int(block_b), int(debug_flags), int(spin_limit_ns))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if t is not None else None
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code < 0:
+        raise RqlpError(code, where)
+    return code
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError("A must be float64 or float32")
+
+
+def _row_major(t, name):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s must be a 2-D row-major tensor (stride(1) == 1)" % name)
+    return t.stride(0)
+
+
+def workspace(nbytes: int, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def read_status(ws, stream=None) -> int:
+    return lib().rqlp_read_status(ctypes.c_void_p(_ptr(ws)), _stream(stream))
+
+
+def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
+         prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
+         stream=None, check: bool = True, debug_flags: int = 0, spin_limit_ns: int = 0) -> dict:
+    """Randomized QLP A ~= Q L P^T on the GPU (Algorithms 2.1, 2.2 and 4.1).
+
+    A: (m, n) float64/float32 CUDA tensor, row-major.  Omega: (n, k + p)
+    float64 CUDA tensor.  Returns a dict with Q, L, P, Lvalues, piv0, piv1,
+    status (and ws, for reuse).  With check=True the stream is synchronized
+    and a device-side error raises RqlpError.
+    """
+    torch = _torch()
+    m, n = A.shape
+    l = k + p
+    lda = _row_major(A, "A")
+    ldo = _row_major(Omega, "Omega")
+    if Omega.dtype != torch.float64 or tuple(Omega.shape) != (n, l):
+        raise ValueError("Omega must be float64 of shape (n, k + p)")
+    o = opts(q, d, pivot2, prec, block_b, debug_flags, spin_limit_ns)
+    L_ = lib()
+    need = L_.rqlp_workspace_size(m, n, k, p, ctypes.byref(o))
+    if need == 0:
+        raise RqlpError(-1, "rqlp_workspace_size")
+    dev = A.device
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    if out is None:
+        out = dict(Q=torch.empty((m, l), dtype=torch.float64, device=dev),
+                   L=torch.empty((l, l), dtype=torch.float64, device=dev),
+                   P=torch.empty((n, l), dtype=torch.float64, device=dev),
+                   Lvalues=torch.empty((l,), dtype=torch.float64, device=dev),
+                   piv0=torch.empty((n,), dtype=torch.int32, device=dev),
+                   piv1=torch.empty((l,), dtype=torch.int32, device=dev))
+    st = _stream(stream)
+    code = L_.rqlp(_ptr(A), _dtype_code(A), m, n, lda, k, p, _ptr(Omega), ldo, ctypes.byref(o),
+                   _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]), _ptr(out["Lvalues"]),
+                   _ptr(out["piv0"]), _ptr(out["piv1"]), _ptr(ws), ws.numel(), st)
+    _check(code, "rqlp")
+    res = dict(out)
+    res["ws"] = ws
+    if check:
+        status = L_.rqlp_read_status(_ptr(ws), st)
+        _check(status, "rqlp (device status)")
+        res["status"] = status
+    return res
+
+
+def rqlp_host(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1, pivot2: bool = True,
+              prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
+              device="cuda", stream=None) -> dict:
+    """rqlp() on host tensors: copies in, factors, copies out, synchronizes.
+
+    A_host / Omega_host are CPU tensors (pinned for full copy speed); the
+    results come back in CPU tensors (pinned when `out` is not given).
+    """
+    torch = _torch()
+    m, n = A_host.shape
+    l = k + p
+    if not A_host.is_contiguous() or not Omega_host.is_contiguous():
+        raise ValueError("host inputs must be contiguous")
+    o = opts(q, d, pivot2, prec, block_b)
+    L_ = lib()
+    dt = _dtype_code(A_host)
+    need = L_.rqlp_host_workspace_size(m, n, k, p, ctypes.byref(o), dt)
+    if need == 0:
+        raise RqlpError(-1, "rqlp_host_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    if out is None:
+        pin = dict(pin_memory=True)
+        out = dict(Q=torch.empty((m, l), dtype=torch.float64, **pin),
+                   L=torch.empty((l, l), dtype=torch.float64, **pin),
+                   P=torch.empty((n, l), dtype=torch.float64, **pin),
+                   Lvalues=torch.empty((l,), dtype=torch.float64, **pin),
+                   piv0=torch.empty((n,), dtype=torch.int32, **pin),
+                   piv1=torch.empty((l,), dtype=torch.int32, **pin))
+    code = L_.rqlp_host(_ptr(A_host), dt, m, n, k, p, _ptr(Omega_host), ctypes.byref(o),
+                        _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]), _ptr(out["Lvalues"]),
+                        _ptr(out["piv0"]), _ptr(out["piv1"]), _ptr(ws), ws.numel(),
+                        _stream(stream))
+    _check(code, "rqlp_host")
+    res = dict(out)
+    res["ws"] = ws
+    res["status"] = code
+    return res
+
+
+# ------------------------------------------------------------------ stages
+def _stage_ws(rows, cols, l, prec, device, ws=None):
+    need = lib().rqlp_stage_workspace_size(rows, cols, l, PREC[prec] if isinstance(prec, str) else prec)
+    if need == 0:
+        raise RqlpError(-1, "rqlp_stage_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    return ws
+
+
+def sketch(A, W, prec="fp64", ws=None, stream=None):
+    """Y = A W (Algorithm 2.1, step 2)."""
+    torch = _torch()
+    m, n = A.shape
+    l = W.shape[1]
+    ws = _stage_ws(m, n, l, prec, A.device, ws)
+    Y = torch.empty((m, l), dtype=torch.float64, device=A.device)
+    st = _stream(stream)
+    _check(lib().rqlp_sketch(_ptr(A), _dtype_code(A), m, n, _row_major(A, "A"), _ptr(W),
+                             _row_major(W, "W"), l, PREC[prec], _ptr(Y), l, _ptr(ws), ws.numel(), st),
+           "rqlp_sketch")
+    _check(lib().rqlp_read_status(_ptr(ws), st), "rqlp_sketch (device status)")
+    return Y
+
+
+def project(A, V, prec="fp64", ws=None, stream=None):
+    """Z = A^T V = (V^T A)^T (Algorithm 2.1, step 4)."""
+    torch = _torch()
+    m, n = A.shape
+    l = V.shape[1]
+    ws = _stage_ws(m, n, l, prec, A.device, ws)
+    Z = torch.empty((n, l), dtype=torch.float64, device=A.device)
+    st = _stream(stream)
+    _check(lib().rqlp_project(_ptr(A), _dtype_code(A), m, n, _row_major(A, "A"), _ptr(V),
+                              _row_major(V, "V"), l, PREC[prec], _ptr(Z), l, _ptr(ws), ws.numel(),
+                              st), "rqlp_project")
+    _check(lib().rqlp_read_status(_ptr(ws), st), "rqlp_project (device status)")
+    return Z
+
+
+def orth(X, want_r=True, ws=None, stream=None):
+    """Thin QR X = Q R by CholeskyQR2 (Algorithm 2.1, step 3); returns (Q, R, status)."""
+    torch = _torch()
+    rows, l = X.shape
+    ws = _stage_ws(rows, l, l, "fp64", X.device, ws)
+    Q = torch.empty((rows, l), dtype=torch.float64, device=X.device)
+    R = torch.empty((l, l), dtype=torch.float64, device=X.device) if want_r else None
+    st = _stream(stream)
+    _check(lib().rqlp_orth(_ptr(X), rows, l, _row_major(X, "X"), _ptr(Q), l, _ptr(R), _ptr(ws),
+                           ws.numel(), st), "rqlp_orth")
+    status = _check(lib().rqlp_read_status(_ptr(ws), st), "rqlp_orth (device status)")
+    return Q, R, status
+
+
+def cpqr(B, ws=None, stream=None):
+    """Column-pivoted QR of the l x n matrix B (Algorithm 2.1, step 5).
+
+    Returns (Q0, R0, piv0) with B[:, piv0] = Q0 @ R0.
+    """
+    torch = _torch()
+    l, n = B.shape
+    Bt = B.t().contiguous()
+    ws = _stage_ws(l, n, l, "fp64", B.device, ws)
+    R0t = torch.empty((n, l), dtype=torch.float64, device=B.device)
+    piv = torch.empty((n,), dtype=torch.int32, device=B.device)
+    Q0 = torch.empty((l, l), dtype=torch.float64, device=B.device)
+    st = _stream(stream)
+    _check(lib().rqlp_cpqr(_ptr(Bt), n, l, l, _ptr(R0t), _ptr(piv), _ptr(Q0), _ptr(ws), ws.numel(),
+                           st), "rqlp_cpqr")
+    _check(lib().rqlp_read_status(_ptr(ws), st), "rqlp_cpqr (device status)")
+    return Q0, R0t.t().contiguous(), piv

@@ -1,0 +1,45 @@
+"""The C-ABI library loads and exports what include/rqlp.h declares (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_1811_09334_gb300 import rqlp as R
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return R.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = R.header_symbols()
+    assert "rqlp" in names and "rqlp_workspace_size" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(R._SIGS)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.rqlp_version() >= 100
+    for code in R.STATUS:
+        assert lib.rqlp_status_string(code)
+    assert lib.rqlp_status_string(12345) == b"unknown status"
+
+
+def test_argument_errors_are_synchronous(lib):
+    o = R.opts()
+    assert lib.rqlp_workspace_size(0, 10, 2, 2, ctypes.byref(o)) == 0
+    assert lib.rqlp_workspace_size(10, 10, 8, 3, ctypes.byref(o)) == 0  # l > n
+    assert lib.rqlp_workspace_size(1000, 500, 200, 60, ctypes.byref(o)) == 0  # l > 256
+    assert lib.rqlp_workspace_size(100, 50, 5, 5, ctypes.byref(o)) > 0
+    bad = R.opts(pivot2=False, d=0)
+    assert lib.rqlp_workspace_size(100, 50, 5, 5, ctypes.byref(bad)) == 0
+    # null pointers are rejected before any CUDA call
+    code = lib.rqlp(None, 0, 100, 50, 50, 5, 5, None, 10, ctypes.byref(o), None, None, None, None,
+                    None, None, None, 0, None)
+    assert code == -1
+    code = lib.rqlp_orth(None, 10, 4, 4, None, 4, None, None, 0, None)
+    assert code == -1

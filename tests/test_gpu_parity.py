@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP64 path): L and the L-values to 1e-10 relative (the target the
+method's FP64 form is held to); pivots identical; Q and P elementwise to
+1e-9 (they inherit the conditioning of the sketch, about 1e4 at most here);
+the single products Y = A Omega and A^T V to 1e-13 relative (K <= 8192 terms
+of FP64 rounding).
+"""
+import numpy as np
+import pytest
+
+from oracle import rqlp_ref as O
+from paper_1811_09334_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1811_09334_gb300 import rqlp
+    rqlp.lib()
+    return rqlp
+
+
+DEV = "cuda"
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def _relmax(a, b):
+    a = a.cpu().numpy() if hasattr(a, "cpu") else a
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# ------------------------------------------------------------------ products
+@pytest.mark.parametrize("m,n,l", [(2000, 1000, 30), (333, 257, 17), (64, 64, 1), (1025, 130, 129)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_sketch_and_projection(R, m, n, l, dt):
+    rng = np.random.default_rng(m + n + l)
+    A = rng.standard_normal((m, n))
+    if dt == "f32":
+        A = A.astype(np.float32)
+    Om = rng.standard_normal((n, l))
+    V = rng.standard_normal((m, l))
+    Y = R.sketch(_t(A), _t(Om))
+    Z = R.project(_t(A), _t(V))
+    A64 = A.astype(np.float64)
+    assert _relmax(Y, O.sketch(A64, Om)) <= 1e-13
+    assert _relmax(Z, O.adjoint_product(A64, V)) <= 1e-13
+
+
+# ------------------------------------------------------------------ thin QR
+@pytest.mark.parametrize("rows,l", [(2000, 30), (8192, 110), (300, 256), (7, 7), (129, 1)])
+def test_orth_matches_householder(R, rows, l):
+    A = W.low_rank_from_spectrum(rows, l, np.linspace(1.0, 0.01, l), 5)
+    Q, Rr, status = R.orth(_t(A))
+    Qo, Ro = O.householder_qr(A)
+    assert status == 0
+    assert _relmax(Q, Qo) <= 1e-11
+    assert _relmax(Rr, Ro) <= 1e-12
+    Qn = Q.cpu().numpy()
+    assert np.abs(Qn.T @ Qn - np.eye(l)).max() <= 1e-14 * max(10, l)
+
+
+def test_orth_shifted_pass_on_ill_conditioned_input(R):
+    # condition number ~1e12: the first Gram matrix is numerically singular,
+    # the shifted pass plus two more passes still give an orthonormal basis.
+    sigma = np.logspace(0, -12, 40)
+    A = W.low_rank_from_spectrum(3000, 40, sigma, 6)
+    Q, Rr, status = R.orth(_t(A))
+    assert status == R.RQLP_WARN_SHIFTED_CHOLQR
+    Qn, Rn = Q.cpu().numpy(), Rr.cpu().numpy()
+    assert np.abs(Qn.T @ Qn - np.eye(40)).max() <= 1e-13
+    assert np.abs(Qn @ Rn - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.all(np.diag(Rn) > 0)
+
+
+# ------------------------------------------------------------------ CPQR
+@pytest.mark.parametrize("l,n", [(30, 1000), (110, 8192), (17, 17), (5, 3000), (256, 1200)])
+def test_cpqr_matches_oracle(R, l, n):
+    rng = np.random.default_rng(l * 7 + n)
+    B = rng.standard_normal((l, n)) * (0.999 ** np.arange(n))[None, :]
+    Q0, R0, piv = R.cpqr(_t(B))
+    Qo, Ro, po = O.cpqr(B)
+    assert np.array_equal(piv.cpu().numpy(), po)
+    assert _relmax(R0, Ro) <= 1e-12
+    assert _relmax(Q0, Qo) <= 1e-12
+
+
+# ------------------------------------------------------------------ whole method
+def _compare(out, ref, l, tolL=1e-10, tolQP=1e-9):
+    Lg = out["L"].cpu().numpy()
+    assert _relmax(Lg, ref["L"]) <= tolL
+    lv = out["Lvalues"].cpu().numpy()
+    assert np.max(np.abs(lv - ref["Lvalues"]) / np.abs(ref["Lvalues"])) <= tolL
+    assert np.array_equal(out["piv0"].cpu().numpy()[:l], ref["piv0"][:l])
+    assert np.array_equal(out["piv1"].cpu().numpy(), ref["piv1"])
+    assert _relmax(out["Q"], ref["Q"]) <= tolQP
+    assert _relmax(out["P"], ref["P"]) <= tolQP
+
+
+@pytest.mark.parametrize("variant", [(True, 1), (False, 1), (False, 2), (False, 3)])
+def test_c1_rqlp_fp64_parity(R, variant):
+    """RQLP / ERQLP on the 2000 x 1000 sigma_j = j^-2 workload, k = 20, p = 10, q = 0."""
+    pr = W.c1()
+    Om = W.omega(pr.n, pr.l, 0)
+    pivot2, d = variant
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=0, d=d, pivot2=pivot2)
+    ref = O.rqlp(pr.A, pr.k, pr.p, Om, q=0, d=d, pivot2=pivot2)
+    _compare(out, ref, pr.l)
+    assert out["status"] == 0
+
+
+@pytest.mark.parametrize("m,n,k,p,q,d,pivot2", [
+    (777, 513, 13, 6, 1, 2, False),
+    (1000, 1000, 100, 10, 1, 2, False),
+    (513, 300, 40, 9, 2, 1, True),
+    (4096, 640, 60, 4, 1, 4, False),
+    (300, 200, 2, 0, 0, 1, True),
+])
+def test_ragged_shapes_with_power_steps(R, m, n, k, p, q, d, pivot2):
+    sigma = 10.0 ** (-np.arange(1, min(m, n) + 1) / 100.0)
+    A = W.low_rank_from_spectrum(m, n, sigma, m + n)
+    Om = W.omega(n, k + p, 3)
+    out = R.rqlp(_t(A), k, p, _t(Om), q=q, d=d, pivot2=pivot2)
+    ref = O.rqlp(A, k, p, Om, q=q, d=d, pivot2=pivot2)
+    _compare(out, ref, k + p)
+
+
+def test_full_width_sketch_is_deterministic_qlp(R):
+    # l = n (square Omega): the result is Stewart's pivoted QLP of A (Section 1).
+    A, _ = W.low_rank_from_spectrum(90, 40, 0.85 ** np.arange(40), 9), None
+    Om = W.omega(40, 40, 1)
+    out = R.rqlp(_t(A), 30, 10, _t(Om), pivot2=True)
+    ref = O.rqlp(A, 30, 10, Om, pivot2=True)
+    _compare(out, ref, 40)
+    s = np.linalg.svd(A, compute_uv=False)
+    Ln = out["L"].cpu().numpy()
+    assert np.allclose(np.linalg.svd(Ln, compute_uv=False), s, rtol=1e-11)
+
+
+def test_factorization_invariants_on_gpu(R):
+    pr = W.c1(m=1500, n=700, k=25, p=7)
+    Om = W.omega(pr.n, pr.l, 2)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False)
+    Q, L, P = (out[x].cpu().numpy() for x in ("Q", "L", "P"))
+    l = pr.l
+    assert np.abs(Q.T @ Q - np.eye(l)).max() <= 1e-13
+    assert np.abs(P.T @ P - np.eye(l)).max() <= 1e-13
+    assert np.abs(np.tril(L, -1)).max() == 0.0  # even d: upper middle factor
+    E = pr.A - Q @ L @ P.T
+    B = Q.T @ pr.A
+    assert abs(np.linalg.norm(E) ** 2 - (np.linalg.norm(pr.A) ** 2 - np.linalg.norm(B) ** 2)) <= 1e-12
+
+
+# ------------------------------------------------------------------ status paths
+def test_nonfinite_input_is_reported(R):
+    A = np.random.default_rng(1).standard_normal((200, 100))
+    A[17, 3] = np.nan
+    with pytest.raises(R.RqlpError) as e:
+        R.rqlp(_t(A), 5, 5, _t(W.omega(100, 10, 0)))
+    assert e.value.code == -2
+
+
+def test_device_wait_timeout_is_reported_and_context_survives(R):
+    # The first grid barrier of the CPQR kernel waits for one arrival that
+    # never comes; the bounded wait gives up after 50 ms and reports a status.
+    pr = W.c1(m=400, n=300, k=10, p=5)
+    Om = _t(W.omega(pr.n, pr.l, 0))
+    A = _t(pr.A)
+    with pytest.raises(R.RqlpError) as e:
+        R.rqlp(A, pr.k, pr.p, Om, debug_flags=1, spin_limit_ns=50_000_000)
+    assert e.value.code == -4
+    out = R.rqlp(A, pr.k, pr.p, Om)
+    assert out["status"] == 0
+
+
+def test_host_entry_point_matches_device_path(R):
+    pr = W.c1(m=1200, n=500, k=15, p=5)
+    Om = W.omega(pr.n, pr.l, 4)
+    dev = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False)
+    host = R.rqlp_host(torch.from_numpy(pr.A).pin_memory(), pr.k, pr.p,
+                       torch.from_numpy(Om).pin_memory(), q=1, d=2, pivot2=False)
+    for key in ("Q", "L", "P", "Lvalues", "piv0", "piv1"):
+        assert torch.equal(dev[key].cpu(), host[key]), key
+
+
+@pytest.mark.slow
+def test_c2_full_size_fp64_parity(R):
+    """The 8192 x 8192 ERQLP workload (q = 1, d = 2) in the launch configuration
+    the benchmark times, against the oracle run on the same matrix."""
+    pr = W.c2(device=DEV)
+    Om = W.omega(pr.n, pr.l, 0)
+    out = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False)
+    ref = O.rqlp(pr.A.cpu().numpy(), pr.k, pr.p, Om, q=1, d=2, pivot2=False)
+    _compare(out, ref, pr.l)
