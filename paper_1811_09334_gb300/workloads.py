@@ -71,11 +71,16 @@ def low_rank_from_spectrum(m: int, n: int, sigma: np.ndarray, seed: int,
     import torch
     tdt = torch.float64 if out_dtype == np.float64 else torch.float32
     def orth(G):
-        Gt = torch.from_numpy(G).to(device)
-        Q, R = torch.linalg.qr(Gt)
-        s = torch.sign(torch.diagonal(R))
-        s[s == 0] = 1.0
-        return Q * s
+        try:
+            Gt = torch.from_numpy(G).to(device)
+            Q, R = torch.linalg.qr(Gt)
+            s = torch.sign(torch.diagonal(R))
+            s[s == 0] = 1.0
+            return Q * s
+        except RuntimeError:
+            # torch's device linear algebra can be unavailable (e.g. under a
+            # profiler); the same construction then runs on the host.
+            return torch.from_numpy(_orthonormal_np(G)).to(device)
     X = orth(GX)
     del GX
     Y = orth(GY)
