@@ -161,6 +161,34 @@ int rqlp_orth(const double *X, int64_t rows, int32_t l, int64_t ldx, double *Qx,
 int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, int32_t *piv0,
               double *Q0, void *ws, size_t ws_bytes, rqlp_stream_t stream);
 
+/*
+ * rqlp_cpqr() for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment variant of Algorithm 2.1 step 5.
+ *
+ * Who needs it: code that runs under another runtime's memory manager which
+ * owns all of the device memory, or a latency-critical loop that must not call
+ * cudaMalloc (it can synchronize the whole device), so it cannot pass a
+ * workspace.  This entry point allocates nothing and calls no allocating
+ * routine; its scratch (control block, reflectors, pivot tables) lives in one
+ * fixed 2 MiB __device__ array inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *
+ * Arguments as for rqlp_cpqr() (Bt n x l device input, R0t n x l, piv0 n and,
+ * if not NULL, Q0 l x l device outputs).  With sync != 0 the call synchronizes
+ * `stream` and returns the device status; with sync == 0 it returns after
+ * enqueueing (the status then stays in the library's array until the next call).
+ * Limits: the pivot tables plus l x l reflectors must fit the 2 MiB array and
+ * each CTA's slab of columns must fit in shared memory (about
+ * n * l * 8 bytes <= 152 * 190 KiB on GB300); larger sizes return
+ * RQLP_ERR_WORKSPACE without touching the GPU.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the one array and clears its control block at the start, so calls
+ * whose work overlaps on the GPU (other streams or threads) race: serialize them.
+ */
+int rqlp_cpqr_static(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t,
+                     int32_t *piv0, double *Q0, int32_t sync, rqlp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Instrumentation.
  * ---------------------------------------------------------------------- */

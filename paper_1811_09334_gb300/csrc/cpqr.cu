@@ -284,6 +284,14 @@ size_t cpqr_ws_bytes(int64_t n, int l) {
   return b + 8192;
 }
 
+size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
+  const Plan pl = plan_for(n, l);
+  *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up(2 * (size_t)pl.G * sizeof(double)) + up(2 * (size_t)pl.G * sizeof(int32_t)) +
+         up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
+}
+
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
                       unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st) {

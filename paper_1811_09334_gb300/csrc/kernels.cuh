@@ -79,6 +79,9 @@ cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t row
 
 // ---- cpqr.cu ---------------------------------------------------------------
 size_t cpqr_ws_bytes(int64_t n, int l);
+// Scratch bytes cpqr_wide() touches when the column slabs fit in shared
+// memory (*fits tells whether they do; otherwise a global slab is needed too).
+size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits);
 // Column-pivoted Householder QR of the l x n matrix whose columns are the
 // rows of Bt (n x l, ld ldb).  Writes R0t (n x l, ld ldr), piv (n), the
 // reflectors Vh (l x l, ld l) and tau (l).  Cooperative launch.

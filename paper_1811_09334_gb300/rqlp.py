@@ -59,6 +59,7 @@ _SIGS = {
                               _c_p, _c_i64, _c_p, _c_sz, _c_p]),
     "rqlp_orth": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_i64, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "rqlp_cpqr_static": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_i32, _c_p]),
     "rqlp_launch_count": (ctypes.c_longlong, []),
     "rqlp_profile_begin": (_c_i32, []),
     "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
