@@ -108,6 +108,31 @@ def _sketch_flops(m, n, l, q):
     return (2 * q + 2) * 2.0 * m * n * l
 
 
+def _class_work(m, n, l, q, d, prec):
+    """Algorithmic work per factorization of each timed kernel class.
+
+    Products with A: 2q + 2 passes of 2 m n l flops, reading A once per pass
+    (8 bytes per element in FP64, 4 for the BF16 pair, 2 for BF16).
+    CholeskyQR on an N x l panel, per pass: Gram N l^2 flops (symmetric),
+    X R^-1 N l^2 flops (triangular) plus the l^3 / 3 R update, Cholesky and
+    triangular inverse l^3 / 3 each; two passes.  CPQR of B: 4 n l^2.
+    """
+    rows = [m] * q + [n] * q + [m, n] + [l] * max(0, d - 1)
+    passes = 2
+    a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0}[prec] * m * n
+    prod = ("flops", (2 * q + 2) * 2.0 * m * n * l) if prec == "fp64" else \
+        ("bytes", (2 * q + 2) * a_bytes)
+    return {
+        "products_with_A": prod,
+        "cpqr_of_B": ("flops", 4.0 * n * l * l),
+        "cholqr_gram": ("flops", passes * sum(r * l * l for r in rows)),
+        "cholqr_cholesky": ("flops", passes * len(rows) * l ** 3 / 3.0),
+        "cholqr_trinv": ("flops", passes * len(rows) * l ** 3 / 3.0),
+        "cholqr_apply": ("flops", passes * sum(r * l * l + l ** 3 / 3.0 for r in rows)),
+        "explicit_Q0": ("flops", 4.0 * l ** 3 / 3.0),
+    }
+
+
 def _oracle_run(A_np, Om_np, prec_forms_out, budget_s=25.0):
     """Times the FP64 CPU oracle on the same factorization (bounded sample)."""
     from oracle import rqlp_ref as O
@@ -163,7 +188,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": M, "n": N_, "k": K_RANK, "p": P_OVER,
-                       "q": Q_POW, "d": D_INNER, "prec": "fp64"},
+                       "q": Q_POW, "d": D_INNER, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
                              "kind": "oracle",
                              "sample": "%d whole factorizations of the workload" % args.steps},
@@ -264,23 +289,21 @@ def run_ours(args):
     prof = main["prof"]
     dom = max(prof, key=lambda c: prof[c][0])
     dom_ms, dom_cnt = prof[dom]
-    roof = None
-    if dom == "products_with_A":
-        per_launch_flops = flops / (2 * Q_POW + 2)
-        achieved = per_launch_flops * dom_cnt / (dom_ms / 1e3) / 1e12
-        if args.prec == "fp64":
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                    "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
-        else:
-            bytes_per = 4.0 * pr.m * pr.n if args.prec == "bf16x3" else 2.0 * pr.m * pr.n
-            gbs = bytes_per * dom_cnt / (dom_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_src}
+    steps_prof = main["steps"]
+    work = _class_work(pr.m, pr.n, pr.l, Q_POW, D_INNER, args.prec)
+    kind, amount = work[dom]
+    per_s = amount * steps_prof / (dom_ms / 1e3)
+    if kind == "bytes":
+        roof = {"bound": "hbm", "achieved": per_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": per_s / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src}
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "peak_source": "nominal FP64"}
+        roof = {"bound": "alu", "achieved": per_s / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": per_s / 1e12 / FP64_NOMINAL_TFLOPS,
+                "peak_source": "GB300 FP64 rate from its unit counts and 2.07 GHz clock "
+                               "(2 FMA/clk/SM x 152 SMs); no measured FP64 peak"}
     roof["kernel_class"] = dom
+    roof["launches_timed"] = int(dom_cnt)
+    roof["algorithmic_per_step"] = amount
     roof["traffic"] = None
     roof["time_share"] = dom_ms / sum(v[0] for v in prof.values()) if prof else None
 
@@ -325,7 +348,7 @@ def run_ours(args):
             "dtype": "f64" if args.prec == "fp64" else args.prec + "+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": pr.m, "n": pr.n, "k": pr.k, "p": pr.p,
-                       "q": Q_POW, "d": D_INNER, "prec": args.prec, "l2": "inputs larger than L2"},
+                       "q": Q_POW, "d": D_INNER, "l2": "inputs larger than L2"},
             "sketch_tflops": forms_out[args.prec]["sketch_tflops"],
             "forms": forms_out,
             "roofline": roof,
@@ -345,7 +368,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -197,7 +197,9 @@ long long rqlp_launch_count(void);
 
 /* Starts timing kernel classes: from now on rqlp() records a CUDA event pair
  * on its stream around (0) every product with A, (1) every column-pivoted QR
- * of B, (2) every CholeskyQR and (3) the explicit Q0 of the first CPQR. */
+ * of B, and, inside every CholeskyQR pass, (2) the Gram matrix, (3) the
+ * Cholesky factor, (4) the triangular inverse, (5) X R^{-1} with the R
+ * update; and (6) the explicit Q0 of the first CPQR. */
 int rqlp_profile_begin(void);
 
 /* Stops timing; waits for the recorded events and writes, per class c <

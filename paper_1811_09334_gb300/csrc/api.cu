@@ -62,52 +62,53 @@ void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBuf
 
 // CholeskyQR2 (+ a third pass iff a pass needed the shift): Xq = X R^{-1}.
 int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
-         const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
+              const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
   site %= kShiftSites;
   const int *flag = &ctrl->shift_flag[site];
-  // pass 1: X -> tmp
-  CK(gemm_f64(true, RQLP_F64, X, ldx, X, ldx, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
-              nullptr, st));
-  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, nullptr, st));
-  CK(trinv_upper(o.Rp, l, o.Rinv, nullptr, st));
-  CK(gemm_f64(false, RQLP_F64, X, ldx, o.Rinv, l, o.tmp, l, rows, l, l, 1.0, 0.0, o.part, nullptr,
-              nullptr, st));
-  if (R) CK(copy2d(o.Rp, l, l, l, o.Racc, l, nullptr, st));
-  // pass 2: tmp -> Xq
-  CK(gemm_f64(true, RQLP_F64, o.tmp, l, o.tmp, l, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
-              nullptr, st));
-  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, nullptr, st));
-  CK(trinv_upper(o.Rp, l, o.Rinv, nullptr, st));
-  CK(gemm_f64(false, RQLP_F64, o.tmp, l, o.Rinv, l, Xq, ldq, rows, l, l, 1.0, 0.0, o.part, nullptr,
-              nullptr, st));
-  if (R) {
-    CK(gemm_f64(false, RQLP_F64, o.Rp, l, o.Racc, l, o.Rtmp, l, l, l, l, 1.0, 0.0, o.part, nullptr,
-                nullptr, st));
-    CK(copy2d(o.Rtmp, l, l, l, o.Racc, l, nullptr, st));
-  }
+  int ev;
+  // one CholeskyQR pass: src -> dst, R_acc <- R_pass R_acc (skip: conditional pass)
+  auto pass = [&](const double *src, int64_t lds, double *dst, int64_t ldd, bool first,
+                  const int *skip) -> int {
+    ev = prof_start(kProfGram, st);
+    CK(gemm_f64(true, RQLP_F64, src, lds, src, lds, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
+                skip, st));
+    prof_stop(kProfGram, ev, st);
+    ev = prof_start(kProfChol, st);
+    CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, skip, st));
+    prof_stop(kProfChol, ev, st);
+    ev = prof_start(kProfTrinv, st);
+    CK(trinv_upper(o.Rp, l, o.Rinv, skip, st));
+    prof_stop(kProfTrinv, ev, st);
+    ev = prof_start(kProfApply, st);
+    CK(gemm_f64(false, RQLP_F64, src, lds, o.Rinv, l, dst, ldd, rows, l, l, 1.0, 0.0, o.part,
+                nullptr, skip, st));
+    if (R) {
+      if (first) {
+        CK(copy2d(o.Rp, l, l, l, o.Racc, l, skip, st));
+      } else {
+        CK(gemm_f64(false, RQLP_F64, o.Rp, l, o.Racc, l, o.Rtmp, l, l, l, l, 1.0, 0.0, o.part,
+                    nullptr, skip, st));
+        CK(copy2d(o.Rtmp, l, l, l, o.Racc, l, skip, st));
+      }
+    }
+    prof_stop(kProfApply, ev, st);
+    return RQLP_OK;
+  };
+  int r = pass(X, ldx, o.tmp, l, true, nullptr);       // pass 1: X -> tmp
+  if (r != RQLP_OK) return r;
+  r = pass(o.tmp, l, Xq, ldq, false, nullptr);         // pass 2: tmp -> Xq
+  if (r != RQLP_OK) return r;
   // pass 3, only when the device raised the shift flag: Xq -> tmp -> Xq
-  CK(gemm_f64(true, RQLP_F64, Xq, ldq, Xq, ldq, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr, flag,
-              st));
-  CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, flag, st));
-  CK(trinv_upper(o.Rp, l, o.Rinv, flag, st));
-  CK(gemm_f64(false, RQLP_F64, Xq, ldq, o.Rinv, l, o.tmp, l, rows, l, l, 1.0, 0.0, o.part, nullptr,
-              flag, st));
+  r = pass(Xq, ldq, o.tmp, l, false, flag);
+  if (r != RQLP_OK) return r;
   CK(copy2d(o.tmp, rows, l, l, Xq, ldq, flag, st));
-  if (R) {
-    CK(gemm_f64(false, RQLP_F64, o.Rp, l, o.Racc, l, o.Rtmp, l, l, l, l, 1.0, 0.0, o.part, nullptr,
-                flag, st));
-    CK(copy2d(o.Rtmp, l, l, l, o.Racc, l, flag, st));
-    CK(copy2d(o.Racc, l, l, l, R, l, nullptr, st));
-  }
+  if (R) CK(copy2d(o.Racc, l, l, l, R, l, nullptr, st));
   return RQLP_OK;
 }
 
 int orth(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
          const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
-  const int ev = prof_start(kProfOrth, st);
-  const int r = orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, st);
-  prof_stop(kProfOrth, ev, st);
-  return r;
+  return orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, st);
 }
 
 // Everything rqlp() carves from its workspace.

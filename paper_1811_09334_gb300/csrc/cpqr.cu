@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
-  __shared__ double s_tau, s_beta;
+  __shared__ double s_tau, s_beta, s_rv0;
 
   const int G = gridDim.x, b = blockIdx.x, l = P.l;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -163,20 +163,30 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       if (r > s) part = fma(v, v, part);
     }
     const double sigma = block_sum(part, red);  // includes a __syncthreads
-    const double x0 = s_v[0];
-    double tau, beta, v0;
-    if (sigma == 0.0) {
-      if (x0 >= 0.0) { tau = 0.0; beta = x0; v0 = 1.0; }
-      else { tau = 2.0; beta = -x0; v0 = 1.0; }
-    } else {
-      const double alpha = sqrt(fma(x0, x0, sigma));
-      v0 = (x0 <= 0.0) ? (x0 - alpha) : (-sigma / (x0 + alpha));
-      tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
-      beta = alpha;
+    // one thread forms the reflector (FP64 sqrt and divisions are costly here)
+    if (tid == 0) {
+      const double x0 = s_v[0];
+      double tau, beta, rv0;
+      if (sigma == 0.0) {
+        if (x0 >= 0.0) { tau = 0.0; beta = x0; }
+        else { tau = 2.0; beta = -x0; }
+        rv0 = 0.0;
+      } else {
+        const double alpha = sqrt(fma(x0, x0, sigma));
+        const double v0 = (x0 <= 0.0) ? (x0 - alpha) : (-sigma / (x0 + alpha));
+        tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        beta = alpha;
+        rv0 = 1.0 / v0;
+      }
+      s_tau = tau;
+      s_beta = beta;
+      s_rv0 = rv0;
     }
     __syncthreads();
-    for (int r = 1 + tid; r < l - s; r += kThreads) s_v[r] = (sigma == 0.0) ? 0.0 : s_v[r] / v0;
-    if (tid == 0) { s_v[0] = 1.0; s_tau = tau; s_beta = beta; }
+    const double tau = s_tau, beta = s_beta, rv0 = s_rv0;
+    for (int r = 1 + tid; r < l - s; r += kThreads) s_v[r] *= rv0;
+    __syncthreads();
+    if (tid == 0) s_v[0] = 1.0;
     __syncthreads();
     if (b == 0) {
       for (int r = tid; r < l; r += kThreads) P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : s_v[r - s];

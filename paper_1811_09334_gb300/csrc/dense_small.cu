@@ -24,6 +24,7 @@ k_chol_upper(const double *__restrict__ G, int l, double rows, double *__restric
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ int s_fail;
+  __shared__ double s_rjj, s_inv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   double *W = use_smem ? sm : R;
   double tr = 0.0;
@@ -39,14 +40,26 @@ k_chol_upper(const double *__restrict__ G, int l, double rows, double *__restric
     if (tid == 0) s_fail = 0;
     __syncthreads();
     for (int j = 0; j < l; ++j) {
-      const double d = W[(int64_t)j * l + j];
-      const double g0 = G[(int64_t)j * l + j] + shift;
-      if (!isfinite(d) || !isfinite(g0)) { if (tid == 0) s_fail = 2; break; }
-      if (!(d > (double)l * 2.0 * kEps * g0) || !(d > 0.0)) { if (tid == 0) s_fail = 1; break; }
-      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      // FP64 square roots and divisions are costly on this part: one thread
+      // takes them and the CTA reads the result.
+      if (tid == 0) {
+        const double d = W[(int64_t)j * l + j];
+        const double g0 = G[(int64_t)j * l + j] + shift;
+        int f = 0;
+        if (!isfinite(d) || !isfinite(g0)) f = 2;
+        else if (!(d > (double)l * 2.0 * kEps * g0) || !(d > 0.0)) f = 1;
+        s_fail = f;
+        if (!f) {
+          const double rjj = sqrt(d);
+          s_rjj = rjj;
+          s_inv = 1.0 / rjj;
+          W[(int64_t)j * l + j] = rjj;
+        }
+      }
       __syncthreads();
+      if (s_fail) break;
+      const double inv = s_inv;
       for (int c = j + 1 + tid; c < l; c += blockDim.x) W[(int64_t)j * l + c] *= inv;
-      if (tid == 0) W[(int64_t)j * l + j] = rjj;
       __syncthreads();
       for (int a = j + 1 + warp; a < l; a += nw) {
         const double ra = W[(int64_t)j * l + a];
@@ -83,19 +96,22 @@ k_trinv_upper(const double *__restrict__ R, int l, double *__restrict__ Rinv,
               const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   __shared__ double xs[8][kMaxL];
+  __shared__ double dinv[kMaxL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) dinv[i] = 1.0 / R[(int64_t)i * l + i];
+  __syncthreads();
   const int c = blockIdx.x * 8 + warp;
   if (c >= l) return;
   double *x = xs[warp];
   for (int i = lane; i < l; i += 32) x[i] = 0.0;
   __syncwarp();
-  if (lane == 0) x[c] = 1.0 / R[(int64_t)c * l + c];
+  if (lane == 0) x[c] = dinv[c];
   __syncwarp();
   for (int i = c - 1; i >= 0; --i) {
     double s = 0.0;
     for (int t = i + 1 + lane; t <= c; t += 32) s = fma(R[(int64_t)i * l + t], x[t], s);
     s = warp_sum(s);
-    if (lane == 0) x[i] = -s / R[(int64_t)i * l + i];
+    if (lane == 0) x[i] = -s * dinv[i];
     __syncwarp();
   }
   for (int i = lane; i < l; i += 32) Rinv[(int64_t)i * l + c] = x[i];

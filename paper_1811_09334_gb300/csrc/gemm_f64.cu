@@ -14,20 +14,23 @@
 namespace rqk {
 
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BM = 64, BK = 16, NT = 256, kMaxNC = 8;
 
 template <typename TA>
 __device__ __forceinline__ double ld_as_f64(const TA *p) { return static_cast<double>(*p); }
 
 // op(A) is A (M x K, row-major, lda) or, with TRANS_A, A^T where A is K x M.
-// B is K x N row-major (ldb).  With part != nullptr the raw sums of K-slice
-// z go to part + z * part_stride (M x N, ld N); otherwise C = alpha acc + beta C.
-template <bool TRANS_A, typename TA>
+// B is K x N row-major (ldb).  The CTA tile is 64 x (16 NC): NC is picked per
+// call so that the N-tiles cover N with little padding (l = 110 -> NC = 7,
+// one 112-wide tile).  With part != nullptr the raw sums of K-slice z go to
+// part + z * part_stride (M x N, ld N); otherwise C = alpha acc + beta C.
+template <bool TRANS_A, typename TA, int NC>
 __global__ void __launch_bounds__(NT)
 k_gemm_f64(const TA *__restrict__ A, int64_t lda, const double *__restrict__ B, int64_t ldb,
            double *__restrict__ C, int64_t ldc, int64_t M, int64_t N, int64_t K, int64_t kchunk,
            double alpha, double beta, double *__restrict__ part, int64_t part_stride,
            const int *skip_unless) {
+  constexpr int BN = 16 * NC;
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN];
@@ -35,11 +38,11 @@ k_gemm_f64(const TA *__restrict__ A, int64_t lda, const double *__restrict__ B, 
   const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = min(K, kbeg + kchunk);
-  double acc[4][4];
+  double acc[4][NC];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
 
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     if (!TRANS_A) {
@@ -58,23 +61,23 @@ k_gemm_f64(const TA *__restrict__ A, int64_t lda, const double *__restrict__ B, 
       }
     }
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      const int jj = tid & 63, kk = (tid >> 6) + 4 * rr;
+    for (int e = tid; e < BK * BN; e += NT) {
+      const int kk = e / BN, jj = e - kk * BN;
       const int64_t j = j0 + jj, k = k0 + kk;
       Bs[kk][jj] = (j < N && k < kend) ? B[k * ldb + j] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[4], b[NC];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < NC; ++c) b[c] = Bs[kk][tx + 16 * c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < NC; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
   }
@@ -83,7 +86,7 @@ k_gemm_f64(const TA *__restrict__ A, int64_t lda, const double *__restrict__ B, 
     const int64_t i = i0 + ty + 16 * r;
     if (i >= M) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NC; ++c) {
       const int64_t j = j0 + tx + 16 * c;
       if (j >= N) continue;
       if (part) {
@@ -95,6 +98,18 @@ k_gemm_f64(const TA *__restrict__ A, int64_t lda, const double *__restrict__ B, 
       }
     }
   }
+}
+
+// N-tiling: the fewest tiles of at most 128 columns, each 16 NC wide.
+inline void n_tiling(int64_t N, int *nc, int64_t *ntiles) {
+  int64_t t = (N + 16 * kMaxNC - 1) / (16 * kMaxNC);
+  if (t < 1) t = 1;
+  int64_t per = (N + t - 1) / t;
+  int c = (int)((per + 15) / 16);
+  if (c < 1) c = 1;
+  if (c > kMaxNC) c = kMaxNC;
+  *nc = c;
+  *ntiles = (N + 16 * c - 1) / (16 * c);
 }
 
 // C[rowmap(i), j] = alpha * sum_z part[z][i][j] + beta * C[rowmap(i), j]
@@ -130,7 +145,10 @@ int num_sms() {
 }
 
 int64_t gemm_f64_splits(int64_t M, int64_t N, int64_t K) {
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  int nc;
+  int64_t nt;
+  n_tiling(N, &nc, &nt);
+  const int64_t tiles = ((M + BM - 1) / BM) * nt;
   const int64_t target = 3LL * num_sms();
   int64_t s = (target + tiles - 1) / tiles;
   const int64_t kmax = (K + 4 * BK - 1) / (4 * BK);  // keep >= 4 slabs per split
@@ -158,17 +176,33 @@ cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const
   if (kchunk <= 0) kchunk = BK;
   S = (K + kchunk - 1) / kchunk;
   if (S < 1) S = 1;
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)S);
+  int nc;
+  int64_t ntiles;
+  n_tiling(N, &nc, &ntiles);
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)ntiles, (unsigned)S);
   const int64_t pstride = M * N;
   double *p = use_part ? part : nullptr;
-#define LAUNCH(TR, T)                                                                              \
-  k_gemm_f64<TR, T><<<grid, NT, 0, st>>>(reinterpret_cast<const T *>(A), lda, B, ldb, C, ldc, M, \
-                                         N, K, kchunk, alpha, beta, p, pstride, skip_unless)
-  if (a_dtype == RQLP_F32) {
-    if (transA) LAUNCH(true, float); else LAUNCH(false, float);
-  } else {
-    if (transA) LAUNCH(true, double); else LAUNCH(false, double);
+#define LAUNCH_NC(TR, T, NCV)                                                                    \
+  k_gemm_f64<TR, T, NCV><<<grid, NT, 0, st>>>(reinterpret_cast<const T *>(A), lda, B, ldb, C,    \
+                                              ldc, M, N, K, kchunk, alpha, beta, p, pstride,    \
+                                              skip_unless)
+#define LAUNCH(TR, T)                          \
+  switch (nc) {                                \
+    case 1: LAUNCH_NC(TR, T, 1); break;        \
+    case 2: LAUNCH_NC(TR, T, 2); break;        \
+    case 3: LAUNCH_NC(TR, T, 3); break;        \
+    case 4: LAUNCH_NC(TR, T, 4); break;        \
+    case 5: LAUNCH_NC(TR, T, 5); break;        \
+    case 6: LAUNCH_NC(TR, T, 6); break;        \
+    case 7: LAUNCH_NC(TR, T, 7); break;        \
+    default: LAUNCH_NC(TR, T, 8); break;       \
   }
+  if (a_dtype == RQLP_F32) {
+    if (transA) { LAUNCH(true, float); } else { LAUNCH(false, float); }
+  } else {
+    if (transA) { LAUNCH(true, double); } else { LAUNCH(false, double); }
+  }
+#undef LAUNCH_NC
 #undef LAUNCH
   count_launch();
   cudaError_t e = cudaGetLastError();

@@ -15,7 +15,16 @@ int num_sms();
 // kernel classes (see prof.cu).
 void count_launch(int n = 1);
 long long launch_count();
-enum ProfClass { kProfProducts = 0, kProfCpqr = 1, kProfOrth = 2, kProfSmall = 3, kProfClasses = 4 };
+enum ProfClass {
+  kProfProducts = 0,  // products with A (sketch, power steps, projection)
+  kProfCpqr = 1,      // column-pivoted QR of B
+  kProfGram = 2,      // CholeskyQR: Gram matrices X^T X
+  kProfChol = 3,      // CholeskyQR: Cholesky factors
+  kProfTrinv = 4,     // CholeskyQR: triangular inverses
+  kProfApply = 5,     // CholeskyQR: X R^{-1} and R products
+  kProfSmall = 6,     // explicit Q0 from the reflectors
+  kProfClasses = 7
+};
 int prof_start(int cls, cudaStream_t st);
 void prof_stop(int cls, int idx, cudaStream_t st);
 

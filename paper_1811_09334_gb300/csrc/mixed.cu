@@ -1,25 +1,546 @@
-// Mixed-precision products (placeholder until the tcgen05 kernels land).
+// Mixed-precision products with A on the 5th-generation tensor cores.
+//
+// The sketch Y = A W, the power-step product Z = A^T V and the projection
+// B^T = A^T V (Algorithm 2.1 steps 2 and 4) are the only O(m n l) work of
+// the method.  In the BF16x3 form A and the skinny operand are split into
+// BF16 pairs, A = Ah + Al and W = Wh + Wl, and three products
+// Ah Wh + Ah Wl + Al Wh are accumulated in FP32 (the dropped Al Wl term is
+// about 2^-16 of the result); the BF16 form keeps Ah Wh only.
+//
+// Both products are computed as C[M x N] = X[M x K] Y[N x K]^T with X and Y
+// K-major BF16: X = A (M = m, K = n) for the sketch and X = A^T (M = n,
+// K = m) for the projection, so A is split once per factorization into
+// row- and column-major BF16 copies (a1, one HBM pass).  One CTA owns a
+// 128-row tile of C and a slice of K:
+//   warp 0 lane 0  TMA producer: 128B-swizzled 128 x 64 tiles of Xh, Xl and
+//                  N x 64 tiles of Yh, Yl into a ring of shared-memory stages;
+//   warp 1 lane 0  MMA issuer: tcgen05.mma kind::f16, M = 128, N = l padded
+//                  to 16, K = 16, FP32 accumulator in TMEM; tcgen05.commit
+//                  releases each stage;
+//   warps 0-3      epilogue: tcgen05.ld of the accumulator, FP32 partial
+//                  sums to global memory (split-K slices are summed in FP64
+//                  by a second kernel).
+// Every mbarrier wait is bounded; a wait that gives up records
+// RQLP_ERR_TIMEOUT, waits (bounded) for its own copies in flight, frees the
+// TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "mixed.cuh"
 
 namespace rqk {
 
-void carve_mixed(Arena &, int64_t, int64_t, int, int, MixedBufs &mx) {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kTileK = 64;                // 64 BF16 = one 128-byte swizzle row
+constexpr uint32_t kXBytes = kTileM * kTileK * 2;
+constexpr int kMaxStages = 4;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// K-major operand tile, 128-byte swizzle: 8-row atoms of 1024 bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct MmaArgs {
+  int M;           // rows of C (rows of X)
+  int n_pad;       // MMA N (multiple of 16)
+  int ncols;       // columns of C that are stored (l)
+  int nk;          // K blocks in total
+  int kb_per;      // K blocks per split
+  int stages;
+  uint32_t tmem_cols;
+  float *part;     // [split][M][ldp]
+  int64_t split_stride;
+  int ldp;
+  Ctrl *ctrl;
+  unsigned long long limit_ns;
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(128, 1)
+k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
+           const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
+           const MmaArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_acc;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t ybytes = (uint32_t)a.n_pad * kTileK * 2;
+  const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (kXBytes + ybytes);
+  const int m_tile = blockIdx.x, split = blockIdx.y;
+  const int kb0 = split * a.kb_per;
+  const int nkb = min(a.kb_per, a.nk - kb0);
+
+  if (tid == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, a.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int issued = 0;
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % a.stages;
+        const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
+        if (!mbar_wait(&bar_empty[s], ph ^ 1u, a.limit_ns) || *(volatile int *)&s_abort) {
+          s_abort = 1;
+          break;
+        }
+        const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+        mbar_expect_tx(&bar_full[s], stage_bytes);
+        const int kx = (kb0 + i) * kTileK, my = m_tile * kTileM;
+        tma_load_2d(st, &tXh, kx, my, &bar_full[s]);
+        tma_load_2d(st + kXBytes, &tYh, kx, 0, &bar_full[s]);
+        if (SPLIT) {
+          tma_load_2d(st + kXBytes + ybytes, &tXl, kx, my, &bar_full[s]);
+          tma_load_2d(st + 2 * kXBytes + ybytes, &tYl, kx, 0, &bar_full[s]);
+        }
+        issued = i + 1;
+      }
+      // never leave with copies in flight: wait for the last load of each stage
+      for (int s = 0; s < a.stages && s < issued; ++s) {
+        const int last = ((issued - 1 - s) / a.stages) * a.stages + s;
+        mbar_wait(&bar_full[s], (uint32_t)(last / a.stages) & 1u, a.limit_ns);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = instr_desc(kTileM, a.n_pad);
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % a.stages;
+        const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
+        if (!mbar_wait(&bar_full[s], ph, a.limit_ns) || *(volatile int *)&s_abort) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t xh = smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t yh = xh + kXBytes;
+        const uint32_t xl = yh + ybytes;
+        const uint32_t yl = xl + kXBytes;
+#pragma unroll
+        for (int k = 0; k < kTileK / 16; ++k) {
+          const uint32_t off = k * 32;  // 16 BF16 along K inside the swizzled row
+          mma_bf16(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+          if (SPLIT) {
+            mma_bf16(tmem, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
+            mma_bf16(tmem, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
+          }
+        }
+        mma_commit(&bar_empty[s]);
+      }
+      // arrives once every MMA issued above has completed (also on the abort path)
+      mma_commit(&bar_acc);
+    }
+    __syncwarp();
+  }
+
+  // ---- epilogue: TMEM -> FP32 partial sums ----
+  const bool ready = mbar_wait(&bar_acc, 0, a.limit_ns);
+  tc_fence_after();
+  __syncthreads();
+  if (!ready || *(volatile int *)&s_abort) {
+    if (tid == 0) set_status(a.ctrl, RQLP_ERR_TIMEOUT);
+  } else {
+    const int row = m_tile * kTileM + warp * 32 + lane;
+    float *out = a.part + (int64_t)split * a.split_stride + (int64_t)row * a.ldp;
+    for (int c0 = 0; c0 < a.n_pad; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (row < a.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < a.ncols) out[c0 + j] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// C (M x ncols, FP64, ldc) = sum of S FP32 partial slices.
+__global__ void k_sum_parts_f32(const float *__restrict__ part, int S, int64_t split_stride,
+                                int64_t M, int ncols, int ldp, double *__restrict__ C,
+                                int64_t ldc) {
+  const int64_t total = M * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols;
+    const int j = (int)(e - i * ncols);
+    double s = 0.0;
+    for (int z = 0; z < S; ++z) s += (double)part[(int64_t)z * split_stride + i * ldp + j];
+    C[i * ldc + j] = s;
+  }
+}
+
+// A (m x n, lda) -> Ah, Al (m x ld1) and A^T halves Ath, Atl (n x ld2), BF16.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloat16 *Ah,
+          __nv_bfloat16 *Al, int64_t ld1, __nv_bfloat16 *Ath, __nv_bfloat16 *Atl, int64_t ld2,
+          int with_lo) {
+  __shared__ __nv_bfloat16 th[32][34];
+  __shared__ __nv_bfloat16 tl[32][34];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t i = i0 + k, j = j0 + tx;
+    if (i < m && j < n) {
+      const double v = (double)A[i * lda + j];
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(h));
+      Ah[i * ld1 + j] = h;
+      if (with_lo) Al[i * ld1 + j] = lo;
+      th[k][tx] = h;
+      tl[k][tx] = lo;
+    }
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t j = j0 + k, i = i0 + tx;
+    if (i < m && j < n) {
+      Ath[j * ld2 + i] = th[tx][k];
+      if (with_lo) Atl[j * ld2 + i] = tl[tx][k];
+    }
+  }
+}
+
+// S (K x l, FP64, lds) -> S^T halves (l x ldk, BF16)
+__global__ void k_split_skinny_t(const double *__restrict__ S, int64_t K, int l, int64_t lds,
+                                 __nv_bfloat16 *Sh, __nv_bfloat16 *Sl, int64_t ldk, int with_lo) {
+  const int64_t total = (int64_t)l * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / K);
+    const int64_t k = e - (int64_t)c * K;
+    const double v = S[k * lds + c];
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    Sh[(int64_t)c * ldk + k] = h;
+    if (with_lo) Sl[(int64_t)c * ldk + k] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: `rows` x `cols` (cols contiguous, ld elements per
+// row), box of box_rows x 64 with the 128-byte swizzle.
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld,
+              int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct GemmPlan {
+  int n_pad, stages, S, kb_per, nk;
+  uint32_t tmem_cols;
+  size_t smem;
+};
+
+GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split) {
+  GemmPlan g;
+  g.n_pad = (int)round_up(l, 16);
+  const size_t ybytes = (size_t)g.n_pad * kTileK * 2;
+  const size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
+  g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
+  g.smem = g.stages * stage + 1024;
+  g.nk = (int)((K + kTileK - 1) / kTileK);
+  const int64_t tiles = (M + kTileM - 1) / kTileM;
+  int S = (int)std::max<int64_t>(1, num_sms() / tiles);
+  S = std::min(S, std::max(1, g.nk / 4));
+  g.kb_per = (g.nk + S - 1) / S;
+  g.S = (g.nk + g.kb_per - 1) / g.kb_per;
+  g.tmem_cols = g.n_pad <= 32 ? 32 : g.n_pad <= 64 ? 64 : g.n_pad <= 128 ? 128 : 256;
+  return g;
+}
+
+// C (M x l, FP64, ld l) = X Y^T with X (M x K) and Y (l x K) given as BF16
+// pairs with leading dimensions ldx / ldy.
+int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const void *Xh,
+             const void *Xl, int64_t ldx, const void *Yh, const void *Yl, int64_t ldy, double *C,
+             Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  GemmPlan g = plan_gemm(M, K, l, split);
+  if (g.stages < 2) return RQLP_ERR_UNSUPPORTED;
+  if ((int64_t)g.S * M * g.n_pad > mx.part_floats) return RQLP_ERR_WORKSPACE;
+  CUtensorMap mXh, mXl, mYh, mYl;
+  if (!make_map(&mXh, Xh, M, K, ldx, kTileM) || !make_map(&mYh, Yh, l, K, ldy, g.n_pad))
+    return RQLP_ERR_CUDA;
+  if (split) {
+    if (!make_map(&mXl, Xl, M, K, ldx, kTileM) || !make_map(&mYl, Yl, l, K, ldy, g.n_pad))
+      return RQLP_ERR_CUDA;
+  } else {
+    mXl = mXh;
+    mYl = mYh;
+  }
+  MmaArgs a;
+  a.M = (int)M;
+  a.n_pad = g.n_pad;
+  a.ncols = l;
+  a.nk = g.nk;
+  a.kb_per = g.kb_per;
+  a.stages = g.stages;
+  a.tmem_cols = g.tmem_cols;
+  a.part = mx.part;
+  a.ldp = g.n_pad;
+  a.split_stride = M * g.n_pad;
+  a.ctrl = ctrl;
+  a.limit_ns = spin_ns > 0 ? (unsigned long long)spin_ns : kDefaultSpinNs;
+  dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)g.S);
+  if (split) {
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_mma_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSmemLimit - 1024)) != cudaSuccess)
+        return RQLP_ERR_CUDA;
+      attr = true;
+    }
+    k_mma_bf16<true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_mma_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSmemLimit - 1024)) != cudaSuccess)
+        return RQLP_ERR_CUDA;
+      attr = true;
+    }
+    k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  }
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return RQLP_ERR_CUDA;
+  const int64_t total = M * l;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4LL * num_sms());
+  k_sum_parts_f32<<<blocks, 256, 0, st>>>(mx.part, g.S, a.split_stride, M, l, a.ldp, C, l);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+int split_skinny(const MixedBufs &mx, bool split, const double *S, int64_t K, int l, int64_t lds,
+                 int64_t ldk, cudaStream_t st) {
+  const int64_t total = (int64_t)l * K;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4LL * num_sms());
+  k_split_skinny_t<<<blocks, 256, 0, st>>>(S, K, l, lds, static_cast<__nv_bfloat16 *>(mx.Whi),
+                                           static_cast<__nv_bfloat16 *>(mx.Wlo), ldk,
+                                           split ? 1 : 0);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+}  // namespace
+
+void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx) {
   mx = MixedBufs{};
+  if (prec == RQLP_PREC_FP64) return;
+  const bool split = prec == RQLP_PREC_BF16X3;
+  mx.m = m;
+  mx.n = n;
+  mx.l = l;
+  const int64_t ld1 = round_up(n, 8), ld2 = round_up(m, 8);
+  mx.Ahi = a.take<__nv_bfloat16>((size_t)m * ld1);
+  mx.Alo = split ? a.take<__nv_bfloat16>((size_t)m * ld1) : nullptr;
+  mx.Athi = a.take<__nv_bfloat16>((size_t)n * ld2);
+  mx.Atlo = split ? a.take<__nv_bfloat16>((size_t)n * ld2) : nullptr;
+  const int64_t ldk = round_up(std::max(m, n), 8);
+  mx.Whi = a.take<__nv_bfloat16>((size_t)l * ldk);
+  mx.Wlo = split ? a.take<__nv_bfloat16>((size_t)l * ldk) : nullptr;
+  int64_t pf = 0;
+  for (int64_t M : {m, n}) {
+    const int64_t K = (M == m) ? n : m;
+    GemmPlan g = plan_gemm(M, K, l, split);
+    pf = std::max<int64_t>(pf, (int64_t)g.S * M * g.n_pad);
+  }
+  mx.part_floats = pf;
+  mx.part = a.take<float>((size_t)pf);
 }
 
-int mixed_prepare_A(const MixedBufs &, int, const void *, int, int64_t, int64_t, int64_t,
-                    cudaStream_t) {
-  return RQLP_ERR_UNSUPPORTED;
+int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, int64_t m,
+                    int64_t n, int64_t lda, cudaStream_t st) {
+  if (!mx.Ahi) return RQLP_ERR_WORKSPACE;
+  const bool split = prec == RQLP_PREC_BF16X3;
+  const int64_t ld1 = round_up(n, 8), ld2 = round_up(m, 8);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+  auto *Ah = static_cast<__nv_bfloat16 *>(mx.Ahi);
+  auto *Al = static_cast<__nv_bfloat16 *>(mx.Alo);
+  auto *Ath = static_cast<__nv_bfloat16 *>(mx.Athi);
+  auto *Atl = static_cast<__nv_bfloat16 *>(mx.Atlo);
+  if (a_dtype == RQLP_F32)
+    k_split_a<float><<<grid, dim3(32, 8), 0, st>>>(static_cast<const float *>(A), m, n, lda, Ah, Al,
+                                                    ld1, Ath, Atl, ld2, split ? 1 : 0);
+  else
+    k_split_a<double><<<grid, dim3(32, 8), 0, st>>>(static_cast<const double *>(A), m, n, lda, Ah,
+                                                     Al, ld1, Ath, Atl, ld2, split ? 1 : 0);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
-int mixed_nn(const MixedBufs &, int, int64_t, int64_t, const double *, int64_t, int, double *,
-             Ctrl *, int64_t, cudaStream_t) {
-  return RQLP_ERR_UNSUPPORTED;
+int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *W, int64_t ldw,
+             int l, double *Y, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  const bool split = prec == RQLP_PREC_BF16X3;
+  const int64_t ldk = round_up(n, 8);
+  int r = split_skinny(mx, split, W, n, l, ldw, ldk, st);
+  if (r != RQLP_OK) return r;
+  return gemm_xyt(mx, split, m, n, l, mx.Ahi, mx.Alo, round_up(n, 8), mx.Whi, mx.Wlo, ldk, Y, ctrl,
+                  spin_ns, st);
 }
 
-int mixed_tn(const MixedBufs &, int, int64_t, int64_t, const double *, int64_t, int, double *,
-             Ctrl *, int64_t, cudaStream_t) {
-  return RQLP_ERR_UNSUPPORTED;
+int mixed_tn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *V, int64_t ldv,
+             int l, double *Z, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  const bool split = prec == RQLP_PREC_BF16X3;
+  const int64_t ldk = round_up(m, 8);
+  int r = split_skinny(mx, split, V, m, l, ldv, ldk, st);
+  if (r != RQLP_OK) return r;
+  return gemm_xyt(mx, split, n, m, l, mx.Athi, mx.Atlo, round_up(m, 8), mx.Whi, mx.Wlo, ldk, Z,
+                  ctrl, spin_ns, st);
 }
 
 }  // namespace rqk

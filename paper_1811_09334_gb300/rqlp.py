@@ -65,7 +65,8 @@ _SIGS = {
     "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
 }
 
-PROFILE_CLASSES = ("products_with_A", "cpqr_of_B", "cholesky_qr", "explicit_Q0")
+PROFILE_CLASSES = ("products_with_A", "cpqr_of_B", "cholqr_gram", "cholqr_cholesky",
+                   "cholqr_trinv", "cholqr_apply", "explicit_Q0")
 
 
 def launch_count() -> int:

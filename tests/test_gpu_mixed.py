@@ -1,0 +1,83 @@
+"""Mixed-precision (tcgen05 BF16 tensor-core) products and factorizations.
+
+Tolerances, derived from the arithmetic: BF16 keeps 8 significant bits
+(unit roundoff u = 2^-8); the BF16x3 split represents A and W to about u^2
+and drops only the Al Wl term (about u^2 |A| |W|), and the FP32 accumulation
+over K <= 16384 adds about 1e-6; so the normwise relative error of a BF16x3
+product is held to 1e-4 and that of a plain BF16 product to 2e-2.  For whole
+factorizations the L-values are compared with the FP64 oracle on the same
+Omega at 1e-3 relative for sigma_j / sigma_1 >= 1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import rqlp_ref as O
+from paper_1811_09334_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1811_09334_gb300 import rqlp
+    rqlp.lib()
+    return rqlp
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _normrel(a, b):
+    a = a.cpu().numpy()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("m,n,l", [(256, 192, 16), (1000, 700, 30), (2048, 1536, 110),
+                                   (333, 257, 17), (130, 4100, 200), (8192, 8192, 110)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("bf16", 2e-2)])
+def test_mixed_products(R, m, n, l, prec, tol):
+    rng = np.random.default_rng(m * 3 + n + l)
+    A = rng.standard_normal((m, n))
+    Om = rng.standard_normal((n, l))
+    V = rng.standard_normal((m, l))
+    Y = R.sketch(_t(A), _t(Om), prec=prec)
+    Z = R.project(_t(A), _t(V), prec=prec)
+    assert _normrel(Y, O.sketch(A, Om)) <= tol
+    assert _normrel(Z, O.adjoint_product(A, V)) <= tol
+
+
+def test_mixed_product_fp32_input(R):
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((1500, 900)).astype(np.float32)
+    Om = rng.standard_normal((900, 40))
+    Y = R.sketch(_t(A), _t(Om), prec="bf16x3")
+    assert _normrel(Y, O.sketch(A.astype(np.float64), Om)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("q,d,pivot2", [(1, 2, False), (0, 1, True), (2, 1, False)])
+def test_mixed_factorization_lvalues(R, prec, q, d, pivot2):
+    pr = W.c2(m=2048, n=1536, k=60, p=10, q=q, d=d)
+    Om = W.omega(pr.n, pr.l, 0)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=q, d=d, pivot2=pivot2, prec=prec)
+    ref = O.rqlp(pr.A, pr.k, pr.p, Om, q=q, d=d, pivot2=pivot2)
+    lv = out["Lvalues"].cpu().numpy()
+    keep = ref["Lvalues"] >= 1e-3 * ref["Lvalues"].max()
+    if prec == "bf16x3":
+        # pivots agree with the FP64 oracle, so L-values compare index by index
+        assert np.array_equal(out["piv0"].cpu().numpy()[:pr.l], ref["piv0"][:pr.l])
+        rel = np.abs(lv - ref["Lvalues"])[keep] / ref["Lvalues"][keep]
+        assert rel.max() <= 1e-3, rel.max()
+    else:
+        # a 2^-8 perturbation may reorder near-equal pivots; compare what does
+        # not depend on them: the singular values of L (= those of B)
+        sg = np.linalg.svd(out["L"].cpu().numpy(), compute_uv=False)
+        so = np.linalg.svd(ref["L"], compute_uv=False)
+        keep = so >= 1e-3 * so[0]
+        assert (np.abs(sg - so)[keep] / so[keep]).max() <= 2e-2
+    Q = out["Q"].cpu().numpy()
+    assert np.abs(Q.T @ Q - np.eye(pr.l)).max() <= 1e-12
