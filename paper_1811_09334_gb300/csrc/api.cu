@@ -208,15 +208,18 @@ int prod_tn(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64
     if (r_ != RQLP_OK) return r_; \
   } while (0)
 
-// The pivoted QLP of the small l x n matrix B, given as Bt = B^T (n x l),
-// followed by the assembly of Q and P (Algorithm 2.1 steps 5-7, Algorithm
-// 2.2 steps 5-9).  V is the m x l range basis.
-int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int l, const double *Vb,
-              const double *Bt, double *Q, double *L, double *Pout, double *Lvalues,
+// The pivoted QLP of the small w x n matrix B, given as Bt = B^T (n x w,
+// ld w), followed by the assembly of Q and P (Algorithm 2.1 steps 5-7,
+// Algorithm 2.2 steps 5-9).  Vb is the m x w range basis (ld ldv); Q (m x w),
+// L (w x w) and P (n x w) are written with leading dimension ldo; piv1 gets w
+// entries.
+int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, const double *Vb,
+              int64_t ldv, const double *Bt, double *Q, double *L, double *Pout, int64_t ldo,
               int32_t *piv0, int32_t *piv1, int site0, cudaStream_t st) {
   Ctrl *ctrl = P.ctrl;
   const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
   const unsigned extra = (o.debug_flags & 1) ? 1u : 0u;
+  const int l = w;
   int ev = prof_start(kProfCpqr, st);
   CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st));
   prof_stop(kProfCpqr, ev, st);
@@ -226,10 +229,11 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int l, co
   if (o.pivot2) {
     RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st));
     CK(transpose(P.Racc, l, l, l, P.Rt, l, st));
-    CK(cpqr_wide(P.Rt, l, l, l, L, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
+    CK(cpqr_wide(P.Rt, l, l, l, P.Tl, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
+    CK(copy2d(P.Tl, l, l, l, L, ldo, nullptr, st));
     CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st));
     CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
-    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, l, n, l, l, 1.0, 0.0, P.ob.part, piv0,
+    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
                 nullptr, st));
   } else {
     RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st));
@@ -246,14 +250,56 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int l, co
     CK(gemm_f64(false, RQLP_F64, P.Q0, l, P.QB, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
                 nullptr, st));
     CK(copy2d(P.sm1, l, l, l, P.QB, l, nullptr, st));
-    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, l, n, l, l, 1.0, 0.0, P.ob.part, piv0,
+    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
                 nullptr, st));
-    if (o.d % 2 == 1) CK(transpose(P.Rprev, l, l, l, L, l, st));
-    else CK(copy2d(P.Rprev, l, l, l, L, l, nullptr, st));
+    if (o.d % 2 == 1) CK(transpose(P.Rprev, l, l, l, L, ldo, st));
+    else CK(copy2d(P.Rprev, l, l, l, L, ldo, nullptr, st));
+    CK(iota(piv1, l, st));
   }
-  CK(gemm_f64(false, RQLP_F64, Vb, l, P.QB, l, Q, l, m, l, l, 1.0, 0.0, P.ob.part, nullptr, nullptr,
-              st));
-  if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
+  CK(gemm_f64(false, RQLP_F64, Vb, ldv, P.QB, l, Q, ldo, m, l, l, 1.0, 0.0, P.ob.part, nullptr,
+              nullptr, st));
+  return RQLP_OK;
+}
+
+__global__ void k_zero(double *p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0.0;
+}
+
+// Block randomized QLP (Algorithm 4.1).  Per block j of b columns:
+// Y_j = A Omega_j; V_j = qr(Y_j); V_j = qr(V_j - V_<j (V_<j^T V_j));
+// B_j^T = A^T V_j; the pivoted QLP of B_j; Q_j = V_j Q_B(j), P_j = P_B(j),
+// L = blkdiag(L_j).  The deflation A(j) = A(j-1) - V_j B_j is not formed:
+// B_j = V_j^T A(j-1) = V_j^T A because V_j is orthogonal to V_<j (Section 4),
+// which saves one pass over A per block.
+int run_brqlp(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64_t m, int64_t n,
+              int64_t lda, int l, const double *Omega, int64_t ldo, double *Q, double *L,
+              double *Pout, int32_t *piv0, int32_t *piv1, cudaStream_t st) {
+  const int b = o.block_b, h = l / b;
+  k_zero<<<(int)std::min<int64_t>(((int64_t)l * l + 255) / 256, 1024), 256, 0, st>>>(L, (int64_t)l * l);
+  count_launch();
+  CK(cudaGetLastError());
+  int site = 0;
+  for (int j = 0; j < h; ++j) {
+    double *Vj = P.V + (size_t)j * b;  // column block of V (m x l, ld l)
+    RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega + (size_t)j * b, ldo, b, P.Y, st));
+    RET(orth(P.Y, m, b, b, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
+    if (j > 0) {
+      const int jb = j * b;
+      // C = V_<j^T V_j (jb x b), then V_j -= V_<j C
+      CK(gemm_f64(true, RQLP_F64, P.V, l, Vj, l, P.sm1, b, jb, b, m, 1.0, 0.0, P.ob.part, nullptr,
+                  nullptr, st));
+      CK(gemm_f64(false, RQLP_F64, P.V, l, P.sm1, b, Vj, l, m, b, jb, -1.0, 1.0, P.ob.part,
+                  nullptr, nullptr, st));
+      RET(orth(Vj, m, b, l, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
+    }
+    RET(prod_tn(P, o, A, a_dtype, m, n, lda, Vj, l, b, P.Z, st));
+    int32_t *p0 = (j == 0) ? piv0 : P.piv0;
+    RET(qlp_stage(P, o, m, n, b, Vj, l, P.Z, Q + (size_t)j * b, L + (size_t)j * b * l + j * b,
+                  Pout + (size_t)j * b, l, p0, piv1 + (size_t)j * b, site, st));
+    site += o.d + 1;
+  }
   return RQLP_OK;
 }
 
@@ -269,7 +315,11 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   int32_t *pv1 = piv1 ? piv1 : P.piv1;
   if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
   int site = 0;
-  if (o.block_b > 0) return RQLP_ERR_UNSUPPORTED;
+  if (o.block_b > 0) {
+    RET(run_brqlp(P, o, A, a_dtype, m, n, lda, l, Omega, ldo, Q, L, Pout, pv0, pv1, st));
+    if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
+    return RQLP_OK;
+  }
   // range finder (Section 2) with q power steps
   RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega, ldo, l, P.Y, st));
   for (int i = 0; i < o.q; ++i) {
@@ -281,8 +331,8 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st));
   // B^T = A^T V  (Algorithm 2.1 step 4)
   RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
-  RET(qlp_stage(P, o, m, n, l, P.V, P.Z, Q, L, Pout, Lvalues, pv0, pv1, site, st));
-  if (!o.pivot2) CK(iota(pv1, l, st));
+  RET(qlp_stage(P, o, m, n, l, P.V, l, P.Z, Q, L, Pout, l, pv0, pv1, site, st));
+  if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
   return RQLP_OK;
 }
 
@@ -323,6 +373,7 @@ int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int3
   const int l = k + p;
   if (lda < n || ldo < l) return RQLP_ERR_INVALID_ARG;
   if (opts->block_b > 0 && (l % opts->block_b != 0)) return RQLP_ERR_INVALID_ARG;
+  if (opts->block_b > 0 && opts->q > 0) return RQLP_ERR_UNSUPPORTED;  // Algorithm 4.1 has no power steps
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
   return run_rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, *opts, Q, L, P, Lvalues, piv0, piv1, ws,
                   ws_bytes, reinterpret_cast<cudaStream_t>(stream));

@@ -268,7 +268,8 @@ struct Plan {
 Plan plan_for(int64_t n, int l) {
   Plan p;
   const int sms = num_sms();
-  int G = (int)std::min<int64_t>(n, (int64_t)sms);
+  const int cap = tuning().cpqr_max_ctas;
+  int G = (int)std::min<int64_t>(n, (int64_t)((cap > 0 && cap < sms) ? cap : sms));
   if (G < 1) G = 1;
   int cpb = (int)((n + G - 1) / G);
   G = (int)((n + cpb - 1) / cpb);
@@ -336,6 +337,12 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   // the permutation stays valid even if the kernel stops early on an error
   e = iota(piv, n, st);
   if (e != cudaSuccess) return e;
+  if (pl.G == 1) {
+    // one CTA: its grid barrier never waits, no co-residency is needed
+    k_cpqr_wide<<<1, kThreads, pl.smem, st>>>(P);
+    count_launch();
+    return cudaGetLastError();
+  }
   void *args[] = {&P};
   e = cudaLaunchCooperativeKernel((const void *)k_cpqr_wide, dim3(pl.G), dim3(kThreads), args,
                                   pl.smem, st);

@@ -149,7 +149,8 @@ int64_t gemm_f64_splits(int64_t M, int64_t N, int64_t K) {
   int64_t nt;
   n_tiling(N, &nc, &nt);
   const int64_t tiles = ((M + BM - 1) / BM) * nt;
-  const int64_t target = 3LL * num_sms();
+  const int tt = tuning().gemm_target_ctas;
+  const int64_t target = (tt > 0 && tt < 3 * num_sms()) ? tt : 3LL * num_sms();
   int64_t s = (target + tiles - 1) / tiles;
   const int64_t kmax = (K + 4 * BK - 1) / (4 * BK);  // keep >= 4 slabs per split
   if (s > kmax) s = kmax;

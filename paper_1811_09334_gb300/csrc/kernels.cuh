@@ -11,6 +11,17 @@ namespace rqk {
 
 int num_sms();
 
+// Launch-shape knobs.  The defaults fill the whole GPU with one problem; the
+// batched driver lowers them so that many problems run side by side (the
+// autotuner picks its values).  Workspace sizes are computed with the
+// defaults, which are upper bounds of every tuned value.
+struct Tuning {
+  int gemm_target_ctas;  // FP64 GEMM: split K until about this many CTAs (0: 3 x SMs)
+  int cpqr_max_ctas;     // CPQR of B: at most this many CTAs (0: one per SM; 1: no grid barrier)
+  int mma_max_splits;    // tcgen05 products: at most this many K splits (0: fill the SMs)
+};
+Tuning &tuning();
+
 // Launch counter (every launcher adds its launches) and event timing of
 // kernel classes (see prof.cu).
 void count_launch(int n = 1);

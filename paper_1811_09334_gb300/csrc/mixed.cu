@@ -399,6 +399,7 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split) {
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   int S = (int)std::max<int64_t>(1, num_sms() / tiles);
   S = std::min(S, std::max(1, g.nk / 4));
+  if (tuning().mma_max_splits > 0) S = std::min(S, tuning().mma_max_splits);
   g.kb_per = (g.nk + S - 1) / S;
   g.S = (g.nk + g.kb_per - 1) / g.kb_per;
   g.tmem_cols = g.n_pad <= 32 ? 32 : g.n_pad <= 64 ? 64 : g.n_pad <= 128 ? 128 : 256;

@@ -23,6 +23,11 @@ std::vector<Pair> g_pool[kProfClasses];
 size_t g_used[kProfClasses] = {};
 }  // namespace
 
+Tuning &tuning() {
+  static thread_local Tuning t = {0, 0, 0};
+  return t;
+}
+
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 

@@ -199,3 +199,35 @@ def test_c2_full_size_fp64_parity(R):
     out = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False)
     ref = O.rqlp(pr.A.cpu().numpy(), pr.k, pr.p, Om, q=1, d=2, pivot2=False)
     _compare(out, ref, pr.l)
+
+
+# ------------------------------------------------------------------ BRQLP
+@pytest.mark.parametrize("b,pivot2,d", [(10, True, 1), (6, True, 1), (15, False, 2), (30, True, 1),
+                                        (5, False, 1)])
+def test_brqlp_parity(R, b, pivot2, d):
+    """Algorithm 4.1 on the 2000 x 1000 workload (l = 30) against the oracle,
+    which forms the deflated A(j) literally."""
+    pr = W.c1()
+    Om = W.omega(pr.n, pr.l, 5)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), pivot2=pivot2, d=d, block_b=b)
+    ref = O.brqlp(pr.A, pr.k, pr.p, b, Om, pivot2=pivot2, d=d)
+    Lg = out["L"].cpu().numpy()
+    assert _relmax(Lg, ref["L"]) <= 1e-10
+    lv = out["Lvalues"].cpu().numpy()
+    assert np.max(np.abs(lv - ref["Lvalues"]) / np.abs(ref["Lvalues"])) <= 1e-10
+    assert _relmax(out["Q"], ref["Q"]) <= 1e-9
+    assert _relmax(out["P"], ref["P"]) <= 1e-9
+    # A - Q L P^T = A - V B (eq. 4.5): the residual identity of eq. 2.1
+    Q, P = out["Q"].cpu().numpy(), out["P"].cpu().numpy()
+    E = pr.A - Q @ Lg @ P.T
+    Bn = np.linalg.norm(Q.T @ pr.A)
+    assert abs(np.linalg.norm(E) ** 2 - (np.linalg.norm(pr.A) ** 2 - Bn ** 2)) <= 1e-12
+
+
+def test_brqlp_large_blocks_bf16x3(R):
+    pr = W.c2(m=4096, n=3000, k=90, p=10)
+    Om = W.omega(pr.n, pr.l, 6)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), pivot2=True, block_b=20, prec="bf16x3")
+    ref = O.brqlp(pr.A, pr.k, pr.p, 20, Om, pivot2=True)
+    lv = out["Lvalues"].cpu().numpy()
+    assert np.max(np.abs(lv - ref["Lvalues"]) / ref["Lvalues"]) <= 1e-3
