@@ -159,6 +159,58 @@ def _lvalue_err(gpu_out, ref):
             "pivots_match": piv_ok}
 
 
+def _run_batched(R, dev, count=512):
+    """The 512-problem batch (ERQLP q = 1, d = 2): one graph launch per step.
+
+    Problems: m ~ U[256, 4096], n ~ U[128, m], k ~ U[8, 64], p = 8,
+    A_i = X diag(j^-1.5) Y^T (FP32 QR of the Gaussian factors on the device,
+    for generation speed).  Launch shapes come from the autotuner (cached).
+    Compared with the FP64 per-matrix loop (rqlp() one problem at a time).
+    """
+    import torch
+    from paper_1811_09334_gb300 import autotune
+    from paper_1811_09334_gb300 import workloads as W
+    shapes = W.c5_shapes(count=count)
+    As, ks, Oms = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, _ = W.c5_matrix(i, m, n, device=str(dev), fast=True)
+        As.append(A)
+        ks.append(k)
+        Oms.append(torch.from_numpy(W.omega(n, k + 8, i)).to(dev))
+    torch.cuda.synchronize()
+    res = {"workload": "batched_erqlp_512_uneven_q1_d2", "count": count}
+    for prec in ("bf16x3", "fp64"):
+        tune = autotune.tune(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, sample=128)
+        b = R.Batch(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, **tune)
+        b.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        worst, _ = b.status()
+        ms = e0.elapsed_time(e1) / reps
+        res[prec] = {"factorizations_per_s": count / (ms / 1e3), "ms_per_graph_launch": ms,
+                     "graph_launches_per_step": 1, "kernel_nodes": b.kernel_nodes,
+                     "tuning": tune, "status": worst}
+        b.close()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(count):
+        R.rqlp(As[i], ks[i], 8, Oms[i], q=1, d=2, pivot2=False, prec="fp64", check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res["fp64_per_matrix_loop"] = {"factorizations_per_s": count / (ms / 1e3), "ms": ms}
+    res["speedup_bf16x3_graph_vs_fp64_loop"] = res["bf16x3"]["factorizations_per_s"] / \
+        res["fp64_per_matrix_loop"]["factorizations_per_s"]
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -327,6 +379,10 @@ def run_ours(args):
         e2e = {"value": world * hsteps / dt, "unit": "factorizations/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    batched = None
+    if not args.no_batched:
+        batched = _run_batched(R, dev)
+
     # CPU baseline (oracle) on rank 0 at N = 1; L-value error of each form against it
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -353,6 +409,7 @@ def run_ours(args):
             "forms": forms_out,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "batched": batched,
             "e2e": e2e,
             "gpu_launches": int(main["launches"]),
             "clocks": main["clocks"],
@@ -370,6 +427,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

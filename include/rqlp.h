@@ -161,6 +161,83 @@ int rqlp_orth(const double *X, int64_t rows, int32_t l, int64_t ldx, double *Qx,
 int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, int32_t *piv0,
               double *Q0, void *ws, size_t ws_bytes, rqlp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Adjoint (reverse-mode derivative) of RQLP.  The paper has no derivative;
+ * this differentiates Algorithm 2.1 (pivot2 = 1) with the column pivots held
+ * fixed (they are piecewise constant in A).
+ * ---------------------------------------------------------------------- */
+/* Workspace of rqlp_backward() (0 if invalid; needs pivot2 = 1, block_b = 0). */
+size_t rqlp_backward_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p,
+                                    const rqlp_opts *opts);
+
+/* dA = J^T (dQ, dL, dP): the vector-Jacobian product of A -> (Q, L, P) of
+ * rqlp() at A with the same Omega and options.  dQ (m x l), dL (l x l), dP
+ * (n x l) are FP64 device cotangents with ld l (NULL = zero); dA (m x n, FP64,
+ * ld ldda) is written.  The forward is recomputed inside (no state is kept
+ * between rqlp() and this call); the sweep runs in FP64. */
+int rqlp_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                  int32_t p, const double *Omega, int64_t ldo, const rqlp_opts *opts,
+                  const double *dQ, const double *dL, const double *dP, double *dA, int64_t ldda,
+                  void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched factorizations: many independent problems in one graph launch.
+ * ---------------------------------------------------------------------- */
+/* One problem of a batch: the arguments of rqlp() (device pointers). */
+typedef struct {
+  const void *A;
+  int32_t a_dtype;
+  int32_t k;
+  int64_t m, n, lda;
+  int32_t p;
+  int32_t reserved;
+  const double *Omega;
+  int64_t ldo;
+  double *Q, *L, *P, *Lvalues;
+  int32_t *piv0, *piv1;
+} rqlp_problem;
+
+/* Launch shapes of a batch (0 selects a default): parallel branches (problems
+ * in flight), CTAs the FP64 products aim for, K splits of the tensor-core
+ * products.  The autotuner of the Python package picks them per batch shape. */
+typedef struct {
+  int32_t branches;
+  int32_t gemm_target_ctas;
+  int32_t mma_max_splits;
+  int32_t reserved;
+} rqlp_batch_tuning;
+
+typedef struct rqlp_batch *rqlp_batch_t;
+
+/* Device workspace of a batch (one rqlp() workspace per branch plus the
+ * per-problem status array); 0 if a problem or the options are invalid
+ * (block_b must be 0: BRQLP is not batched). */
+size_t rqlp_batched_workspace_size(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts,
+                                   const rqlp_batch_tuning *tune);
+
+/* Records the factorizations of all `count` problems (Algorithms 2.1 / 2.2 with
+ * the options in `opts`) into one CUDA graph over tune->branches parallel
+ * streams and instantiates it.  Problems run with small launch shapes so that
+ * many fit on the GPU at once; results are those of rqlp() on each problem.
+ * Not thread-safe with other calls of this library on the same host thread
+ * while it records.  The problem table is read during this call only. */
+int rqlp_batched_create(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts,
+                        const rqlp_batch_tuning *tune, void *ws, size_t ws_bytes,
+                        rqlp_batch_t *plan);
+
+/* Runs the whole batch: one cudaGraphLaunch on `stream`. */
+int rqlp_batched_launch(rqlp_batch_t plan, rqlp_stream_t stream);
+
+/* Synchronizes `stream`, writes each problem's status to statuses[count] (may
+ * be NULL) and returns the first error, else the first warning, else RQLP_OK. */
+int rqlp_batched_status(rqlp_batch_t plan, rqlp_stream_t stream, int32_t *statuses);
+
+/* Number of kernel nodes in the batch's graph (kernels per launch). */
+int rqlp_batched_kernel_nodes(rqlp_batch_t plan);
+
+/* Frees the graph (not the workspace, which the caller owns). */
+void rqlp_batched_destroy(rqlp_batch_t plan);
+
 /*
  * rqlp_cpqr() for callers that cannot allocate device memory.  The paper has
  * no counterpart: this is a deployment variant of Algorithm 2.1 step 5.

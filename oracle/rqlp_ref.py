@@ -286,3 +286,129 @@ def brqlp(A: np.ndarray, k: int, p: int, b: int, Omega: np.ndarray, pivot2: bool
 def lvalue_err(sigma: np.ndarray, Lvalues: np.ndarray, k: int) -> float:
     """err = max_{j<=k} |sigma_j(A) - |L_jj|| (Section 5 error measure)."""
     return float(np.max(np.abs(np.asarray(sigma)[:k] - np.abs(np.asarray(Lvalues)[:k]))))
+
+
+# ------------------------------------------------------------------ adjoint
+# Reverse-mode derivative of RQLP (Algorithm 2.1) with the column pivots
+# held fixed (the pivots are piecewise constant in A).  Not in the paper.
+def qr_vjp(Q, R, dQ, dR):
+    """Cotangent of X for the thin QR X = Q R (rows >= cols, R invertible).
+
+    dX = (dQ + Q copyltu(M)) R^{-T},  M = R dR^T - dQ^T Q,
+    copyltu(M) = tril(M) + tril(M, -1)^T.
+    """
+    M = R @ dR.T - dQ.T @ Q
+    S = np.tril(M) + np.tril(M, -1).T
+    T = dQ + Q @ S
+    return sla_solve_triangular(R, T.T, lower=False, trans="N").T  # T R^{-T}
+
+
+def sla_solve_triangular(R, B, lower, trans):
+    import scipy.linalg as sla
+    return sla.solve_triangular(R, B, lower=lower, trans=trans)
+
+
+def wide_qr(C):
+    """Unpivoted QR C = Q R of an l x n matrix (l <= n), diag(R) >= 0."""
+    l = C.shape[0]
+    Q, U = householder_qr(C[:, :l])
+    return Q, np.concatenate([U, Q.T @ C[:, l:]], axis=1)
+
+
+def wide_qr_vjp(Q, R, dQ, dR):
+    """Cotangent of C for C = Q R, C l x n (l <= n), R = [U | V].
+
+    C2 = Q V gives V = Q^T C2: dC2 = Q dV and dQ picks up C2 dV^T; the
+    square part C1 = Q U then follows qr_vjp.
+    """
+    l = Q.shape[0]
+    U, Vr = R[:, :l], R[:, l:]
+    dU, dV = dR[:, :l], dR[:, l:]
+    C2 = Q @ Vr
+    dC1 = qr_vjp(Q, U, dQ + C2 @ dV.T, dU)
+    return np.concatenate([dC1, Q @ dV], axis=1)
+
+
+def rqlp_trace(A, k, p, Omega, q=0, piv0=None, piv1=None):
+    """RQLP forward (Algorithm 2.1) keeping every intermediate.
+
+    With piv0 / piv1 given, the two column-pivoted QRs use these pivots
+    instead of choosing them (B Pi0 = Q0 R0 and R0^T Pi1 = Q1 R1 as
+    unpivoted QRs of the permuted matrices).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Om = np.asarray(Omega, dtype=np.float64)
+    t = {"Ys": [A @ Om], "Vs": [], "RYs": [], "Zs": [], "Ws": [], "RZs": []}
+    for _ in range(q):
+        V, RY = householder_qr(t["Ys"][-1])
+        Z = A.T @ V
+        Wq, RZ = householder_qr(Z)
+        t["Vs"].append(V); t["RYs"].append(RY); t["Zs"].append(Z); t["Ws"].append(Wq)
+        t["RZs"].append(RZ)
+        t["Ys"].append(A @ Wq)
+    V, RY = householder_qr(t["Ys"][-1])
+    t["V"], t["RY"] = V, RY
+    B = V.T @ A
+    if piv0 is None or piv1 is None:
+        Q0, R0, piv0 = cpqr(B)
+        Q1, R1, piv1 = cpqr(R0.T)
+    else:
+        piv0 = np.asarray(piv0)
+        piv1 = np.asarray(piv1)
+        Q0, R0 = wide_qr(B[:, piv0])
+        Q1, R1 = householder_qr(R0.T[:, piv1])
+    n, l = A.shape[1], V.shape[1]
+    P = np.zeros((n, l))
+    P[piv0, :] = Q1
+    QB = Q0[:, piv1]
+    t.update(B=B, Q0=Q0, R0=R0, Q1=Q1, R1=R1, piv0=piv0, piv1=piv1, QB=QB,
+             Q=V @ QB, L=R1.T, P=P)
+    return t
+
+
+def rqlp_vjp(A, k, p, Omega, dQ, dL, dP, q=0):
+    """dA = J^T (dQ, dL, dP) for RQLP (Algorithm 2.1) with fixed pivots.
+
+    The sweep runs the forward of rqlp_trace backwards, product by product
+    and QR by QR (qr_vjp, wide_qr_vjp), recomputing the forward first.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Om = np.asarray(Omega, dtype=np.float64)
+    t = rqlp_trace(A, k, p, Om, q)
+    l = t["V"].shape[1]
+    n = A.shape[1]
+    dQ = np.zeros_like(t["Q"]) if dQ is None else dQ
+    dL = np.zeros((l, l)) if dL is None else dL
+    dP = np.zeros_like(t["P"]) if dP is None else dP
+    piv0, piv1 = t["piv0"], t["piv1"]
+    # step 7: Q = V Q0[:, piv1], L = R1^T, P[piv0] = Q1
+    dV = dQ @ t["QB"].T
+    dQ0 = np.zeros((l, l))
+    dQ0[:, piv1] = t["V"].T @ dQ
+    dQ1 = dP[piv0, :]
+    dR1 = np.triu(dL.T)
+    # step 6: R0^T[:, piv1] = Q1 R1
+    dXp = qr_vjp(t["Q1"], t["R1"], dQ1, dR1)
+    dX = np.zeros((n, l))
+    dX[:, piv1] = dXp
+    dR0 = np.triu(dX.T)
+    # step 5: B[:, piv0] = Q0 R0
+    dC = wide_qr_vjp(t["Q0"], t["R0"], dQ0, dR0)
+    dB = np.zeros((l, n))
+    dB[:, piv0] = dC
+    # step 4: B = V^T A
+    dV = dV + A @ dB.T
+    dA = t["V"] @ dB
+    # step 3: V = qr(Y_q), R discarded
+    dY = qr_vjp(t["V"], t["RY"], dV, np.zeros((l, l)))
+    # step 2, backwards: Y_i = A W_i, W_i = qr(Z_i), Z_i = A^T V_i, V_i = qr(Y_{i-1})
+    for i in reversed(range(q)):
+        dA += dY @ t["Ws"][i].T
+        dW = A.T @ dY
+        dZ = qr_vjp(t["Ws"][i], t["RZs"][i], dW, np.zeros((l, l)))
+        dA += t["Vs"][i] @ dZ.T
+        dVi = A @ dZ
+        dY = qr_vjp(t["Vs"][i], t["RYs"][i], dVi, np.zeros((l, l)))
+    # step 1: Y_0 = A Omega
+    dA += dY @ Om.T
+    return dA

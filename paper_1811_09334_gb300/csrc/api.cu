@@ -530,3 +530,224 @@ int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+// Reverse-mode derivative of RQLP (Algorithm 2.1, pivot2 = 1) with the
+// column pivots held fixed: dA = J^T (dQ, dL, dP).  The forward is recomputed
+// (Y is not stored by rqlp()), keeping the range-finder bases and their R
+// factors, then every product and QR is swept backwards.  For a thin QR
+// X = Q R:  dX = (dQ + Q copyltu(R dR^T - dQ^T Q)) R^{-T};  for the wide
+// QR C = Q [U | V] the V block adds C2 dV^T to dQ and Q dV to dC2.  All
+// rank-l updates of dA are gathered into one product [L_1 .. L_P][R_1 .. R_P]^T
+// with K = (2q + 2) l.
+namespace {
+
+struct BwdPlan {
+  Plan F;
+  double *Vs, *RYs, *Ws, *RZs, *RY, *Q1, *R1;
+  double *M, *S, *Rinv, *RinvT, *sm2, *dQ0, *dQB, *dR1, *U, *dU, *dC1, *QBt, *Q0t;
+  double *T, *dV, *dW, *dQ1, *dXp, *dX, *dCt, *dBt;
+  double *Lcat, *Rcat, *RcatT;
+  size_t bytes;
+};
+
+BwdPlan carve_bwd(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
+  BwdPlan b;
+  b.F = carve(ws, m, n, l, o);
+  Arena a(ws ? reinterpret_cast<char *>(ws) + (b.F.bytes + 255) / 256 * 256 : nullptr);
+  const int q = o.q, P = 2 * q + 2;
+  const size_t ll = (size_t)l * l;
+  const int64_t big = std::max(m, n);
+  b.Vs = a.take<double>((size_t)std::max(q, 1) * m * l);
+  b.RYs = a.take<double>((size_t)std::max(q, 1) * ll);
+  b.Ws = a.take<double>((size_t)std::max(q, 1) * n * l);
+  b.RZs = a.take<double>((size_t)std::max(q, 1) * ll);
+  b.RY = a.take<double>(ll);
+  b.Q1 = a.take<double>((size_t)n * l);
+  b.R1 = a.take<double>(ll);
+  for (double **p : {&b.M, &b.S, &b.Rinv, &b.RinvT, &b.sm2, &b.dQ0, &b.dQB, &b.dR1, &b.U, &b.dU,
+                     &b.dC1, &b.QBt, &b.Q0t})
+    *p = a.take<double>(ll);
+  for (double **p : {&b.T, &b.dV, &b.dW, &b.dQ1, &b.dXp, &b.dX, &b.dCt, &b.dBt})
+    *p = a.take<double>((size_t)big * l);
+  b.Lcat = a.take<double>((size_t)m * P * l);
+  b.Rcat = a.take<double>((size_t)n * P * l);
+  b.RcatT = a.take<double>((size_t)P * l * n);
+  b.bytes = (b.F.bytes + 255) / 256 * 256 + a.off;
+  return b;
+}
+
+// dX (rows x l, ld lddx) = (dQ + Q copyltu(M)) R^{-T}, M = R dR^T - dQ^T Q.
+int qr_vjp_dev(const BwdPlan &B, const double *Qm, int64_t ldq, const double *R, const double *dQ,
+               int64_t lddq, const double *dR, int64_t rows, int l, double *dX, int64_t lddx,
+               cudaStream_t st) {
+  double *part = B.F.ob.part;
+  CK(gemm_f64(true, RQLP_F64, dQ, lddq, Qm, ldq, B.M, l, l, l, rows, -1.0, 0.0, part, nullptr,
+              nullptr, st));
+  if (dR) {
+    CK(transpose(dR, l, l, l, B.sm2, l, st));
+    CK(gemm_f64(false, RQLP_F64, R, l, B.sm2, l, B.M, l, l, l, l, 1.0, 1.0, part, nullptr, nullptr,
+                st));
+  }
+  CK(copyltu(B.M, l, B.S, st));
+  CK(copy2d(dQ, rows, l, lddq, B.T, l, nullptr, st));
+  CK(gemm_f64(false, RQLP_F64, Qm, ldq, B.S, l, B.T, l, rows, l, l, 1.0, 1.0, part, nullptr,
+              nullptr, st));
+  CK(trinv_upper(R, l, B.Rinv, nullptr, st));
+  CK(transpose(B.Rinv, l, l, l, B.RinvT, l, st));
+  CK(gemm_f64(false, RQLP_F64, B.T, l, B.RinvT, l, dX, lddx, rows, l, l, 1.0, 0.0, part, nullptr,
+              nullptr, st));
+  return RQLP_OK;
+}
+
+__global__ void k_fill(double *p, int64_t n, double v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+cudaError_t zero(double *p, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(p, n, 0.0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int run_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int l,
+                 const double *Omega, int64_t ldo, const rqlp_opts &o, const double *dQ,
+                 const double *dL, const double *dP, double *dA, int64_t ldda, void *ws,
+                 size_t ws_bytes, cudaStream_t st) {
+  BwdPlan B = carve_bwd(ws, m, n, l, o);
+  if (B.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
+  const Plan &F = B.F;
+  Ctrl *ctrl = F.ctrl;
+  const int q = o.q, Pc = 2 * q + 2;
+  const int64_t ldc = (int64_t)Pc * l;
+  const size_t ml = (size_t)m * l, nl = (size_t)n * l, ll = (size_t)l * l;
+  double *part = F.ob.part;
+  const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
+  CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  // ---- forward with intermediates (Algorithm 2.1) ----
+  int site = 0;
+  RET(prod_nn(F, o, A, a_dtype, m, n, lda, Omega, ldo, l, F.Y, st));
+  for (int i = 0; i < q; ++i) {
+    RET(orth(F.Y, m, l, l, B.Vs + i * ml, l, B.RYs + i * ll, F.ob, ctrl, site++, st));
+    RET(prod_tn(F, o, A, a_dtype, m, n, lda, B.Vs + i * ml, l, l, F.Z, st));
+    RET(orth(F.Z, n, l, l, B.Ws + i * nl, l, B.RZs + i * ll, F.ob, ctrl, site++, st));
+    RET(prod_nn(F, o, A, a_dtype, m, n, lda, B.Ws + i * nl, l, l, F.Y, st));
+  }
+  RET(orth(F.Y, m, l, l, F.V, l, B.RY, F.ob, ctrl, site++, st));
+  RET(prod_tn(F, o, A, a_dtype, m, n, lda, F.V, l, l, F.Z, st));  // B^T
+  CK(cpqr_wide(F.Z, n, l, l, F.R0t, l, F.piv0, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st));
+  CK(form_q(F.Vh, l, F.tau, l, l, F.Q0, l, st));
+  RET(orth(F.R0t, n, l, l, F.X, l, F.Racc, F.ob, ctrl, site++, st));
+  CK(transpose(F.Racc, l, l, l, F.Rt, l, st));
+  CK(cpqr_wide(F.Rt, l, l, l, F.Tl, l, F.piv1, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st));
+  CK(form_q(F.Vh, l, F.tau, l, l, F.Qi, l, st));
+  CK(gemm_f64(false, RQLP_F64, F.X, l, F.Qi, l, B.Q1, l, n, l, l, 1.0, 0.0, part, nullptr, nullptr,
+              st));                                               // Q1 = Qa Qc
+  CK(transpose(F.Tl, l, l, l, B.R1, l, st));                     // R1 = L^T
+  CK(gather_cols(F.Q0, l, l, l, F.piv1, F.QB, l, st));            // Q_B = Q0 Pi1
+  // ---- step 7: Q = V Q_B, L = R1^T, P = Pi0 Q1 ----
+  if (dQ) {
+    CK(transpose(F.QB, l, l, l, B.QBt, l, st));
+    CK(gemm_f64(false, RQLP_F64, dQ, l, B.QBt, l, B.dV, l, m, l, l, 1.0, 0.0, part, nullptr,
+                nullptr, st));
+    CK(gemm_f64(true, RQLP_F64, F.V, l, dQ, l, B.dQB, l, l, l, m, 1.0, 0.0, part, nullptr, nullptr,
+                st));
+    CK(zero(B.dQ0, ll, st));
+    CK(scatter_cols(B.dQB, l, l, l, F.piv1, B.dQ0, l, st));
+  } else {
+    CK(zero(B.dV, ml, st));
+    CK(zero(B.dQ0, ll, st));
+  }
+  if (dP) CK(permute_rows(dP, n, l, l, F.piv0, B.dQ1, l, false, st));
+  else CK(zero(B.dQ1, nl, st));
+  if (dL) {
+    CK(transpose(dL, l, l, l, B.dR1, l, st));
+    CK(zero_triangle(B.dR1, l, l, true, st));
+  } else {
+    CK(zero(B.dR1, ll, st));
+  }
+  // ---- step 6: R0^T Pi1 = Q1 R1 ----
+  RET(qr_vjp_dev(B, B.Q1, l, B.R1, B.dQ1, l, B.dR1, n, l, B.dXp, l, st));
+  CK(zero(B.dX, nl, st));
+  CK(scatter_cols(B.dXp, n, l, l, F.piv1, B.dX, l, st));
+  CK(mask_lower_trapezoid(B.dX, n, l, l, st));  // dR0^T: R0 is upper trapezoidal
+  // ---- step 5: B Pi0 = Q0 R0, R0 = [U | V] ----
+  CK(transpose(F.R0t, l, l, l, B.U, l, st));
+  CK(transpose(B.dX, l, l, l, B.dU, l, st));
+  if (n > l) {
+    CK(gemm_f64(true, RQLP_F64, F.R0t + ll, l, B.dX + ll, l, B.M, l, l, l, n - l, 1.0, 0.0, part,
+                nullptr, nullptr, st));
+    CK(gemm_f64(false, RQLP_F64, F.Q0, l, B.M, l, B.dQ0, l, l, l, l, 1.0, 1.0, part, nullptr,
+                nullptr, st));
+  }
+  RET(qr_vjp_dev(B, F.Q0, l, B.U, B.dQ0, l, B.dU, l, l, B.dC1, l, st));
+  CK(transpose(B.dC1, l, l, l, B.dCt, l, st));
+  if (n > l) {
+    CK(transpose(F.Q0, l, l, l, B.Q0t, l, st));
+    CK(gemm_f64(false, RQLP_F64, B.dX + ll, l, B.Q0t, l, B.dCt + ll, l, n - l, l, l, 1.0, 0.0, part,
+                nullptr, nullptr, st));
+  }
+  CK(permute_rows(B.dCt, n, l, l, F.piv0, B.dBt, l, true, st));  // dB[:, piv0] = dC
+  // ---- step 4: B = V^T A ----
+  CK(gemm_f64(false, a_dtype, A, lda, B.dBt, l, B.dV, l, m, l, n, 1.0, 1.0, part, nullptr, nullptr,
+              st));
+  int pc = 0;
+  CK(copy2d(F.V, m, l, l, B.Lcat + pc * l, ldc, nullptr, st));
+  CK(copy2d(B.dBt, n, l, l, B.Rcat + pc * l, ldc, nullptr, st));
+  ++pc;
+  // ---- step 3: V = qr(Y_q) ----
+  RET(qr_vjp_dev(B, F.V, l, B.RY, B.dV, l, nullptr, m, l, B.Lcat + pc * l, ldc, st));
+  // ---- step 2, backwards ----
+  for (int i = q - 1; i >= 0; --i) {
+    const double *dY = B.Lcat + pc * l;
+    CK(copy2d(B.Ws + i * nl, n, l, l, B.Rcat + pc * l, ldc, nullptr, st));  // dA += dY W^T
+    ++pc;
+    CK(gemm_f64(true, a_dtype, A, lda, dY, ldc, B.dW, l, n, l, m, 1.0, 0.0, part, nullptr, nullptr,
+                st));                                                        // dW = A^T dY
+    RET(qr_vjp_dev(B, B.Ws + i * nl, l, B.RZs + i * ll, B.dW, l, nullptr, n, l, B.Rcat + pc * l,
+                   ldc, st));                                                // dZ
+    CK(copy2d(B.Vs + i * ml, m, l, l, B.Lcat + pc * l, ldc, nullptr, st));   // dA += V dZ^T
+    CK(gemm_f64(false, a_dtype, A, lda, B.Rcat + pc * l, ldc, B.dV, l, m, l, n, 1.0, 0.0, part,
+                nullptr, nullptr, st));                                      // dV = A dZ
+    ++pc;
+    RET(qr_vjp_dev(B, B.Vs + i * ml, l, B.RYs + i * ll, B.dV, l, nullptr, m, l, B.Lcat + pc * l,
+                   ldc, st));                                                // dY_{i-1}
+  }
+  // ---- step 1: Y_0 = A Omega ----
+  CK(copy2d(Omega, n, l, ldo, B.Rcat + pc * l, ldc, nullptr, st));
+  ++pc;
+  // dA = Lcat Rcat^T (one product, K = (2q + 2) l)
+  CK(transpose(B.Rcat, n, ldc, ldc, B.RcatT, n, st));
+  CK(gemm_f64(false, RQLP_F64, B.Lcat, ldc, B.RcatT, n, dA, ldda, m, n, ldc, 1.0, 0.0, nullptr,
+              nullptr, nullptr, st));
+  return RQLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rqlp_backward_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p,
+                                    const rqlp_opts *opts) {
+  if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return 0;
+  if (!opts->pivot2 || opts->block_b != 0) return 0;
+  return carve_bwd(nullptr, m, n, k + p, *opts).bytes + 256;
+}
+
+int rqlp_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                  int32_t p, const double *Omega, int64_t ldo, const rqlp_opts *opts,
+                  const double *dQ, const double *dL, const double *dP, double *dA, int64_t ldda,
+                  void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
+  if (!A || !Omega || !dA || !ws || lda < n || ldo < k + p || ldda < n) return RQLP_ERR_INVALID_ARG;
+  if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
+  if (!opts->pivot2 || opts->block_b != 0) return RQLP_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  return run_backward(A, a_dtype, m, n, lda, k + p, Omega, ldo, *opts, dQ, dL, dP, dA, ldda, ws,
+                      ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -203,6 +203,50 @@ k_form_q(const double *__restrict__ Vh, int64_t ldv, const double *__restrict__ 
   for (int i = lane; i < rows; i += 32) Q[(int64_t)i * ldq + c] = x[i];
 }
 
+// S = tril(M) + tril(M, -1)^T
+__global__ void k_copyltu(const double *__restrict__ M, int l, double *__restrict__ S) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
+    const int i = e / l, j = e - i * l;
+    S[e] = (i >= j) ? M[e] : M[(int64_t)j * l + i];
+  }
+}
+
+// Y[:, perm[j]] = X[:, j] (rows x c)
+__global__ void k_scatter_cols(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
+                               const int32_t *__restrict__ perm, double *__restrict__ Y,
+                               int64_t ldy) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    const int32_t pj = perm[j];
+    if (pj >= 0 && pj < c) Y[i * ldy + pj] = X[i * ldx + j];
+  }
+}
+
+// gather (Y[i] = X[perm[i]]) or scatter (Y[perm[i]] = X[i]) of rows
+__global__ void k_permute_rows(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
+                               const int32_t *__restrict__ perm, double *__restrict__ Y,
+                               int64_t ldy, int scatter) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    const int64_t pi = perm[i];
+    if (pi < 0 || pi >= r) continue;
+    if (scatter) Y[pi * ldy + j] = X[i * ldx + j];
+    else Y[i * ldy + j] = X[pi * ldx + j];
+  }
+}
+
+// zero X[i][j] for j > i in the first min(r, c) rows (the transposed
+// structure of an upper-trapezoidal factor)
+__global__ void k_mask_lower_trapezoid(double *X, int64_t r, int64_t c, int64_t ld) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e - i * c;
+    if (j > i) X[i * ld + j] = 0.0;
+  }
+}
+
 inline int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
   if (b > 4LL * num_sms()) b = 4LL * num_sms();
@@ -211,6 +255,11 @@ inline int grid_for(int64_t total, int threads) {
 }
 
 }  // namespace
+
+cudaError_t chol_init() {
+  return cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(200 * 1024));
+}
 
 cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
                        const int *skip_unless, cudaStream_t st) {
@@ -225,8 +274,12 @@ cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ct
       set_to = 200 * 1024;
     }
   }
-  k_chol_upper<<<1, 1024, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, ctrl, site,
-                                                      skip_unless, use_smem ? 1 : 0);
+  // enough threads for the first trailing update, no more: every column
+  // step ends in CTA barriers whose cost grows with the CTA size
+  int threads = ((l * l / 12) + 31) / 32 * 32;
+  threads = std::max(128, std::min(1024, threads));
+  k_chol_upper<<<1, threads, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, ctrl, site,
+                                                         skip_unless, use_smem ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }
@@ -273,6 +326,37 @@ cudaError_t gather_cols(const double *X, int64_t r, int64_t c, int64_t ldx, cons
 cudaError_t iota(int32_t *p, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_iota<<<grid_for(n, 256), 256, 0, st>>>(p, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t copyltu(const double *M, int l, double *S, cudaStream_t st) {
+  k_copyltu<<<grid_for((int64_t)l * l, 256), 256, 0, st>>>(M, l, S);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_cols(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                         double *Y, int64_t ldy, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_scatter_cols<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ldx, perm, Y, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t permute_rows(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                         double *Y, int64_t ldy, bool scatter, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_permute_rows<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ldx, perm, Y, ldy,
+                                                       scatter ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mask_lower_trapezoid(double *X, int64_t r, int64_t c, int64_t ld, cudaStream_t st) {
+  if (r <= 0 || c <= 0) return cudaSuccess;
+  k_mask_lower_trapezoid<<<grid_for(std::min(r, c) * c, 256), 256, 0, st>>>(X, std::min(r, c),
+                                                                             c, ld);
   count_launch();
   return cudaGetLastError();
 }

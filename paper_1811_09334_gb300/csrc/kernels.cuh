@@ -70,6 +70,7 @@ cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const
 // ---- dense_small.cu ------------------------------------------------------
 // Cholesky G = R^T R of an l x l SPD matrix (upper R, ld l), breakdown
 // detection, one shifted retry with Fukaya's shift for `rows` x l data.
+cudaError_t chol_init();
 cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
                        const int *skip_unless, cudaStream_t st);
 // Rinv = R^{-1} for upper triangular R (l x l, ld l).
@@ -88,6 +89,16 @@ cudaError_t gather_cols(const double *X, int64_t r, int64_t c, int64_t ldx, cons
                         double *Y, int64_t ldy, cudaStream_t st);
 // p[i] = i (a valid permutation, written before a pivoting kernel that may abort)
 cudaError_t iota(int32_t *p, int64_t n, cudaStream_t st);
+// S = tril(M) + tril(M, -1)^T for an l x l M (ld l)
+cudaError_t copyltu(const double *M, int l, double *S, cudaStream_t st);
+// Y[:, perm[j]] = X[:, j]
+cudaError_t scatter_cols(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                         double *Y, int64_t ldy, cudaStream_t st);
+// rows: Y[i] = X[perm[i]] (gather) or Y[perm[i]] = X[i] (scatter)
+cudaError_t permute_rows(const double *X, int64_t r, int64_t c, int64_t ldx, const int32_t *perm,
+                         double *Y, int64_t ldy, bool scatter, cudaStream_t st);
+// X[i][j] = 0 for j > i (i < min(r, c))
+cudaError_t mask_lower_trapezoid(double *X, int64_t r, int64_t c, int64_t ld, cudaStream_t st);
 // Lvalues[i] = T[i][i]
 cudaError_t diag_of(const double *T, int l, int64_t ldt, double *out, cudaStream_t st);
 // Zero the strict lower (lower_zero = 1) or strict upper part of an l x l matrix.

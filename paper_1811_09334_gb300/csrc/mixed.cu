@@ -479,6 +479,16 @@ int split_skinny(const MixedBufs &mx, bool split, const double *S, int64_t K, in
 
 }  // namespace
 
+int mixed_init() {
+  if (!encode_fn()) return RQLP_ERR_CUDA;
+  if (cudaFuncSetAttribute(k_mma_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  return RQLP_OK;
+}
+
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx) {
   mx = MixedBufs{};
   if (prec == RQLP_PREC_FP64) return;

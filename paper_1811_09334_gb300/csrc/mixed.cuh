@@ -16,6 +16,9 @@ struct MixedBufs {
   int l;
 };
 
+// One-time set-up (driver entry point, kernel attributes) done before any
+// stream capture.
+int mixed_init();
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx);
 // Splits A (and A^T) into BF16 pairs once per factorization.
 int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, int64_t m, int64_t n,

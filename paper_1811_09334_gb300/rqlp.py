@@ -32,6 +32,19 @@ class Opts(ctypes.Structure):
                 ("block_b", _c_i32), ("debug_flags", _c_i32), ("spin_limit_ns", _c_i64)]
 
 
+class Problem(ctypes.Structure):
+    """rqlp_problem: one problem of a batch (device pointers)."""
+    _fields_ = [("A", _c_p), ("a_dtype", _c_i32), ("k", _c_i32), ("m", _c_i64), ("n", _c_i64),
+                ("lda", _c_i64), ("p", _c_i32), ("reserved", _c_i32), ("Omega", _c_p),
+                ("ldo", _c_i64), ("Q", _c_p), ("L", _c_p), ("P", _c_p), ("Lvalues", _c_p),
+                ("piv0", _c_p), ("piv1", _c_p)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("branches", _c_i32), ("gemm_target_ctas", _c_i32), ("mma_max_splits", _c_i32),
+                ("reserved", _c_i32)]
+
+
 class RqlpError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -60,6 +73,18 @@ _SIGS = {
     "rqlp_orth": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_i64, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr_static": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_i32, _c_p]),
+    "rqlp_batched_workspace_size": (_c_sz, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
+                                            ctypes.POINTER(BatchTuning)]),
+    "rqlp_batched_create": (_c_i32, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
+                                     ctypes.POINTER(BatchTuning), _c_p, _c_sz, ctypes.POINTER(_c_p)]),
+    "rqlp_batched_launch": (_c_i32, [_c_p, _c_p]),
+    "rqlp_batched_status": (_c_i32, [_c_p, _c_p, _c_p]),
+    "rqlp_batched_kernel_nodes": (_c_i32, [_c_p]),
+    "rqlp_batched_destroy": (None, [_c_p]),
+    "rqlp_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
+    "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
+                               ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_sz,
+                               _c_p]),
     "rqlp_launch_count": (ctypes.c_longlong, []),
     "rqlp_profile_begin": (_c_i32, []),
     "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
@@ -315,3 +340,132 @@ def cpqr(B, ws=None, stream=None):
                            st), "rqlp_cpqr")
     _check(lib().rqlp_read_status(_ptr(ws), st), "rqlp_cpqr (device status)")
     return Q0, R0t.t().contiguous(), piv
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """Many independent factorizations recorded into one CUDA graph.
+
+    As: list of (m_i, n_i) CUDA tensors (float64/float32, row-major); ks: the
+    target ranks; p: oversampling; Omegas: list of (n_i, k_i + p) float64
+    CUDA tensors.  Outputs are allocated here (self.out[i] holds Q, L, P,
+    Lvalues, piv0, piv1).  launch() runs the whole batch with one
+    cudaGraphLaunch; status() synchronizes and returns (worst, per-problem).
+    """
+
+    def __init__(self, As, ks, p, Omegas, q=0, d=1, pivot2=True, prec="fp64", branches=0,
+                 gemm_target_ctas=0, mma_max_splits=0):
+        torch = _torch()
+        L_ = lib()
+        self.count = len(As)
+        self._keep = [As, Omegas]
+        self.out = []
+        probs = (Problem * self.count)()
+        for i, (A, k, Om) in enumerate(zip(As, ks, Omegas)):
+            m, n = A.shape
+            l = k + p
+            dev = A.device
+            o = dict(Q=torch.empty((m, l), dtype=torch.float64, device=dev),
+                     L=torch.empty((l, l), dtype=torch.float64, device=dev),
+                     P=torch.empty((n, l), dtype=torch.float64, device=dev),
+                     Lvalues=torch.empty((l,), dtype=torch.float64, device=dev),
+                     piv0=torch.empty((n,), dtype=torch.int32, device=dev),
+                     piv1=torch.empty((l,), dtype=torch.int32, device=dev))
+            self.out.append(o)
+            probs[i] = Problem(_ptr(A), _dtype_code(A), int(k), m, n, _row_major(A, "A"), int(p), 0,
+                               _ptr(Om), _row_major(Om, "Omega"), _ptr(o["Q"]), _ptr(o["L"]),
+                               _ptr(o["P"]), _ptr(o["Lvalues"]), _ptr(o["piv0"]), _ptr(o["piv1"]))
+        self._probs = probs
+        self.opts = opts(q, d, pivot2, prec)
+        self.tuning = BatchTuning(int(branches), int(gemm_target_ctas), int(mma_max_splits), 0)
+        need = L_.rqlp_batched_workspace_size(probs, self.count, ctypes.byref(self.opts),
+                                              ctypes.byref(self.tuning))
+        if need == 0:
+            raise RqlpError(-1, "rqlp_batched_workspace_size")
+        self.ws = workspace(need, As[0].device)
+        handle = _c_p()
+        _check(L_.rqlp_batched_create(probs, self.count, ctypes.byref(self.opts),
+                                      ctypes.byref(self.tuning), _ptr(self.ws), self.ws.numel(),
+                                      ctypes.byref(handle)), "rqlp_batched_create")
+        self.handle = handle
+
+    @property
+    def kernel_nodes(self) -> int:
+        return int(lib().rqlp_batched_kernel_nodes(self.handle))
+
+    def launch(self, stream=None):
+        _check(lib().rqlp_batched_launch(self.handle, _stream(stream)), "rqlp_batched_launch")
+
+    def status(self, stream=None):
+        arr = (_c_i32 * self.count)()
+        worst = lib().rqlp_batched_status(self.handle, _stream(stream), ctypes.cast(arr, _c_p))
+        return worst, list(arr)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rqlp_batched_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- adjoint
+def vjp(A, k, p, Omega, dQ=None, dL=None, dP=None, q=0, prec="fp64", ws=None, stream=None):
+    """dA = J^T (dQ, dL, dP) of A -> (Q, L, P) for RQLP (Algorithm 2.1) with
+    fixed pivots, computed on the GPU (FP64 sweep, forward recomputed)."""
+    torch = _torch()
+    m, n = A.shape
+    o = opts(q, 1, True, prec)
+    L_ = lib()
+    need = L_.rqlp_backward_workspace_size(m, n, k, p, ctypes.byref(o))
+    if need == 0:
+        raise RqlpError(-1, "rqlp_backward_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    dA = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    cont = lambda t: None if t is None else t.detach().to(torch.float64).contiguous()
+    dQ, dL, dP = cont(dQ), cont(dL), cont(dP)
+    st = _stream(stream)
+    _check(L_.rqlp_backward(_ptr(A), _dtype_code(A), m, n, _row_major(A, "A"), k, p, _ptr(Omega),
+                            _row_major(Omega, "Omega"), ctypes.byref(o), _ptr(dQ), _ptr(dL),
+                            _ptr(dP), _ptr(dA), n, _ptr(ws), ws.numel(), st), "rqlp_backward")
+    _check(L_.rqlp_read_status(_ptr(ws), st), "rqlp_backward (device status)")
+    return dA
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class RQLPFunction(torch.autograd.Function):
+        """(Q, L, P) = RQLP(A) on the GPU with a hand-written adjoint (pivots fixed)."""
+
+        @staticmethod
+        def forward(ctx, A, Omega, k, p, q, prec):
+            out = rqlp(A.detach(), k, p, Omega, q=q, pivot2=True, prec=prec)
+            ctx.save_for_backward(A, Omega)
+            ctx.cfg = (k, p, q, prec)
+            return out["Q"], out["L"], out["P"]
+
+        @staticmethod
+        def backward(ctx, dQ, dL, dP):
+            A, Omega = ctx.saved_tensors
+            k, p, q, prec = ctx.cfg
+            dA = vjp(A.detach(), k, p, Omega, dQ, dL, dP, q=q, prec=prec)
+            return dA.to(A.dtype), None, None, None, None, None
+
+    return RQLPFunction
+
+
+_RQLPFunction = None
+
+
+def rqlp_autograd(A, k, p, Omega, q=0, prec="fp64"):
+    """Differentiable (Q, L, P) = RQLP(A) (torch.autograd, pivots held fixed)."""
+    global _RQLPFunction
+    if _RQLPFunction is None:
+        _RQLPFunction = _autograd_function()
+    return _RQLPFunction.apply(A, Omega, k, p, q, prec)

@@ -54,10 +54,14 @@ def _orthonormal_np(G: np.ndarray) -> np.ndarray:
 
 
 def low_rank_from_spectrum(m: int, n: int, sigma: np.ndarray, seed: int,
-                           device: Optional[str] = None, out_dtype=np.float64):
+                           device: Optional[str] = None, out_dtype=np.float64,
+                           qr_float32: bool = False):
     """A = X diag(sigma) Y^T, X (m x r) and Y (n x r) orthonormal, r = len(sigma).
 
     Returns a numpy array, or a torch tensor on ``device`` if one is given.
+    qr_float32 (device only) takes the QR of the Gaussian factors in FP32 for
+    speed; X and Y are then orthonormal to about 1e-6, i.e. A's singular
+    values are sigma to that relative accuracy.
     """
     r = len(sigma)
     rng = _rng(seed)
@@ -73,10 +77,12 @@ def low_rank_from_spectrum(m: int, n: int, sigma: np.ndarray, seed: int,
     def orth(G):
         try:
             Gt = torch.from_numpy(G).to(device)
+            if qr_float32:
+                Gt = Gt.float()
             Q, R = torch.linalg.qr(Gt)
             s = torch.sign(torch.diagonal(R))
             s[s == 0] = 1.0
-            return Q * s
+            return (Q * s).double()
         except RuntimeError:
             # torch's device linear algebra can be unavailable (e.g. under a
             # profiler); the same construction then runs on the host.
@@ -195,11 +201,12 @@ def c5_shapes(count: int = 512, mmax: int = 4096, seed: int = SEED_A + 4):
     return shapes
 
 
-def c5_matrix(i: int, m: int, n: int, device=None):
-    """Matrix i of the batched workload: X diag(j^-1.5) Y^T."""
+def c5_matrix(i: int, m: int, n: int, device=None, fast: bool = False):
+    """Matrix i of the batched workload: X diag(j^-1.5) Y^T (fast: FP32 QR on the device)."""
     r = min(m, n)
     sigma = np.arange(1, r + 1, dtype=np.float64) ** -1.5
-    return low_rank_from_spectrum(m, n, sigma, SEED_A + 100 + i, device=device), sigma
+    return low_rank_from_spectrum(m, n, sigma, SEED_A + 100 + i, device=device,
+                                  qr_float32=fast), sigma
 
 
 def w6(kind: str, n: int, t: int = 30, s: Optional[float] = None, seed: int = SEED_A + 5,
