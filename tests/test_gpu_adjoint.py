@@ -3,8 +3,10 @@ and against central finite differences of the oracle forward.
 
 Tolerances: the FP64 sweep against the oracle's sweep to 1e-8 normwise
 (both recompute the forward; the conditioning of the QR adjoints, about
-kappa(R)^2 <= 1e6 here, scales eps); finite differences with h = 1e-3 in
-FP64 (the oracle forward with the pivots fixed) to 1e-4 relative.
+kappa(R)^2 <= 1e6 here, scales eps); through torch.autograd the gradient
+comes back in A's dtype, FP32 for the differentiable workload, so 1e-6
+there; finite differences with h = 1e-3 in FP64 (the oracle forward with
+the pivots fixed) to 1e-4 relative.
 """
 import numpy as np
 import pytest
@@ -80,8 +82,9 @@ def test_c4_losses_autograd_vs_oracle_and_fd(R, small):
     dP[:, :k] = -2 * Ek.T @ base["Q"][:, :k] @ base["L"][:k, :k]
     ref2 = 2 * Ek + O.rqlp_vjp(A64, k, p, Om, dQ, dLm, dP, q=1)
     g1n, g2n = g1.double().cpu().numpy(), g2.double().cpu().numpy()
-    assert np.linalg.norm(g1n - ref1) <= 1e-8 * np.linalg.norm(ref1)
-    assert np.linalg.norm(g2n - ref2) <= 1e-8 * np.linalg.norm(ref2)
+    # autograd returns the gradient in A's dtype (FP32): FP32 rounding level
+    assert np.linalg.norm(g1n - ref1) <= 1e-6 * np.linalg.norm(ref1)
+    assert np.linalg.norm(g2n - ref2) <= 1e-6 * np.linalg.norm(ref2)
     # central differences (h = 1e-3, FP64 forward with the pivots fixed)
     h = 1e-3
     piv0, piv1 = base["piv0"], base["piv1"]
