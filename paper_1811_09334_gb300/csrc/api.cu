@@ -28,9 +28,10 @@ namespace {
 
 // Scratch for CholeskyQR2 on rows x l data.
 struct OrthBufs {
-  double *part;  // split-K partials
-  double *G, *Rp, *Rinv, *Racc, *Rtmp;
-  double *tmp;   // rows x l ping-pong
+  double *part;   // split-K partials
+  double *gpart;  // Gram chunk partials
+  double *G, *Rp, *Rinv, *Racc, *Rtmp, *Dinv;
+  double *tmp;    // rows x l ping-pong
 };
 
 size_t part_doubles(int64_t m, int64_t n, int l) {
@@ -52,6 +53,8 @@ size_t part_doubles(int64_t m, int64_t n, int l) {
 void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBufs &o,
                 double *shared_part) {
   o.part = shared_part ? shared_part : a.take<double>(part_doubles(m, n, l));
+  o.gpart = a.take<double>((size_t)gram_chunks(std::max<int64_t>(rows_max, l)) * l * l);
+  o.Dinv = a.take<double>((size_t)l * l);
   o.G = a.take<double>((size_t)l * l);
   o.Rp = a.take<double>((size_t)l * l);
   o.Rinv = a.take<double>((size_t)l * l);
@@ -62,26 +65,22 @@ void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBuf
 
 // CholeskyQR2 (+ a third pass iff a pass needed the shift): Xq = X R^{-1}.
 int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
-              const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
+              const OrthBufs &o, Ctrl *ctrl, int site, int passes, double again_tol,
+              cudaStream_t st) {
   site %= kShiftSites;
   const int *flag = &ctrl->shift_flag[site];
   int ev;
   // one CholeskyQR pass: src -> dst, R_acc <- R_pass R_acc (skip: conditional pass)
   auto pass = [&](const double *src, int64_t lds, double *dst, int64_t ldd, bool first,
-                  const int *skip) -> int {
+                  const int *skip, double tol) -> int {
     ev = prof_start(kProfGram, st);
-    CK(gemm_f64(true, RQLP_F64, src, lds, src, lds, o.G, l, l, l, rows, 1.0, 0.0, o.part, nullptr,
-                skip, st));
+    CK(gram_sym(src, rows, l, lds, o.gpart, o.G, skip, st));
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
-    CK(chol_upper(o.G, l, rows, o.Rp, ctrl, site, skip, st));
+    CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol));
     prof_stop(kProfChol, ev, st);
-    ev = prof_start(kProfTrinv, st);
-    CK(trinv_upper(o.Rp, l, o.Rinv, skip, st));
-    prof_stop(kProfTrinv, ev, st);
     ev = prof_start(kProfApply, st);
-    CK(gemm_f64(false, RQLP_F64, src, lds, o.Rinv, l, dst, ldd, rows, l, l, 1.0, 0.0, o.part,
-                nullptr, skip, st));
+    CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st));
     if (R) {
       if (first) {
         CK(copy2d(o.Rp, l, l, l, o.Racc, l, skip, st));
@@ -94,12 +93,25 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfApply, ev, st);
     return RQLP_OK;
   };
-  int r = pass(X, ldx, o.tmp, l, true, nullptr);       // pass 1: X -> tmp
+  int r;
+  if (passes >= 2 && again_tol >= 0.0) {
+    // adaptive: the second pass runs only when the first one says it is needed
+    r = pass(X, ldx, o.tmp, l, true, nullptr, again_tol);
+    if (r != RQLP_OK) return r;
+    r = pass(o.tmp, l, Xq, ldq, false, &ctrl->again_flag[site], -1.0);
+    if (r != RQLP_OK) return r;
+    CK(copy2d(o.tmp, rows, l, l, Xq, ldq, &ctrl->done_flag[site], st));
+  } else if (passes >= 2) {
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0);   // pass 1: X -> tmp
+    if (r != RQLP_OK) return r;
+    r = pass(o.tmp, l, Xq, ldq, false, nullptr, -1.0); // pass 2: tmp -> Xq
+  } else {
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0);   // one pass: X -> tmp -> Xq
+    if (r == RQLP_OK) CK(copy2d(o.tmp, rows, l, l, Xq, ldq, nullptr, st));
+  }
   if (r != RQLP_OK) return r;
-  r = pass(o.tmp, l, Xq, ldq, false, nullptr);         // pass 2: tmp -> Xq
-  if (r != RQLP_OK) return r;
-  // pass 3, only when the device raised the shift flag: Xq -> tmp -> Xq
-  r = pass(Xq, ldq, o.tmp, l, false, flag);
+  // one more pass, only when the device raised the shift flag: Xq -> tmp -> Xq
+  r = pass(Xq, ldq, o.tmp, l, false, flag, -1.0);
   if (r != RQLP_OK) return r;
   CK(copy2d(o.tmp, rows, l, l, Xq, ldq, flag, st));
   if (R) CK(copy2d(o.Racc, l, l, l, R, l, nullptr, st));
@@ -107,9 +119,15 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
 }
 
 int orth(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
-         const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st) {
-  return orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, st);
+         const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st, int passes = 2,
+         double again_tol = -1.0) {
+  return orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, passes, again_tol, st);
 }
+
+// Mixed forms: a CholeskyQR pass leaves Q orthonormal to about eps cond(X)^2;
+// the second pass of CholeskyQR2 runs only when that exceeds 1e-10, far below
+// the error of the BF16 products.  The FP64 form always runs both passes.
+double again_tol_of(const rqlp_opts &o) { return o.prec == RQLP_PREC_FP64 ? -1.0 : 1e-10; }
 
 // Everything rqlp() carves from its workspace.
 struct Plan {
@@ -227,7 +245,7 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
   CK(form_q(P.Vh, l, P.tau, l, l, P.Q0, l, st));
   prof_stop(kProfSmall, ev, st);
   if (o.pivot2) {
-    RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st));
+    RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
     CK(transpose(P.Racc, l, l, l, P.Rt, l, st));
     CK(cpqr_wide(P.Rt, l, l, l, P.Tl, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
     CK(copy2d(P.Tl, l, l, l, L, ldo, nullptr, st));
@@ -236,12 +254,13 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
                 nullptr, st));
   } else {
-    RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st));
+    RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
     CK(set_identity(P.QB, l, l, l, st));
     CK(set_identity(P.Macc, l, l, l, st));
     for (int i = 2; i <= o.d; ++i) {
       CK(transpose(P.Rprev, l, l, l, P.Xs, l, st));
-      RET(orth(P.Xs, l, l, l, P.Qi, l, P.Rprev, P.ob, ctrl, site0 + i - 1, st));
+      RET(orth(P.Xs, l, l, l, P.Qi, l, P.Rprev, P.ob, ctrl, site0 + i - 1, st, 2,
+               again_tol_of(o)));
       double *acc = (i % 2 == 0) ? P.QB : P.Macc;
       CK(gemm_f64(false, RQLP_F64, acc, l, P.Qi, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
                   nullptr, st));
@@ -322,13 +341,15 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   }
   // range finder (Section 2) with q power steps
   RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega, ldo, l, P.Y, st));
+  // between power steps one CholeskyQR pass suffices: only the span of the
+  // intermediate bases matters; the final V is CholeskyQR2
   for (int i = 0; i < o.q; ++i) {
-    RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st));
+    RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 1));
     RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
-    RET(orth(P.Z, n, l, l, P.W, l, nullptr, P.ob, P.ctrl, site++, st));
+    RET(orth(P.Z, n, l, l, P.W, l, nullptr, P.ob, P.ctrl, site++, st, 1));
     RET(prod_nn(P, o, A, a_dtype, m, n, lda, P.W, l, l, P.Y, st));
   }
-  RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st));
+  RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 2, again_tol_of(o)));
   // B^T = A^T V  (Algorithm 2.1 step 4)
   RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
   RET(qlp_stage(P, o, m, n, l, P.V, l, P.Z, Q, L, Pout, l, pv0, pv1, site, st));

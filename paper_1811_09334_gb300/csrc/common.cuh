@@ -18,8 +18,10 @@ struct Ctrl {
   unsigned bar_gen;         // grid barrier: generation counter
   int timeout_site;         // diagnostics: which wait gave up
   int pad[13];
+  int again_flag[16];       // per CholeskyQR site: 1 when a second pass is needed
+  int done_flag[16];        // per CholeskyQR site: 1 when one pass was enough
 };
-static_assert(sizeof(Ctrl) == 128, "Ctrl layout");
+static_assert(sizeof(Ctrl) == 256, "Ctrl layout");
 
 constexpr int kMaxL = 256;               // widest sketch supported
 constexpr int kShiftSites = 15;

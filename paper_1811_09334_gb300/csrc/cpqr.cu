@@ -52,11 +52,13 @@ struct CpqrParams {
 };
 
 __device__ __forceinline__ bool better(double na, int ia, double nb, int ib) {
-  // (na, ia) beats (nb, ib): larger norm, ties to the lower index; ia < 0 is empty
+  // (na, ia) beats (nb, ib): larger norm, ties to the lower index; ia < 0 is
+  // empty.  Norms are >= 0 (empty slots hold -1), so their bit patterns order
+  // like the values and the comparison stays on the integer pipe.
   if (ia < 0) return false;
   if (ib < 0) return true;
-  if (na > nb) return true;
-  if (na < nb) return false;
+  const long long ka = __double_as_longlong(na), kb = __double_as_longlong(nb);
+  if (ka != kb) return ka > kb;
   return ia < ib;
 }
 
@@ -75,7 +77,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   const int nc = (int)max((int64_t)0, min(P.n, c0 + P.cpb) - c0);
   double *cols = P.use_smem ? sm : P.gcols + (int64_t)b * P.cpb * l;
   double *nrm = P.use_smem ? sm + (int64_t)P.cpb * l : reinterpret_cast<double *>(sm);
-  int *pivoted = reinterpret_cast<int *>(nrm + P.cpb);
+  double *nrm0 = nrm + P.cpb;  // norm^2 when last computed exactly
+  int *pivoted = reinterpret_cast<int *>(nrm0 + P.cpb);
 
   // ---- load the slab, exact initial norms ------------------------------
   for (int jj = warp; jj < nc; jj += kWarps) {
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     s = warp_sum(s);
     if (lane == 0) {
       nrm[jj] = s;
+      nrm0[jj] = s;
       pivoted[jj] = 0;
       if (!isfinite(s)) set_status(P.ctrl, RQLP_ERR_NONFINITE);
     }
@@ -193,26 +197,60 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       if (tid == 0) { P.tau[s] = tau; P.piv[s] = wi; }
     }
     // ---- 3. apply to the slab ----
-    for (int jj = warp; jj < nc; jj += kWarps) {
-      if (pivoted[jj]) continue;
-      double *col = cols + (int64_t)jj * l;
-      if ((int)(c0 + jj) == wi) {
-        double *out = P.R0t + (int64_t)s * P.ldr;
-        for (int r = lane; r < l; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
-        if (lane == 0) { pivoted[jj] = 1; nrm[jj] = -1.0; }
-        continue;
-      }
-      if (tau != 0.0) {
+    // the winner's column is final: rows < s from the slab, beta at s, zeros below
+    if ((int)(wi - c0) >= 0 && (int)(wi - c0) < nc && warp == 0) {
+      const int jw = (int)(wi - c0);
+      const double *col = cols + (int64_t)jw * l;
+      double *out = P.R0t + (int64_t)s * P.ldr;
+      for (int r = lane; r < l; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
+      if (lane == 0) { pivoted[jw] = 1; nrm[jw] = -1.0; }
+    }
+    // groups of 8 lanes per column, four columns per warp: the dot product
+    // needs a 3-level reduction, and each FP64 warp instruction works on four
+    // columns at once
+    {
+      const int sub = lane >> 3, gl = lane & 7;
+      for (int jb = warp * 4; jb < nc; jb += kWarps * 4) {
+        const int jj = jb + sub;
+        const bool act = jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi;
+        double *col = cols + (int64_t)(act ? jj : 0) * l;
         double w = 0.0;
-        for (int r = s + lane; r < l; r += 32) w = fma(s_v[r - s], col[r], w);
-        w = warp_sum(w) * tau;
-        for (int r = s + lane; r < l; r += 32) col[r] = fma(-w, s_v[r - s], col[r]);
+        if (act && tau != 0.0)
+          for (int r = s + gl; r < l; r += 8) w = fma(s_v[r - s], col[r], w);
+        w += __shfl_xor_sync(0xffffffffu, w, 4);
+        w += __shfl_xor_sync(0xffffffffu, w, 2);
+        w += __shfl_xor_sync(0xffffffffu, w, 1);
+        if (act && tau != 0.0) {
+          w *= tau;
+          for (int r = s + gl; r < l; r += 8) col[r] = fma(-w, s_v[r - s], col[r]);
+        }
+        __syncwarp();
+        // norm downdating: ||col(s+1:)||^2 = ||col(s:)||^2 - col(s)^2 (the
+        // reflector preserves ||col(s:)||); recomputed exactly when more than
+        // 99% of the norm has cancelled since the last exact value
+        int need = 0;
+        double nd = 0.0;
+        if (act && gl == 0) {
+          const double rsv = col[s];
+          nd = nrm[jj] - rsv * rsv;
+          need = !(nd > 0.01 * nrm0[jj]);
+        }
+        need = __shfl_sync(0xffffffffu, need, lane & ~7);
+        double t = 0.0;
+        if (need)
+          for (int r = s + 1 + gl; r < l; r += 8) t = fma(col[r], col[r], t);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (act && gl == 0) {
+          if (need) {
+            nrm[jj] = t;
+            nrm0[jj] = t;
+          } else {
+            nrm[jj] = nd;
+          }
+        }
       }
-      __syncwarp();
-      double t = 0.0;
-      for (int r = s + 1 + lane; r < l; r += 32) t = fma(col[r], col[r], t);
-      t = warp_sum(t);
-      if (lane == 0) nrm[jj] = t;
     }
     __syncthreads();
     if (s + 1 < l) {
@@ -273,7 +311,7 @@ Plan plan_for(int64_t n, int l) {
   if (G < 1) G = 1;
   int cpb = (int)((n + G - 1) / G);
   G = (int)((n + cpb - 1) / cpb);
-  const size_t state = (size_t)cpb * (sizeof(double) + sizeof(int));
+  const size_t state = (size_t)cpb * (2 * sizeof(double) + sizeof(int));
   const size_t slab = (size_t)cpb * l * sizeof(double);
   p.use_smem = (slab + state <= 190 * 1024) ? 1 : 0;
   p.smem = (p.use_smem ? slab : 0) + state;

@@ -257,8 +257,9 @@ inline int grid_for(int64_t total, int threads) {
 }  // namespace
 
 cudaError_t chol_init() {
-  return cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(200 * 1024));
+  cudaError_t e = cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(200 * 1024));
+  return e == cudaSuccess ? cholqr_init() : e;
 }
 
 cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,

@@ -108,6 +108,24 @@ cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaS
 cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
                    double *Q, int64_t ldq, cudaStream_t st);
 
+// ---- cholqr.cu: one CholeskyQR pass on a rows x l panel -------------------
+int64_t gram_chunks(int64_t rows);
+cudaError_t cholqr_init();  // kernel attributes, set before any stream capture
+// G = X^T X (symmetric, l x l, ld l); part: gram_chunks(rows) * l * l doubles
+cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *part, double *G,
+                     const int *skip_unless, cudaStream_t st);
+// G = R^T R (R upper, ld l) with shifted retry; Dinv: inverses of R's 16 x 16
+// diagonal blocks (block-diagonal, ld l)
+// again_tol >= 0: set ctrl->again_flag[site] (and done_flag = 1 - it) when
+// eps cond(R)^2 > again_tol, i.e. when one pass leaves Q less orthonormal
+cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
+                         int site, const int *skip_unless, cudaStream_t st,
+                         double again_tol = -1.0);
+// Q = X R^{-1} by a blocked triangular solve (X and Q must not alias)
+cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
+                       const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
+                       cudaStream_t st);
+
 // ---- cpqr.cu ---------------------------------------------------------------
 size_t cpqr_ws_bytes(int64_t n, int l);
 // Scratch bytes cpqr_wide() touches when the column slabs fit in shared
