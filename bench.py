@@ -119,7 +119,7 @@ def _class_work(m, n, l, q, d, prec):
     """
     rows = [m] * q + [n] * q + [m, n] + [l] * max(0, d - 1)
     passes = 2
-    a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0}[prec] * m * n
+    a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0, "fp8": 1.0}[prec] * m * n
     prod = ("flops", (2 * q + 2) * 2.0 * m * n * l) if prec == "fp64" else \
         ("bytes", (2 * q + 2) * a_bytes)
     return {
@@ -130,6 +130,8 @@ def _class_work(m, n, l, q, d, prec):
         "cholqr_trinv": ("flops", passes * len(rows) * l ** 3 / 3.0),
         "cholqr_apply": ("flops", passes * sum(r * l * l + l ** 3 / 3.0 for r in rows)),
         "explicit_Q0": ("flops", 4.0 * l ** 3 / 3.0),
+        "prep_A": ("bytes", {"fp64": 0.0, "bf16x3": 16.0, "bf16": 12.0, "fp8": 18.0}[prec] * m * n),
+        "assembly": ("flops", 2.0 * (m + n) * l * l),
     }
 
 
@@ -425,7 +427,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()

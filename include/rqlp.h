@@ -59,7 +59,10 @@ typedef enum {
   RQLP_PREC_FP64 = 0,   /* FP64 CUDA-core products (A in FP64 or FP32) */
   RQLP_PREC_BF16X3 = 1, /* tcgen05 BF16 tensor cores, split A = Ah + Al and W = Wh + Wl,
                            three products Ah Wh + Ah Wl + Al Wh accumulated in FP32 */
-  RQLP_PREC_BF16 = 2    /* tcgen05 BF16 tensor cores, one product, FP32 accumulation */
+  RQLP_PREC_BF16 = 2,   /* tcgen05 BF16 tensor cores, one product, FP32 accumulation */
+  RQLP_PREC_FP8 = 3     /* tcgen05 E4M3 tensor cores, one product, FP32 accumulation; A scaled
+                           by a power of two per row (per column for the A^T products) and the
+                           skinny operand per column, the scales divided out in FP64 */
 } rqlp_prec;
 
 /* Element type of A. */
@@ -276,7 +279,8 @@ long long rqlp_launch_count(void);
  * on its stream around (0) every product with A, (1) every column-pivoted QR
  * of B, and, inside every CholeskyQR pass, (2) the Gram matrix, (3) the
  * Cholesky factor, (4) the triangular inverse, (5) X R^{-1} with the R
- * update; and (6) the explicit Q0 of the first CPQR. */
+ * update; (6) the explicit Q0 of the first CPQR; (7) the precision
+ * preparation of A; (8) the final products Q = V Q_B and P. */
 int rqlp_profile_begin(void);
 
 /* Stops timing; waits for the recorded events and writes, per class c <

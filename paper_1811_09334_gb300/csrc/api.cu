@@ -179,7 +179,7 @@ bool valid_opts(const rqlp_opts *o) {
   if (o->q < 0 || o->q > 16) return false;
   if (o->pivot2 != 0 && o->pivot2 != 1) return false;
   if (!o->pivot2 && (o->d < 1 || o->d > 64)) return false;
-  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_BF16) return false;
+  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_FP8) return false;
   if (o->block_b < 0) return false;
   if (o->spin_limit_ns < 0) return false;
   return true;
@@ -251,8 +251,10 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     CK(copy2d(P.Tl, l, l, l, L, ldo, nullptr, st));
     CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st));
     CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
+    const int eva = prof_start(kProfAssembly, st);
     CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
                 nullptr, st));
+    prof_stop(kProfAssembly, eva, st);
   } else {
     RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
     CK(set_identity(P.QB, l, l, l, st));
@@ -269,14 +271,23 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     CK(gemm_f64(false, RQLP_F64, P.Q0, l, P.QB, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
                 nullptr, st));
     CK(copy2d(P.sm1, l, l, l, P.QB, l, nullptr, st));
-    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
-                nullptr, st));
+    const int eva = prof_start(kProfAssembly, st);
+    if (o.d <= 2) {
+      // no odd inner factor beyond Q(1): P = Pi0 Q(1), a row scatter
+      CK(permute_rows(P.X, n, l, l, piv0, Pout, ldo, true, st));
+    } else {
+      CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part,
+                  piv0, nullptr, st));
+    }
+    prof_stop(kProfAssembly, eva, st);
     if (o.d % 2 == 1) CK(transpose(P.Rprev, l, l, l, L, ldo, st));
     else CK(copy2d(P.Rprev, l, l, l, L, ldo, nullptr, st));
     CK(iota(piv1, l, st));
   }
+  const int evq = prof_start(kProfAssembly, st);
   CK(gemm_f64(false, RQLP_F64, Vb, ldv, P.QB, l, Q, ldo, m, l, l, 1.0, 0.0, P.ob.part, nullptr,
               nullptr, st));
+  prof_stop(kProfAssembly, evq, st);
   return RQLP_OK;
 }
 
@@ -332,7 +343,11 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
   int32_t *pv0 = piv0 ? piv0 : P.piv0;
   int32_t *pv1 = piv1 ? piv1 : P.piv1;
-  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
+  if (o.prec != RQLP_PREC_FP64) {
+    const int ev = prof_start(kProfPrep, st);
+    RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
+    prof_stop(kProfPrep, ev, st);
+  }
   int site = 0;
   if (o.block_b > 0) {
     RET(run_brqlp(P, o, A, a_dtype, m, n, lda, l, Omega, ldo, Q, L, Pout, pv0, pv1, st));
@@ -476,7 +491,7 @@ int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t ld
   if (!A || !W || !Y || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldw < l ||
       ldy < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_BF16) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP8) return RQLP_ERR_INVALID_ARG;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;
@@ -502,7 +517,7 @@ int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   if (!A || !V || !Z || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldv < l ||
       ldz < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_BF16) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP8) return RQLP_ERR_INVALID_ARG;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;

@@ -148,19 +148,19 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     __syncthreads();
     for (int j = 0; j < l && !s_fail; ++j) {
       const double rs = s_next;
-      const double d = W[(int64_t)j * l + j];
+      double *Wj = W + j * l;  // l <= 256: 32-bit offsets
+      const double d = Wj[j];
       __syncthreads();
-      for (int c = j + 1 + tid; c < l; c += blockDim.x) W[(int64_t)j * l + c] *= rs;
-      if (tid == 0) {
-        W[(int64_t)j * l + j] = d * rs;
-      }
+      for (int c = j + 1 + tid; c < l; c += blockDim.x) Wj[c] *= rs;
+      if (tid == 0) Wj[j] = d * rs;
       __syncthreads();
       if (warp == 0) {
         if (j + 1 < l) {
-          const double r1 = W[(int64_t)j * l + j + 1];
+          double *W1 = W + (j + 1) * l;
+          const double r1 = Wj[j + 1];
           if (lane == 0) {
-            const double dn = W[(int64_t)(j + 1) * l + j + 1] - r1 * r1;
-            W[(int64_t)(j + 1) * l + j + 1] = dn;
+            const double dn = W1[j + 1] - r1 * r1;
+            W1[j + 1] = dn;
             const double g0 = s_gdiag[j + 1];
             int f = 0;
             if (!isfinite(dn) || !isfinite(g0)) f = 2;
@@ -169,13 +169,20 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
             s_next = f ? 1.0 : rsqrt(dn);
           }
           // the rest of row j + 1 of the trailing triangle
-          for (int c = j + 2 + lane; c < l; c += 32)
-            W[(int64_t)(j + 1) * l + c] -= r1 * W[(int64_t)j * l + c];
+          for (int c = j + 2 + lane; c < l; c += 32) W1[c] = fma(-r1, Wj[c], W1[c]);
         }
       } else {
         for (int a = j + 2 + (warp - 1); a < l; a += nw - 1) {
-          const double ra = W[(int64_t)j * l + a];
-          for (int c = a + lane; c < l; c += 32) W[(int64_t)a * l + c] -= ra * W[(int64_t)j * l + c];
+          const double ra = Wj[a];
+          double *Wa = W + a * l;
+          int c = a + lane;
+          for (; c + 32 < l; c += 64) {
+            const double x0 = fma(-ra, Wj[c], Wa[c]);
+            const double x1 = fma(-ra, Wj[c + 32], Wa[c + 32]);
+            Wa[c] = x0;
+            Wa[c + 32] = x1;
+          }
+          if (c < l) Wa[c] = fma(-ra, Wj[c], Wa[c]);
         }
       }
       __syncthreads();

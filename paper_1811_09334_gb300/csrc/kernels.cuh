@@ -34,7 +34,9 @@ enum ProfClass {
   kProfTrinv = 4,     // CholeskyQR: triangular inverses
   kProfApply = 5,     // CholeskyQR: X R^{-1} and R products
   kProfSmall = 6,     // explicit Q0 from the reflectors
-  kProfClasses = 7
+  kProfPrep = 7,      // precision preparation of A (mixed forms)
+  kProfAssembly = 8,  // Q = V Q_B and P = Pi0 (Q1 ...), the final products
+  kProfClasses = 9
 };
 int prof_start(int cls, cudaStream_t st);
 void prof_stop(int cls, int idx, cudaStream_t st);

@@ -25,6 +25,7 @@
 // TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -32,6 +33,8 @@
 #include "mixed.cuh"
 
 namespace rqk {
+
+int mixed_init();
 
 namespace {
 
@@ -119,9 +122,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major.
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+// Instruction descriptor, both operands K-major, F32 accumulator:
+// kind::f16 with BF16 x BF16 (format 1), or kind::f8f6f4 with E4M3 x E4M3
+// (format 0).
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool fp8 = false) {
+  return (1u << 4) | (fp8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -131,6 +136,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_fp8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -168,7 +183,9 @@ struct MmaArgs {
   unsigned long long limit_ns;
 };
 
-template <bool SPLIT>
+// SPLIT: three BF16 products of the hi/lo pairs; FP8: one E4M3 product with
+// 128 values per 128-byte K row (K tile of 128 elements instead of 64).
+template <bool SPLIT, bool FP8 = false>
 __global__ void __launch_bounds__(128, 1)
 k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
            const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
@@ -180,7 +197,8 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const uint32_t ybytes = (uint32_t)a.n_pad * kTileK * 2;
+  constexpr int KT = FP8 ? 128 : kTileK;  // K elements per stage
+  const uint32_t ybytes = (uint32_t)a.n_pad * 128;
   const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (kXBytes + ybytes);
   const int m_tile = blockIdx.x, split = blockIdx.y;
   const int kb0 = split * a.kb_per;
@@ -214,7 +232,7 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
         }
         const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
         mbar_expect_tx(&bar_full[s], stage_bytes);
-        const int kx = (kb0 + i) * kTileK, my = m_tile * kTileM;
+        const int kx = (kb0 + i) * KT, my = m_tile * kTileM;
         tma_load_2d(st, &tXh, kx, my, &bar_full[s]);
         tma_load_2d(st + kXBytes, &tYh, kx, 0, &bar_full[s]);
         if (SPLIT) {
@@ -233,7 +251,7 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      const uint32_t idesc = instr_desc(kTileM, a.n_pad);
+      const uint32_t idesc = instr_desc(kTileM, a.n_pad, FP8);
       for (int i = 0; i < nkb; ++i) {
         const int s = i % a.stages;
         const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
@@ -247,8 +265,13 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
         const uint32_t xl = yh + ybytes;
         const uint32_t yl = xl + kXBytes;
 #pragma unroll
-        for (int k = 0; k < kTileK / 16; ++k) {
-          const uint32_t off = k * 32;  // 16 BF16 along K inside the swizzled row
+        for (int k = 0; k < 4; ++k) {
+          // 32 bytes along K inside the swizzled row: 16 BF16 or 32 FP8 values
+          const uint32_t off = k * 32;
+          if (FP8) {
+            mma_fp8(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            continue;
+          }
           mma_bf16(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
           if (SPLIT) {
             mma_bf16(tmem, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
@@ -287,10 +310,12 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
-// C (M x ncols, FP64, ldc) = sum of S FP32 partial slices.
+// C (M x ncols, FP64, ldc) = sum of S FP32 partial slices, divided by the
+// row and column scales of a scaled (FP8) product when they are given.
 __global__ void k_sum_parts_f32(const float *__restrict__ part, int S, int64_t split_stride,
                                 int64_t M, int ncols, int ldp, double *__restrict__ C,
-                                int64_t ldc) {
+                                int64_t ldc, const float *__restrict__ rscale,
+                                const float *__restrict__ cscale) {
   const int64_t total = M * ncols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -298,38 +323,201 @@ __global__ void k_sum_parts_f32(const float *__restrict__ part, int S, int64_t s
     const int j = (int)(e - i * ncols);
     double s = 0.0;
     for (int z = 0; z < S; ++z) s += (double)part[(int64_t)z * split_stride + i * ldp + j];
+    if (rscale) s /= (double)rscale[i] * (double)cscale[j];
     C[i * ldc + j] = s;
   }
 }
 
-// A (m x n, lda) -> Ah, Al (m x ld1) and A^T halves Ath, Atl (n x ld2), BF16.
+// Per-row maxima of |A| and per-column maxima (one atomic max per column and
+// CTA, on the bit patterns of non-negative floats).  CTA = 32 rows.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloat16 *Ah,
-          __nv_bfloat16 *Al, int64_t ld1, __nv_bfloat16 *Ath, __nv_bfloat16 *Atl, int64_t ld2,
-          int with_lo) {
-  __shared__ __nv_bfloat16 th[32][34];
-  __shared__ __nv_bfloat16 tl[32][34];
+k_absmax(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, float *__restrict__ rmax,
+         unsigned *__restrict__ cmax_bits) {
+  __shared__ float red[32][9];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int nr = (int)min((int64_t)32, m - i0);
+  float rmx[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) rmx[r] = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    float cm = 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      if (r < nr) {
+        const float v = fabsf((float)A[(i0 + r) * lda + j]);
+        cm = fmaxf(cm, v);
+        rmx[r] = fmaxf(rmx[r], v);
+      }
+    }
+    atomicMax(cmax_bits + j, __float_as_uint(cm));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    float v = rmx[r];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[r][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[threadIdx.x][w]);
+    rmax[i0 + threadIdx.x] = t;
+  }
+}
+
+// Power-of-two scale putting the largest magnitude at or below 448 (E4M3 max).
+__device__ __forceinline__ float e4m3_scale(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+  return exp2f(floorf(log2f(448.f / amax)));
+}
+
+__global__ void k_scales(const float *__restrict__ rmax, int64_t m,
+                         const unsigned *__restrict__ cmax_bits, int64_t n, float *rscale,
+                         float *cscale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m + n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < m) rscale[i] = e4m3_scale(rmax[i]);
+    else cscale[i - m] = e4m3_scale(__uint_as_float(cmax_bits[i - m]));
+  }
+}
+
+// A -> E4M3 row-scaled (m x ld1) and E4M3 column-scaled transpose (n x ld2).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_quant_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, const float *rscale,
+          const float *cscale, __nv_fp8_storage_t *A8, int64_t ld1, __nv_fp8_storage_t *At8,
+          int64_t ld2) {
+  __shared__ __nv_fp8_storage_t t[32][36];
   const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int k = ty; k < 32; k += 8) {
     const int64_t i = i0 + k, j = j0 + tx;
     if (i < m && j < n) {
-      const double v = (double)A[i * lda + j];
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(h));
-      Ah[i * ld1 + j] = h;
-      if (with_lo) Al[i * ld1 + j] = lo;
-      th[k][tx] = h;
-      tl[k][tx] = lo;
+      const float v = (float)A[i * lda + j];
+      A8[i * ld1 + j] = __nv_cvt_float_to_fp8(v * rscale[i], __NV_SATFINITE, __NV_E4M3);
+      t[k][tx] = __nv_cvt_float_to_fp8(v * cscale[j], __NV_SATFINITE, __NV_E4M3);
     }
   }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
     const int64_t j = j0 + k, i = i0 + tx;
-    if (i < m && j < n) {
-      Ath[j * ld2 + i] = th[tx][k];
-      if (with_lo) Atl[j * ld2 + i] = tl[tx][k];
+    if (i < m && j < n) At8[j * ld2 + i] = t[tx][k];
+  }
+}
+
+// S (K x l, FP64) -> S^T as E4M3 (l x ldk) with one scale per column of S;
+// one CTA per column.
+__global__ void k_quant_skinny_t(const double *__restrict__ S, int64_t K, int l, int64_t lds,
+                                 __nv_fp8_storage_t *S8, int64_t ldk, float *scale) {
+  __shared__ float red[32];
+  __shared__ float s_sc;
+  for (int c = blockIdx.x; c < l; c += gridDim.x) {
+    float mx = 0.f;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, fabsf((float)S[k * lds + c]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+      s_sc = e4m3_scale(t);
+      scale[c] = s_sc;
+    }
+    __syncthreads();
+    const float sc = s_sc;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
+      S8[(int64_t)c * ldk + k] = __nv_cvt_float_to_fp8((float)S[k * lds + c] * sc, __NV_SATFINITE,
+                                                       __NV_E4M3);
+    __syncthreads();
+  }
+}
+
+// A (m x n, lda) -> Ah, Al (m x ld1) and A^T halves Ath, Atl (n x ld2), BF16.
+// Tile of 32 rows x 64 columns per CTA; each thread loads two neighbouring
+// elements and stores BF16 pairs, the transposed halves go through shared
+// memory.  One HBM pass: read A once, write the four BF16 arrays.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloat16 *Ah,
+          __nv_bfloat16 *Al, int64_t ld1, __nv_bfloat16 *Ath, __nv_bfloat16 *Atl, int64_t ld2,
+          int with_lo) {
+  __shared__ __nv_bfloat16 th[64][34];
+  __shared__ __nv_bfloat16 tl[64][34];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const bool vec = ((lda & 1) == 0) && ((ld1 & 1) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(A) & (2 * sizeof(T) - 1)) == 0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k;
+    const int64_t i = i0 + r, j = j0 + 2 * tx;
+    double v0 = 0.0, v1 = 0.0;  // FP64 or FP32 source values
+    if (i < m) {
+      if (vec && j + 1 < n) {
+        if (sizeof(T) == 8) {
+          const double2 p = *reinterpret_cast<const double2 *>(A + i * lda + j);
+          v0 = p.x;
+          v1 = p.y;
+        } else {
+          const float2 p = *reinterpret_cast<const float2 *>(A + i * lda + j);
+          v0 = p.x;
+          v1 = p.y;
+        }
+      } else {
+        if (j < n) v0 = (double)A[i * lda + j];
+        if (j + 1 < n) v1 = (double)A[i * lda + j + 1];
+      }
+    }
+    // one FP64 -> FP32 conversion per element, the split in FP32 (FP64
+    // arithmetic runs at 2 operations per clock per SM on this part): f - h
+    // is exact in FP32, and the FP32 rounding of v (2^-24) is far below the
+    // precision of the pair (about 2^-17)
+    const float f0 = (float)v0, f1 = (float)v1;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+    if (i < m) {
+      if (vec && j + 1 < n) {
+        *reinterpret_cast<__nv_bfloat162 *>(Ah + i * ld1 + j) = __halves2bfloat162(h0, h1);
+        if (with_lo) *reinterpret_cast<__nv_bfloat162 *>(Al + i * ld1 + j) = __halves2bfloat162(l0, l1);
+      } else {
+        if (j < n) {
+          Ah[i * ld1 + j] = h0;
+          if (with_lo) Al[i * ld1 + j] = l0;
+        }
+        if (j + 1 < n) {
+          Ah[i * ld1 + j + 1] = h1;
+          if (with_lo) Al[i * ld1 + j + 1] = l1;
+        }
+      }
+    }
+    th[2 * tx][r] = h0;
+    th[2 * tx + 1][r] = h1;
+    tl[2 * tx][r] = l0;
+    tl[2 * tx + 1][r] = l1;
+  }
+  __syncthreads();
+  // transposed: 64 rows (j) x 32 columns (i); a thread writes a BF16 pair of i
+  const bool tvec = ((ld2 & 1) == 0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jr = (ty + 8 * k) * 2 + (tx >> 4);  // 0..63
+    const int ic = (tx & 15) * 2;                 // 0..30
+    const int64_t j = j0 + jr, i = i0 + ic;
+    if (j >= n || i >= m) continue;
+    if (tvec && i + 1 < m) {
+      *reinterpret_cast<__nv_bfloat162 *>(Ath + j * ld2 + i) = __halves2bfloat162(th[jr][ic], th[jr][ic + 1]);
+      if (with_lo)
+        *reinterpret_cast<__nv_bfloat162 *>(Atl + j * ld2 + i) = __halves2bfloat162(tl[jr][ic], tl[jr][ic + 1]);
+    } else {
+      Ath[j * ld2 + i] = th[jr][ic];
+      if (with_lo) Atl[j * ld2 + i] = tl[jr][ic];
+      if (i + 1 < m) {
+        Ath[j * ld2 + i + 1] = th[jr][ic + 1];
+        if (with_lo) Atl[j * ld2 + i + 1] = tl[jr][ic + 1];
+      }
     }
   }
 }
@@ -367,14 +555,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2-D BF16 tensor map: `rows` x `cols` (cols contiguous, ld elements per
 // row), box of box_rows x 64 with the 128-byte swizzle.
 bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld,
-              int box_rows) {
+              int box_rows, bool fp8 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const int es = fp8 ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+  CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void *>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -388,14 +578,15 @@ struct GemmPlan {
   size_t smem;
 };
 
-GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split) {
+GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false) {
   GemmPlan g;
   g.n_pad = (int)round_up(l, 16);
-  const size_t ybytes = (size_t)g.n_pad * kTileK * 2;
+  const size_t ybytes = (size_t)g.n_pad * 128;
   const size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
   g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
   g.smem = g.stages * stage + 1024;
-  g.nk = (int)((K + kTileK - 1) / kTileK);
+  const int kt = fp8 ? 128 : kTileK;
+  g.nk = (int)((K + kt - 1) / kt);
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   int S = (int)std::max<int64_t>(1, num_sms() / tiles);
   S = std::min(S, std::max(1, g.nk / 4));
@@ -407,15 +598,16 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split) {
 }
 
 // C (M x l, FP64, ld l) = X Y^T with X (M x K) and Y (l x K) given as BF16
-// pairs with leading dimensions ldx / ldy.
+// pairs (or E4M3 with row scales of X and of Y) with leading dimensions ldx / ldy.
 int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const void *Xh,
              const void *Xl, int64_t ldx, const void *Yh, const void *Yl, int64_t ldy, double *C,
-             Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
-  GemmPlan g = plan_gemm(M, K, l, split);
+             Ctrl *ctrl, int64_t spin_ns, cudaStream_t st, bool fp8 = false,
+             const float *xscale = nullptr, const float *yscale = nullptr) {
+  GemmPlan g = plan_gemm(M, K, l, split, fp8);
   if (g.stages < 2) return RQLP_ERR_UNSUPPORTED;
   if ((int64_t)g.S * M * g.n_pad > mx.part_floats) return RQLP_ERR_WORKSPACE;
   CUtensorMap mXh, mXl, mYh, mYl;
-  if (!make_map(&mXh, Xh, M, K, ldx, kTileM) || !make_map(&mYh, Yh, l, K, ldy, g.n_pad))
+  if (!make_map(&mXh, Xh, M, K, ldx, kTileM, fp8) || !make_map(&mYh, Yh, l, K, ldy, g.n_pad, fp8))
     return RQLP_ERR_CUDA;
   if (split) {
     if (!make_map(&mXl, Xl, M, K, ldx, kTileM) || !make_map(&mYl, Yl, l, K, ldy, g.n_pad))
@@ -438,30 +630,16 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   a.ctrl = ctrl;
   a.limit_ns = spin_ns > 0 ? (unsigned long long)spin_ns : kDefaultSpinNs;
   dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)g.S);
-  if (split) {
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k_mma_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSmemLimit - 1024)) != cudaSuccess)
-        return RQLP_ERR_CUDA;
-      attr = true;
-    }
-    k_mma_bf16<true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k_mma_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSmemLimit - 1024)) != cudaSuccess)
-        return RQLP_ERR_CUDA;
-      attr = true;
-    }
-    k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
-  }
+  if (mixed_init() != RQLP_OK) return RQLP_ERR_CUDA;
+  if (fp8) k_mma_bf16<false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else if (split) k_mma_bf16<true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return RQLP_ERR_CUDA;
   const int64_t total = M * l;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4LL * num_sms());
-  k_sum_parts_f32<<<blocks, 256, 0, st>>>(mx.part, g.S, a.split_stride, M, l, a.ldp, C, l);
+  k_sum_parts_f32<<<blocks, 256, 0, st>>>(mx.part, g.S, a.split_stride, M, l, a.ldp, C, l,
+                                          fp8 ? xscale : nullptr, fp8 ? yscale : nullptr);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
@@ -480,18 +658,45 @@ int split_skinny(const MixedBufs &mx, bool split, const double *S, int64_t K, in
 }  // namespace
 
 int mixed_init() {
+  static int done = 0;
+  if (done) return RQLP_OK;
   if (!encode_fn()) return RQLP_ERR_CUDA;
   if (cudaFuncSetAttribute(k_mma_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess ||
       cudaFuncSetAttribute(k_mma_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess)
     return RQLP_ERR_CUDA;
+  done = 1;
   return RQLP_OK;
 }
 
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx) {
   mx = MixedBufs{};
   if (prec == RQLP_PREC_FP64) return;
+  if (prec == RQLP_PREC_FP8) {
+    mx.m = m;
+    mx.n = n;
+    mx.l = l;
+    const int64_t ld1 = round_up(n, 16), ld2 = round_up(m, 16);
+    mx.Ahi = a.take<uint8_t>((size_t)m * ld1);
+    mx.Athi = a.take<uint8_t>((size_t)n * ld2);
+    mx.Whi = a.take<uint8_t>((size_t)l * round_up(std::max(m, n), 16));
+    mx.sA = a.take<float>((size_t)m);
+    mx.sAt = a.take<float>((size_t)n);
+    mx.sW = a.take<float>((size_t)l);
+    mx.rmax = a.take<float>((size_t)m);
+    mx.cmax = a.take<unsigned>((size_t)n);
+    int64_t pf = 0;
+    for (int64_t M : {m, n}) {
+      GemmPlan g = plan_gemm(M, (M == m) ? n : m, l, false, true);
+      pf = std::max<int64_t>(pf, (int64_t)g.S * M * g.n_pad);
+    }
+    mx.part_floats = pf;
+    mx.part = a.take<float>((size_t)pf);
+    return;
+  }
   const bool split = prec == RQLP_PREC_BF16X3;
   mx.m = m;
   mx.n = n;
@@ -517,9 +722,33 @@ void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx)
 int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, int64_t m,
                     int64_t n, int64_t lda, cudaStream_t st) {
   if (!mx.Ahi) return RQLP_ERR_WORKSPACE;
+  if (prec == RQLP_PREC_FP8) {
+    if (cudaMemsetAsync(mx.cmax, 0, (size_t)n * sizeof(unsigned), st) != cudaSuccess)
+      return RQLP_ERR_CUDA;
+    const int rb = (int)((m + 31) / 32);
+    if (a_dtype == RQLP_F32)
+      k_absmax<float><<<rb, 256, 0, st>>>(static_cast<const float *>(A), m, n, lda, mx.rmax, mx.cmax);
+    else
+      k_absmax<double><<<rb, 256, 0, st>>>(static_cast<const double *>(A), m, n, lda, mx.rmax, mx.cmax);
+    count_launch();
+    k_scales<<<(int)std::min<int64_t>((m + n + 255) / 256, 1024), 256, 0, st>>>(mx.rmax, m, mx.cmax, n,
+                                                                            mx.sA, mx.sAt);
+    count_launch();
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+    auto *A8 = static_cast<__nv_fp8_storage_t *>(mx.Ahi);
+    auto *At8 = static_cast<__nv_fp8_storage_t *>(mx.Athi);
+    if (a_dtype == RQLP_F32)
+      k_quant_a<float><<<grid, dim3(32, 8), 0, st>>>(static_cast<const float *>(A), m, n, lda, mx.sA,
+                                                      mx.sAt, A8, round_up(n, 16), At8, round_up(m, 16));
+    else
+      k_quant_a<double><<<grid, dim3(32, 8), 0, st>>>(static_cast<const double *>(A), m, n, lda, mx.sA,
+                                                       mx.sAt, A8, round_up(n, 16), At8, round_up(m, 16));
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+  }
   const bool split = prec == RQLP_PREC_BF16X3;
   const int64_t ld1 = round_up(n, 8), ld2 = round_up(m, 8);
-  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+  dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 31) / 32));
   auto *Ah = static_cast<__nv_bfloat16 *>(mx.Ahi);
   auto *Al = static_cast<__nv_bfloat16 *>(mx.Alo);
   auto *Ath = static_cast<__nv_bfloat16 *>(mx.Athi);
@@ -534,8 +763,23 @@ int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, i
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
+int quant_skinny(const MixedBufs &mx, const double *S, int64_t K, int l, int64_t lds, int64_t ldk,
+                 cudaStream_t st) {
+  k_quant_skinny_t<<<l, 256, 0, st>>>(S, K, l, lds, static_cast<__nv_fp8_storage_t *>(mx.Whi), ldk,
+                                      mx.sW);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
 int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *W, int64_t ldw,
              int l, double *Y, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  if (prec == RQLP_PREC_FP8) {
+    const int64_t ldk = round_up(n, 16);
+    int r = quant_skinny(mx, W, n, l, ldw, ldk, st);
+    if (r != RQLP_OK) return r;
+    return gemm_xyt(mx, false, m, n, l, mx.Ahi, nullptr, round_up(n, 16), mx.Whi, nullptr, ldk, Y,
+                    ctrl, spin_ns, st, true, mx.sA, mx.sW);
+  }
   const bool split = prec == RQLP_PREC_BF16X3;
   const int64_t ldk = round_up(n, 8);
   int r = split_skinny(mx, split, W, n, l, ldw, ldk, st);
@@ -546,6 +790,13 @@ int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *
 
 int mixed_tn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *V, int64_t ldv,
              int l, double *Z, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  if (prec == RQLP_PREC_FP8) {
+    const int64_t ldk = round_up(m, 16);
+    int r = quant_skinny(mx, V, m, l, ldv, ldk, st);
+    if (r != RQLP_OK) return r;
+    return gemm_xyt(mx, false, n, m, l, mx.Athi, nullptr, round_up(m, 16), mx.Whi, nullptr, ldk, Z,
+                    ctrl, spin_ns, st, true, mx.sAt, mx.sW);
+  }
   const bool split = prec == RQLP_PREC_BF16X3;
   const int64_t ldk = round_up(m, 8);
   int r = split_skinny(mx, split, V, m, l, ldv, ldk, st);

@@ -12,6 +12,9 @@ struct MixedBufs {
   void *Whi, *Wlo;    // l_pad x max(m, n) BF16 split of a transposed skinny operand
   float *part;        // split-K FP32 partial sums
   int64_t part_floats;
+  // E4M3 form: A row-scaled, A^T column-scaled, skinny operand column-scaled
+  float *sA, *sAt, *sW, *rmax;
+  unsigned *cmax;
   int64_t m, n;
   int l;
 };

@@ -81,3 +81,29 @@ def test_mixed_factorization_lvalues(R, prec, q, d, pivot2):
         assert (np.abs(sg - so)[keep] / so[keep]).max() <= 2e-2
     Q = out["Q"].cpu().numpy()
     assert np.abs(Q.T @ Q - np.eye(pr.l)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("m,n,l", [(256, 192, 16), (2048, 1536, 110), (333, 257, 17), (8192, 8192, 110)])
+def test_fp8_products(R, m, n, l):
+    """E4M3 products with power-of-two row / column scales: u = 2^-4 per
+    operand, so a single product is held to 8e-2 normwise."""
+    rng = np.random.default_rng(m + 7 * n + l)
+    A = rng.standard_normal((m, n)) * (1.0 + 10.0 * rng.random((m, 1)))
+    Om = rng.standard_normal((n, l))
+    V = rng.standard_normal((m, l))
+    assert _normrel(R.sketch(_t(A), _t(Om), prec="fp8"), O.sketch(A, Om)) <= 8e-2
+    assert _normrel(R.project(_t(A), _t(V), prec="fp8"), O.adjoint_product(A, V)) <= 8e-2
+
+
+def test_fp8_factorization_singular_values(R):
+    pr = W.c2(m=2048, n=1536, k=60, p=10, q=1, d=2)
+    Om = W.omega(pr.n, pr.l, 0)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False, prec="fp8")
+    ref = O.rqlp(pr.A, pr.k, pr.p, Om, q=1, d=2, pivot2=False)
+    sg = np.linalg.svd(out["L"].cpu().numpy(), compute_uv=False)
+    so = np.linalg.svd(ref["L"], compute_uv=False)
+    keep = so >= 1e-3 * so[0]
+    # reported, not a precision claim: the E4M3 sketch moves sigma(L) by a few percent
+    assert (np.abs(sg - so)[keep] / so[keep]).max() <= 0.1
+    Q = out["Q"].cpu().numpy()
+    assert np.abs(Q.T @ Q - np.eye(pr.l)).max() <= 1e-12
