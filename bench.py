@@ -9,7 +9,9 @@ factorization A ~= Q L P^T through the C ABI with A resident in HBM (A is
 steps).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--prec fp64|bf16x3|bf16]
+                       [--prec fp64|bf16x3|bf16|fp8] [--shape M N]
+--shape runs the same recipe at another size (profiling captures use a
+smaller case); the default is the 8192 x 8192 workload.
 Prints ONE JSON line (rank 0).  With N > 1 (torchrun), each rank factors
 its own matrix (independent problems, no collective on the data path), and
 the value is the whole-job throughput.
@@ -31,8 +33,17 @@ if ROOT not in sys.path:
 
 M = N_ = 8192
 K_RANK, P_OVER, Q_POW, D_INNER = 100, 10, 1, 2
-WORKLOAD = "erqlp_8192x8192_k100_p10_q1_d2_expdecay"
+
+
+def workload_name(m: int, n: int) -> str:
+    return "erqlp_%dx%d_k%d_p%d_q%d_d%d_expdecay" % (m, n, K_RANK, P_OVER, Q_POW, D_INNER)
+
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA-core and DMMA) nominal rate
+
+
+def _l2_note(m: int, n: int) -> str:
+    # FP64 A against the 129 MB L2: no flush is needed when A cannot stay there
+    return "inputs larger than L2" if m * n * 8 > 129e6 else "inputs fit in L2 (not a bench line)"
 
 
 def _peaks():
@@ -225,7 +236,7 @@ def run_reference(args):
         dev = "cuda" if torch.cuda.is_available() else None
     except ImportError:
         dev = None
-    pr = W.c2(device=dev)
+    pr = W.c2(m=args.shape[0], n=args.shape[1], device=dev)
     A = pr.A.cpu().numpy() if dev else pr.A
     Om = W.omega(pr.n, pr.l, 0)
     for _ in range(args.warmup):
@@ -241,8 +252,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M, "n": N_, "k": K_RANK, "p": P_OVER,
-                       "q": Q_POW, "d": D_INNER, "l2": "inputs larger than L2"},
+            "config": {"workload": workload_name(pr.m, pr.n), "m": pr.m, "n": pr.n,
+                       "k": K_RANK, "p": P_OVER,
+                       "q": Q_POW, "d": D_INNER, "l2": _l2_note(pr.m, pr.n)},
             "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
                              "kind": "oracle",
                              "sample": "%d whole factorizations of the workload" % args.steps},
@@ -269,7 +281,7 @@ def run_ours(args):
         dist.barrier()
     R.lib()
     dev = torch.device("cuda", local)
-    pr = W.c2(device=str(dev))
+    pr = W.c2(m=args.shape[0], n=args.shape[1], device=str(dev))
     A = pr.A
     Om_np = W.omega(pr.n, pr.l, 0)
     Om = torch.from_numpy(Om_np).to(dev)
@@ -405,8 +417,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else args.prec + "+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": pr.m, "n": pr.n, "k": pr.k, "p": pr.p,
-                       "q": Q_POW, "d": D_INNER, "l2": "inputs larger than L2"},
+            "config": {"workload": workload_name(pr.m, pr.n), "m": pr.m, "n": pr.n,
+                       "k": pr.k, "p": pr.p,
+                       "q": Q_POW, "d": D_INNER, "l2": _l2_note(pr.m, pr.n)},
             "sketch_tflops": forms_out[args.prec]["sketch_tflops"],
             "forms": forms_out,
             "roofline": roof,
@@ -430,6 +443,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=2, default=[M, N_], metavar=("M", "N"))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

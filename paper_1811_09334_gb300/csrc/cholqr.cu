@@ -8,7 +8,12 @@
 //                   of 32 rows (4 x 4 register tiles of the triangle); a second
 //                   kernel sums the chunks in a fixed order (deterministic) and
 //                   mirrors the triangle.  Half the FMAs of a full product.
-//   k_chol_blocked  one CTA, right-looking over columns with the work of each
+//   k_chol_cluster  upper Cholesky of G on a cluster of 16 (or 8) CTAs (l <= 224):
+//                   rows dealt round-robin, finished rows pushed to every CTA
+//                   through distributed shared memory, look-ahead on the next
+//                   row; breakdown detection and the shifted retry.
+//   k_chol_blocked  the same for l > 224 on one CTA, right-looking over
+//                   columns with the work of each
 //                   column spread over every warp (a warp-wide FP64
 //                   instruction holds an SMSP's FP64 pipe for many cycles, so
 //                   single-warp FP64 work is slow here); warp 0 updates the
@@ -149,10 +154,10 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     for (int j = 0; j < l && !s_fail; ++j) {
       const double rs = s_next;
       double *Wj = W + j * l;  // l <= 256: 32-bit offsets
-      const double d = Wj[j];
-      __syncthreads();
+      // only thread 0 reads and rewrites the pivot; s_next and row j were
+      // written before the previous barrier
       for (int c = j + 1 + tid; c < l; c += blockDim.x) Wj[c] *= rs;
-      if (tid == 0) Wj[j] = d * rs;
+      if (tid == 0) Wj[j] = Wj[j] * rs;
       __syncthreads();
       if (warp == 0) {
         if (j + 1 < l) {
@@ -254,6 +259,366 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster Cholesky.  One SM does the l^3/6 FP64 FMAs of an l x l Cholesky at
+// about 2 FMA per clock, and every column adds a chain of dependent FP64
+// operations; here a cluster of C = 16 (or 8) CTAs shares the work.  Row a of
+// the trailing matrix belongs to CTA a % C; thread c of that CTA keeps column
+// c of its rows in registers.  Every finished row is also kept packed in each
+// CTA's shared memory (row j at off(j), entries j .. l-1): the owner pushes it
+// to the other CTAs with st.async stores that complete bytes on the
+// receiver's mbarrier for that row.  Every row is written once per attempt,
+// so no buffer is reused and nothing has to be acknowledged.  The owner of
+// row j + 1 applies row j to it first, scales it and sends it (look-ahead),
+// then updates its other rows.  A breakdown is sent in place of the diagonal
+// entry (-1: not positive enough, -2: not finite), so every CTA stops at the
+// same row; the shifted retry (as in the single-CTA kernel) uses a second set
+// of mbarriers.  The critical path per column (pivot test, reciprocal square
+// root, scaling) uses integer tests on the bit patterns and an FP32 estimate
+// refined in FP64, so few dependent FP64 operations sit on it.
+constexpr int kClusterMaxL = 224;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned map_shared(unsigned addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void bar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// false when the phase did not complete within limit_ns
+__device__ __forceinline__ bool bar_wait_bounded(unsigned bar, unsigned parity,
+                                                 unsigned long long limit_ns) {
+  if (bar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!bar_try(bar, parity))
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void st_async_f64(unsigned raddr, double v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(
+                   raddr),
+               "d"(v), "r"(rbar)
+               : "memory");
+}
+
+// 1/sqrt(x) for finite x > 0.  Inside the FP32 exponent range: an FP32
+// estimate built from the top bits by integer operations, then one
+// third-order Newton-Householder step in FP64, y1 = y0 (1 + r/2 + 3 r^2/8)
+// with r = 1 - x y0^2 (relative error O(r^3), far below FP64 rounding for
+// the ~2^-22 error of the estimate).  Outside that range: the library rsqrt.
+__device__ __forceinline__ double rsqrt_fast(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)(b >> 52) & 0x7ff;
+  if (e < 1023 - 120 || e > 1023 + 120) return rsqrt(x);
+  const unsigned fb = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+  const float y0f = rsqrtf(__uint_as_float(fb));
+  const unsigned yb = __float_as_uint(y0f);
+  const long long ye = (long long)(((yb >> 23) & 0xff) - 127 + 1023);
+  const double y0 = __longlong_as_double((ye << 52) | ((long long)(yb & 0x7fffff) << 29));
+  const double h = x * y0;
+  const double r = fma(-h, y0, 1.0);
+  const double q = r * fma(0.375, r, 0.5);
+  return fma(y0, q, y0);
+}
+
+// pivot test on bit patterns: 0 accepted, 1 not above thr (or not positive),
+// 2 not finite; thr >= 0
+__device__ __forceinline__ int pivot_code(double x, double thr) {
+  const long long b = __double_as_longlong(x);
+  if (((b >> 52) & 0x7ff) == 0x7ff) return 2;
+  return (b > __double_as_longlong(thr)) ? 0 : 1;  // negative x: b < 0 <= thr bits
+}
+
+// blockDim.x = 32 NW with NW = 4 (l <= 128) or 8 (l <= 256); l <= kClusterMaxL;
+// ceil(l / C) <= RMAX.  Thread (warp w, lane) holds, of own row i (a_i =
+// rank + i C), the entry in column a_i + 32 ((w - i) mod NW) + lane: each row's
+// 32-wide chunks rotate over the warps, so the FP64 work of a column (one warp
+// instruction per chunk, about 64 clocks of an SMSP's FP64 unit each) is
+// spread evenly over the SM's four schedulers.
+template <int C, int RMAX>
+__global__ void __launch_bounds__(256)
+k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
+               double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless,
+               double again_tol, unsigned long long limit_ns) {
+  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ntri = l * (l + 1) / 2;
+  double *tri = reinterpret_cast<double *>(smraw);  // packed upper triangle
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(tri + ntri);  // [2][l]
+  double *thr = reinterpret_cast<double *>(bars + 2 * l);  // [l] pivot thresholds
+  __shared__ double red[32];
+  __shared__ double s_rs;
+  __shared__ int s_f, s_code;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const unsigned me = cluster_rank();
+  auto off = [l](int j) { return j * l - (j * (j - 1)) / 2; };
+  // column of own row i held by this thread
+  auto col = [&](int i) { return (int)me + i * C + ((((warp - i) & (nw - 1))) << 5) + lane; };
+  const unsigned tri0 = smem_u32(tri), bar0 = smem_u32(bars);
+  unsigned rtri[C], rbar[C];  // this layout in every CTA of the cluster
+#pragma unroll
+  for (int d = 0; d < C; ++d) {
+    rtri[d] = map_shared(tri0, d);
+    rbar[d] = map_shared(bar0, d);
+  }
+
+  for (int i = tid; i < 2 * l; i += blockDim.x) bar_init(bar0 + 8u * i, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  for (int i = tid; i < 2 * l; i += blockDim.x) {
+    const int j = i % l;
+    if ((unsigned)(j % C) != me) bar_expect(bar0 + 8u * i, (unsigned)(l - j) * 8u);
+  }
+  double tr = 0.0;
+  for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
+  tr = block_sum(tr, red);
+  // no CTA sends before every CTA's barriers are initialised and armed
+  cluster_sync_all();
+
+  double v[RMAX];  // v[i] = working entry (a_i, col(i))
+  int fail = 0;
+  for (int att = 0; att < 2; ++att) {
+    const double shift = att ? 11.0 * (rows * l + (double)l * (l + 1)) * kEps * tr : 0.0;
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) {
+      const int a = (int)me + i * C, c = col(i);
+      v[i] = (a < l && c < l) ? G[(int64_t)a * l + c] + (c == a ? shift : 0.0) : 0.0;
+    }
+    for (int a = (int)me + tid * C; a < l; a += (int)blockDim.x * C)
+      thr[a] = (double)l * 2.0 * kEps * (G[(int64_t)a * l + a] + shift);
+    if (tid == 0) s_code = 0;
+    __syncthreads();
+    const unsigned barA = bar0 + 8u * (unsigned)(att * l);
+    // row r of R from its fully updated entries: this thread holds x = (r, cx)
+    auto produce = [&](int r, double x, int cx) {
+      if (cx == r) {
+        int f = pivot_code(x, thr[r]);
+        if (f == 0 && pivot_code(thr[r], 0.0) == 2) f = 2;  // threshold from a non-finite G
+        s_f = f;
+        s_rs = f ? 1.0 : rsqrt_fast(x);
+      }
+      __syncthreads();
+      if (cx < l) {
+        const int f = s_f;
+        double y = x * s_rs;
+        if (cx == r && f) y = -(double)f;
+        const unsigned e8 = 8u * (unsigned)(off(r) + (cx - r)), b8 = 8u * (unsigned)(att * l + r);
+        tri[e8 >> 3] = y;
+#pragma unroll
+        for (int d = 0; d < C; ++d)
+          if ((unsigned)d != me) st_async_f64(rtri[d] + e8, y, rbar[d] + b8);
+      }
+    };
+    if (me == 0) produce(0, v[0], col(0));
+    int j = 0;
+    for (; j < l; ++j) {
+      int code;
+      if ((unsigned)(j % C) != me) {
+        if (!bar_wait_bounded(barA + 8u * j, 0, limit_ns)) {
+          code = 3;
+        } else {
+          const long long bv = __double_as_longlong(tri[off(j)]);
+          code = bv > 0 ? 0 : (bv == __double_as_longlong(-1.0) ? 1 : 2);
+        }
+      } else {
+        code = s_f;
+      }
+      if (code) atomicMax(&s_code, code);
+      if (__syncthreads_or(code != 0)) break;
+      const double *Rj = tri + off(j) - j;  // Rj[t] = R(j, t), t >= j
+      if (j + 1 < l && (unsigned)((j + 1) % C) == me) {
+        const int i1 = (j + 1 - (int)me) / C;
+        double w = 0.0;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i)
+          if (i == i1) w = v[i];
+        const int c1 = col(i1);
+        produce(j + 1, c1 < l ? fma(-Rj[j + 1], Rj[c1], w) : 0.0, c1);
+      }
+      // own rows a >= j + 2; a warp skips rows where its chunk is empty
+#pragma unroll
+      for (int i = 0; i < RMAX; ++i) {
+        const int a = (int)me + i * C;
+        if (a >= j + 2 && a < l && ((((warp - i) & (nw - 1))) << 5) < l - a) {
+          const int c = col(i);
+          if (c < l) v[i] = fma(-Rj[a], Rj[c], v[i]);
+        }
+      }
+    }
+    fail = (j < l) ? s_code : 0;
+    if (fail == 1 && att == 0) {
+      if (me == 0 && tid == 0) {
+        ctrl->shift_flag[site] = 1;
+        set_status(ctrl, RQLP_WARN_SHIFTED_CHOLQR);
+      }
+      cluster_sync_all();  // every CTA has left the first attempt
+      continue;
+    }
+    break;
+  }
+  if (me == 0 && tid == 0) {
+    if (fail == 2) set_status(ctrl, RQLP_ERR_NONFINITE);
+    else if (fail == 1) set_status(ctrl, RQLP_ERR_RANK_DEFICIENT);
+  }
+  if (fail == 3 && tid == 0) {
+    set_status(ctrl, RQLP_ERR_TIMEOUT);
+    atomicExch(&ctrl->timeout_site, 200 + site);
+  }
+  __syncthreads();
+  // own rows of R, zeros below the diagonal
+  for (int a = (int)me; a < l; a += C)
+    for (int t = tid; t < l; t += blockDim.x)
+      R[(int64_t)a * l + t] = t >= a ? tri[off(a) + t - a] : 0.0;
+  // a second pass is needed when eps * cond(R)^2 exceeds again_tol (cond
+  // estimated from diag(R)), as in the single-CTA kernel
+  if (again_tol >= 0.0 && me == 0 && warp == 0) {
+    double mx = 0.0, mn = 1e300;
+    for (int i = lane; i < l; i += 32) {
+      const double d = tri[off(i)];
+      mx = fmax(mx, d);
+      mn = fmin(mn, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if (lane == 0) {
+      const double cn = (mn > 0.0) ? mx / mn : 1e300;
+      const int again = (fail != 0) || !(2.0 * kEps * cn * cn <= again_tol);
+      ctrl->again_flag[site] = again;
+      ctrl->done_flag[site] = 1 - again;
+    }
+  }
+  // inverses of the 16 x 16 diagonal blocks, block bk on CTA bk % C: lane
+  // cc solves U x = e_cc by back substitution with the reciprocals of U's
+  // diagonal taken once
+  const int nblk = (l + kB - 1) / kB;
+  for (int bk = (int)me + C * warp; bk < nblk; bk += C * nw) {
+    const int c0 = bk * kB, bs = min(kB, l - c0);
+    const int cc = lane;
+    auto U = [&](int i, int t) { return tri[off(c0 + i) + (t - i)]; };  // t >= i
+    const double dl = (lane < bs) ? 1.0 / U(lane, lane) : 0.0;
+    double x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) x[i] = 0.0;
+#pragma unroll
+    for (int i = kB - 1; i >= 0; --i) {
+      const double di = __shfl_sync(0xffffffffu, dl, i);
+      if (i < bs && cc < bs && i <= cc) {
+        double s = (i == cc) ? 1.0 : 0.0;
+#pragma unroll
+        for (int t = i + 1; t < kB; ++t)
+          if (t <= cc && t < bs) s = fma(-U(i, t), x[t], s);
+        x[i] = s * di;
+      }
+    }
+    if (cc < bs)
+#pragma unroll
+      for (int i = 0; i < kB; ++i)
+        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = x[i];
+  }
+  // no CTA leaves while another may still send to it
+  cluster_sync_all();
+}
+
+size_t chol_cluster_smem(int l) {
+  return (size_t)l * (l + 1) / 2 * sizeof(double) + 2 * (size_t)l * 8 + (size_t)l * sizeof(double);
+}
+
+template <int C, int RMAX>
+cudaError_t launch_chol_cluster(const double *G, int l, int64_t rows, double *R, double *Dinv,
+                                Ctrl *ctrl, int site, const int *skip_unless, cudaStream_t st,
+                                double again_tol) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(l <= 128 ? 128 : 256);
+  cfg.dynamicSmemBytes = chol_cluster_smem(l);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_cluster<C, RMAX>, G, l, (double)rows, R,
+                                           Dinv, ctrl, site, skip_unless, again_tol,
+                                           (unsigned long long)kDefaultSpinNs);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int C, int RMAX>
+cudaError_t chol_cluster_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<C, RMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)chol_cluster_smem(kClusterMaxL));
+  if (e == cudaSuccess && C > 8)
+    e = cudaFuncSetAttribute(k_chol_cluster<C, RMAX>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// kernel attributes of the cluster Cholesky (once) and the cluster size it
+// uses by default: 16 CTAs where a 16-CTA cluster of it fits, else 8
+int chol_cluster_init() {
+  static int best = 0;
+  if (best == 0) {
+    if (chol_cluster_attr<8, 16>() != cudaSuccess || chol_cluster_attr<8, 28>() != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    best = 8;
+    if (chol_cluster_attr<16, 8>() == cudaSuccess && chol_cluster_attr<16, 14>() == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = chol_cluster_smem(kClusterMaxL);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_chol_cluster<16, 14>, &cfg) == cudaSuccess && n > 0)
+        best = 16;
+    }
+    cudaGetLastError();
+  }
+  return best;
+}
+
 constexpr int kApplyRows = 32;
 constexpr int kApplyThreads = 128;
 
@@ -337,6 +702,7 @@ cudaError_t cholqr_init() {
                              200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_apply_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess && chol_cluster_init() < 0) e = cudaErrorInvalidValue;
   return e;
 }
 
@@ -366,6 +732,19 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
 
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st, double again_tol) {
+  const int best = chol_cluster_init();
+  if (best < 0) return cudaErrorInvalidValue;
+  const int cc = l > kClusterMaxL ? 1 : (tuning().chol_ctas > 0 ? tuning().chol_ctas : best);
+  if (cc == 16)
+    return l <= 128 ? launch_chol_cluster<16, 8>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
+                                                 again_tol)
+                    : launch_chol_cluster<16, 14>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
+                                                  again_tol);
+  if (cc == 8)
+    return l <= 128 ? launch_chol_cluster<8, 16>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
+                                                 again_tol)
+                    : launch_chol_cluster<8, 28>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
+                                                 again_tol);
   const size_t smem = (size_t)l * l * sizeof(double);
   const bool use_smem = smem <= 200 * 1024;
   static bool attr = false;
