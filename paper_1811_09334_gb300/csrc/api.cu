@@ -53,7 +53,7 @@ size_t part_doubles(int64_t m, int64_t n, int l) {
 void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBufs &o,
                 double *shared_part) {
   o.part = shared_part ? shared_part : a.take<double>(part_doubles(m, n, l));
-  o.gpart = a.take<double>((size_t)gram_chunks(std::max<int64_t>(rows_max, l)) * l * l);
+  o.gpart = a.take<double>((size_t)gram_chunks_max(std::max<int64_t>(rows_max, l)) * l * l);
   o.Dinv = a.take<double>((size_t)l * l);
   o.G = a.take<double>((size_t)l * l);
   o.Rp = a.take<double>((size_t)l * l);

@@ -34,22 +34,22 @@ namespace {
 
 constexpr double kEps = 1.1102230246251565e-16;
 constexpr int kB = 16;       // block size of the Cholesky and the solve
-constexpr int kGramRows = 32;
+constexpr int kGramMaxRows = 32;  // rows of X per Gram chunk, at most
 constexpr int kGramThreads = 256;
 
-// Upper triangle of X_c^T X_c for the rows of chunk c = blockIdx.x, into
+// Upper triangle of X_c^T X_c for the rc rows of chunk c = blockIdx.x, into
 // part[c] (l x l, only j >= i written).  Tiles of 4 x 4 over the triangle.
 __global__ void __launch_bounds__(kGramThreads)
-k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
+k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int rc,
            double *__restrict__ part, const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  extern __shared__ double xs[];  // [kGramRows][lp]
+  extern __shared__ double xs[];  // [rc][lp]
   const int lp = ((l + 3) / 4) * 4 + 1;
-  const int64_t r0 = (int64_t)blockIdx.x * kGramRows;
-  const int nr = (int)min((int64_t)kGramRows, rows - r0);
-  for (int e = threadIdx.x; e < kGramRows * lp; e += blockDim.x) {
+  const int64_t r0 = (int64_t)blockIdx.x * rc;
+  const int nr = (int)min((int64_t)rc, rows - r0);
+  for (int e = threadIdx.x; e < nr * lp; e += blockDim.x) {
     const int r = e / lp, c = e - r * lp;
-    xs[e] = (r < nr && c < l) ? X[(r0 + r) * ldx + c] : 0.0;
+    xs[e] = (c < l) ? X[(r0 + r) * ldx + c] : 0.0;
   }
   __syncthreads();
   const int nb = (l + 3) / 4;
@@ -68,7 +68,7 @@ k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-    for (int r = 0; r < kGramRows; ++r) {
+    for (int r = 0; r < nr; ++r) {
       const double *row = xs + r * lp;
       double x[4], y[4];
 #pragma unroll
@@ -327,26 +327,6 @@ __device__ __forceinline__ void st_async_f64(unsigned raddr, double v, unsigned 
                    raddr),
                "d"(v), "r"(rbar)
                : "memory");
-}
-
-// 1/sqrt(x) for finite x > 0.  Inside the FP32 exponent range: an FP32
-// estimate built from the top bits by integer operations, then one
-// third-order Newton-Householder step in FP64, y1 = y0 (1 + r/2 + 3 r^2/8)
-// with r = 1 - x y0^2 (relative error O(r^3), far below FP64 rounding for
-// the ~2^-22 error of the estimate).  Outside that range: the library rsqrt.
-__device__ __forceinline__ double rsqrt_fast(double x) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)(b >> 52) & 0x7ff;
-  if (e < 1023 - 120 || e > 1023 + 120) return rsqrt(x);
-  const unsigned fb = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
-  const float y0f = rsqrtf(__uint_as_float(fb));
-  const unsigned yb = __float_as_uint(y0f);
-  const long long ye = (long long)(((yb >> 23) & 0xff) - 127 + 1023);
-  const double y0 = __longlong_as_double((ye << 52) | ((long long)(yb & 0x7fffff) << 29));
-  const double h = x * y0;
-  const double r = fma(-h, y0, 1.0);
-  const double q = r * fma(0.375, r, 0.5);
-  return fma(y0, q, y0);
 }
 
 // pivot test on bit patterns: 0 accepted, 1 not above thr (or not positive),
@@ -639,8 +619,10 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     const int r = e / l, c = e - r * l;
     qs[r * lp + c] = (r < nr) ? X[(r0 + r) * ldx + c] : 0.0;
   }
-  // thread -> (row r, 4 columns j0..j0+3 of the block)
-  const int r = threadIdx.x >> 2, j0 = (threadIdx.x & 3) * 4;
+  // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
+  // warp needs the same rows of inv(R[b, b]), so the triangular product
+  // stops at row j0 + 3 for the whole warp
+  const int r = threadIdx.x & 31, j0 = (threadIdx.x >> 5) * 4;
   for (int c0 = 0; c0 < l; c0 += kB) {
     const int bs = min(kB, l - c0);
     __syncthreads();
@@ -668,7 +650,8 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
       if (j0 + a < bs) qs[r * lp + c0 + j0 + a] = acc[a];
     __syncthreads();
     double out[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = 0; i < bs; ++i) {
+    const int iend = min(bs, j0 + 4);  // inv(R[b, b]) is upper triangular
+    for (int i = 0; i < iend; ++i) {
       const double v = qs[r * lp + c0 + i];
 #pragma unroll
       for (int a = 0; a < 4; ++a) out[a] = fma(v, dv[i * kB + j0 + a], out[a]);
@@ -706,13 +689,30 @@ cudaError_t cholqr_init() {
   return e;
 }
 
-int64_t gram_chunks(int64_t rows) { return (rows + kGramRows - 1) / kGramRows; }
+// Rows per Gram chunk: two chunks per SM where that gives 8..32 rows, so
+// that every SM gets the same number of rows (no partial second wave).
+int gram_rows_per_chunk(int64_t rows) {
+  const int64_t target = 2LL * num_sms();
+  const int64_t r = (rows + target - 1) / target;
+  return (int)std::max<int64_t>(8, std::min<int64_t>(kGramMaxRows, r));
+}
+
+int64_t gram_chunks(int64_t rows) {
+  const int rc = gram_rows_per_chunk(rows);
+  return (rows + rc - 1) / rc;
+}
+
+// bound on gram_chunks(r) for every r <= rows_max
+int64_t gram_chunks_max(int64_t rows_max) {
+  return std::max<int64_t>(2LL * num_sms(), (rows_max + kGramMaxRows - 1) / kGramMaxRows);
+}
 
 cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *part, double *G,
                      const int *skip_unless, cudaStream_t st) {
+  const int rc = gram_rows_per_chunk(rows);
   const int64_t chunks = gram_chunks(rows);
   const int lp = ((l + 3) / 4) * 4 + 1;
-  const size_t smem = (size_t)kGramRows * lp * sizeof(double);
+  const size_t smem = (size_t)rc * lp * sizeof(double);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -720,7 +720,7 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gram_sym<<<(unsigned)chunks, kGramThreads, smem, st>>>(X, rows, l, ldx, part, skip_unless);
+  k_gram_sym<<<(unsigned)chunks, kGramThreads, smem, st>>>(X, rows, l, ldx, rc, part, skip_unless);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

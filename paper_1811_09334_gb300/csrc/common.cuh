@@ -17,7 +17,8 @@ struct Ctrl {
   unsigned bar_count;       // grid barrier: arrivals in the current generation
   unsigned bar_gen;         // grid barrier: generation counter
   int timeout_site;         // diagnostics: which wait gave up
-  int pad[13];
+  unsigned cpqr_arrive;     // CPQR grid barriers: arrivals since the launch began
+  int pad[12];
   int again_flag[16];       // per CholeskyQR site: 1 when a second pass is needed
   int done_flag[16];        // per CholeskyQR site: 1 when one pass was enough
 };
@@ -92,6 +93,48 @@ __device__ inline bool grid_barrier(Ctrl *c, unsigned nblocks, unsigned long lon
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Reciprocal and reciprocal square root for finite x != 0 (x > 0 for the
+// square root) with few dependent FP64 operations, which on this GPU cost
+// about 64 clocks each: an FP32 estimate from the top bits of x (integer
+// operations and one MUFU instruction, ~2^-22 relative error), then one
+// third-order Newton step in FP64, whose error O(e^3) lies below FP64
+// rounding.  Outside the FP32 exponent range the plain FP64 operation is used.
+__device__ __forceinline__ bool fp32_range(long long b) {
+  const int e = (int)(b >> 52) & 0x7ff;
+  return e > 1023 - 120 && e < 1023 + 120;
+}
+__device__ __forceinline__ float top_as_float(long long b) {
+  const int e = (int)(b >> 52) & 0x7ff;
+  const unsigned f = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23) |
+                     (unsigned)((b >> 29) & 0x7fffff);
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double float_as_double_bits(float y) {
+  const unsigned u = __float_as_uint(y);
+  const long long e = (long long)((u >> 23) & 0xff) - 127 + 1023;
+  return __longlong_as_double(((long long)(u & 0x80000000u) << 32) | (e << 52) |
+                              ((long long)(u & 0x7fffff) << 29));
+}
+__device__ __forceinline__ double rcp_fast(double x) {
+  const long long b = __double_as_longlong(x);
+  if (!fp32_range(b)) return 1.0 / x;
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(top_as_float(b)));
+  const double y0 = float_as_double_bits(yf);
+  const double e = fma(-x, y0, 1.0);  // 1 - x y0
+  return fma(y0, fma(e, e, e), y0);   // y0 (1 + e + e^2)
+}
+__device__ __forceinline__ double rsqrt_fast(double x) {
+  const long long b = __double_as_longlong(x);
+  if (!fp32_range(b)) return rsqrt(x);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(top_as_float(b)));
+  const double y0 = float_as_double_bits(yf);
+  const double h = x * y0;
+  const double r = fma(-h, y0, 1.0);                // 1 - x y0^2
+  return fma(y0, r * fma(0.375, r, 0.5), y0);       // y0 (1 + r/2 + 3 r^2 / 8)
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -39,8 +39,8 @@ struct CpqrParams {
   int32_t *piv;
   double *Vh;
   double *tau;
-  double *cand_norm;  // [2][G]
-  int32_t *cand_idx;  // [2][G]
+  double2 *cand;      // [2][G] (norm^2, index as a 64-bit integer)
+  int2 *win;          // [2] (CTA, index) of the winner picked by the last arriver
   double *pcol;       // [2][G][l]
   int32_t *counts;    // [G]
   double *gcols;      // G * cpb * l when the slab does not fit in shared memory
@@ -62,10 +62,55 @@ __device__ __forceinline__ bool better(double na, int ia, double nb, int ib) {
   return ia < ib;
 }
 
+// (norm, index) of the better of this lane's pair and its xor partners'
+__device__ __forceinline__ void warp_best(double &bn, int &bi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (better(on, oi, bn, bi)) { bn = on; bi = oi; }
+  }
+}
+
+// Grid barriers count arrivals on one counter that the host zeroes before
+// every launch.  A step barrier takes G + 1 increments: the G-th arriver
+// (it sees G - 1 earlier arrivals) reads the whole candidate table, picks the
+// winner, publishes it and adds the last increment, so the other CTAs read
+// one record instead of the table.  Every wait is bounded by limit_ns; an
+// error recorded by another CTA ends it.  `extra` (only the timeout test sets
+// it) makes the first wait need arrivals that never come.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// lane-0 wait until the counter reaches target; false on timeout or error
+__device__ __forceinline__ bool wait_count(Ctrl *c, unsigned target, unsigned long long limit_ns,
+                                           int site) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0; (int)(ld_acquire_u32(&c->cpqr_arrive) - target) < 0; ++it) {
+    if ((it & 15) == 15) {
+      if (ld_volatile_i32(&c->status) < 0) return false;
+      const unsigned long long t = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > limit_ns) {
+        set_status(c, RQLP_ERR_TIMEOUT);
+        atomicExch(&c->timeout_site, site);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   extern __shared__ double sm[];
   __shared__ double red[32];
-  __shared__ double s_v[kMaxL];
+  __shared__ double s_v[kMaxL], s_vt[kMaxL];
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
@@ -77,8 +122,85 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   const int nc = (int)max((int64_t)0, min(P.n, c0 + P.cpb) - c0);
   double *cols = P.use_smem ? sm : P.gcols + (int64_t)b * P.cpb * l;
   double *nrm = P.use_smem ? sm + (int64_t)P.cpb * l : reinterpret_cast<double *>(sm);
-  double *nrm0 = nrm + P.cpb;  // norm^2 when last computed exactly
-  int *pivoted = reinterpret_cast<int *>(nrm0 + P.cpb);
+  // 1% of the norm^2 when it was last computed exactly: below that the
+  // downdated value has lost too many digits and is recomputed
+  double *thr = nrm + P.cpb;
+  int *pivoted = reinterpret_cast<int *>(thr + P.cpb);
+  __shared__ int s_ok;
+  unsigned nsteps = 0;  // step barriers passed
+  // step barrier: afterwards s_win_cta / s_win_idx name the winner of slot buf
+  auto step_sync = [&](int buf, int site) {
+    ++nsteps;
+    const unsigned done = nsteps * (unsigned)(G + 1);
+    __syncthreads();
+    if (warp == 0) {
+      unsigned old = 0;
+      if (lane == 0) old = atom_add_acq_rel(&P.ctrl->cpqr_arrive, 1u);
+      old = __shfl_sync(0xffffffffu, old, 0);
+      __syncwarp();
+      if (old == done - 2u) {
+        // the last arriver: every candidate of this step is in the table
+        double bn = -1.0;
+        int bi = -1, bc = -1;
+        if (G <= 160) {
+          double2 e[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const int c = lane + 32 * k;
+            e[k] = c < G ? __ldcg(P.cand + buf * G + c)
+                         : make_double2(-1.0, __longlong_as_double(-1LL));
+          }
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const int ci = (int)__double_as_longlong(e[k].y);
+            if (better(e[k].x, ci, bn, bi)) { bn = e[k].x; bi = ci; bc = lane + 32 * k; }
+          }
+        } else {
+          for (int c = lane; c < G; c += 32) {
+            const double2 e = __ldcg(P.cand + buf * G + c);
+            const int ci = (int)__double_as_longlong(e.y);
+            if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+          if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
+        }
+        if (lane == 0) {
+          P.win[buf] = make_int2(bc, bi);
+          red_add_release(&P.ctrl->cpqr_arrive, 1u);
+        }
+      }
+      if (lane == 0) {
+        const bool ok = wait_count(P.ctrl, done + P.extra, P.limit_ns, site);
+        s_ok = ok;
+        if (ok) {
+          const int2 w = __ldcg(P.win + buf);
+          s_win_cta = w.x;
+          s_win_idx = w.y;
+        }
+      }
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+  // plain barrier after the last step
+  auto final_sync = [&](int site) {
+    __syncthreads();
+    if (tid == 0) {
+      red_add_release(&P.ctrl->cpqr_arrive, 1u);
+      s_ok = wait_count(P.ctrl, nsteps * (unsigned)(G + 1) + (unsigned)G + P.extra, P.limit_ns,
+                        site);
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+
+  // nothing to do after an earlier error (its data may be garbage)
+  if (ld_volatile_i32(&P.ctrl->status) < 0) return;
 
   // ---- load the slab, exact initial norms ------------------------------
   for (int jj = warp; jj < nc; jj += kWarps) {
@@ -92,37 +214,23 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     s = warp_sum(s);
     if (lane == 0) {
       nrm[jj] = s;
-      nrm0[jj] = s;
+      thr[jj] = 0.01 * s;
       pivoted[jj] = 0;
       if (!isfinite(s)) set_status(P.ctrl, RQLP_ERR_NONFINITE);
     }
   }
   __syncthreads();
 
-  // local best candidate -> table slot `buf`
-  auto publish = [&](int buf, int from_row) {
-    double bn = -1.0;
-    int bi = -1;
-    for (int jj = tid; jj < nc; jj += kThreads) {
-      if (pivoted[jj]) continue;
-      const int idx = (int)(c0 + jj);
-      if (better(nrm[jj], idx, bn, bi)) { bn = nrm[jj]; bi = idx; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double on = __shfl_xor_sync(0xffffffffu, bn, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (better(on, oi, bn, bi)) { bn = on; bi = oi; }
-    }
-    if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
-    __syncthreads();
+  // this CTA's candidate (the per-warp bests in s_bn / s_bi) -> table slot
+  // `buf`, and its column from row from_row on
+  auto publish_best = [&](int buf, int from_row) {
     if (tid == 0) {
       double cn = -1.0;
       int ci = -1;
       for (int w = 0; w < kWarps; ++w)
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
       s_win_idx = ci;
-      P.cand_norm[buf * G + b] = cn;
-      P.cand_idx[buf * G + b] = ci;
+      P.cand[buf * G + b] = make_double2(cn, __longlong_as_double((long long)ci));
     }
     __syncthreads();
     const int ci = s_win_idx;
@@ -133,29 +241,21 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     }
   };
 
-  publish(0, 0);
-  if (!grid_barrier(P.ctrl, G, P.limit_ns, P.extra, 1)) return;
+  {
+    double bn = -1.0;
+    int bi = -1;
+    for (int jj = tid; jj < nc; jj += kThreads)
+      if (better(nrm[jj], (int)(c0 + jj), bn, bi)) { bn = nrm[jj]; bi = (int)(c0 + jj); }
+    warp_best(bn, bi);
+    if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
+    __syncthreads();
+    publish_best(0, 0);
+  }
+  if (!step_sync(0, 1)) return;
 
   for (int s = 0; s < l; ++s) {
     const int buf = s & 1;
-    // ---- 1. winner ----
-    if (warp == 0) {
-      double bn = -1.0;
-      int bi = -1, bc = -1;
-      for (int c = lane; c < G; c += 32) {
-        const double cn = __ldcg(P.cand_norm + buf * G + c);
-        const int ci = __ldcg(P.cand_idx + buf * G + c);
-        if (better(cn, ci, bn, bi)) { bn = cn; bi = ci; bc = c; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double on = __shfl_xor_sync(0xffffffffu, bn, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
-      }
-      if (lane == 0) { s_win_cta = bc; s_win_idx = bi; }
-    }
-    __syncthreads();
+    // ---- 1. winner: picked by the last CTA to arrive at the barrier ----
     const int wc = s_win_cta, wi = s_win_idx;
     if (wi < 0) { if (tid == 0) set_status(P.ctrl, RQLP_ERR_INVALID_ARG); return; }
     // ---- 2. reflector from the winner's column, rows s..l-1 ----
@@ -167,7 +267,9 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       if (r > s) part = fma(v, v, part);
     }
     const double sigma = block_sum(part, red);  // includes a __syncthreads
-    // one thread forms the reflector (FP64 sqrt and divisions are costly here)
+    // one thread forms H = I - tau v v^T with v(0) = 1 and H x = alpha e_1,
+    // alpha = ||x|| >= 0: tau = 1 - x0/alpha, v(1:) = x(1:) / (x0 - alpha),
+    // where x0 > 0 uses x0 - alpha = -sigma / (x0 + alpha) (no cancellation)
     if (tid == 0) {
       const double x0 = s_v[0];
       double tau, beta, rv0;
@@ -176,11 +278,19 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
         else { tau = 2.0; beta = -x0; }
         rv0 = 0.0;
       } else {
-        const double alpha = sqrt(fma(x0, x0, sigma));
-        const double v0 = (x0 <= 0.0) ? (x0 - alpha) : (-sigma / (x0 + alpha));
-        tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        const double isig = rcp_fast(sigma);
+        const double n2 = fma(x0, x0, sigma);
+        const double ra = rsqrt_fast(n2);  // 1 / alpha
+        const double alpha = n2 * ra;
+        if (x0 <= 0.0) {
+          rv0 = rcp_fast(x0 - alpha);
+          tau = fma(-x0, ra, 1.0);
+        } else {
+          const double t = x0 + alpha;
+          rv0 = -t * isig;
+          tau = (sigma * ra) * rcp_fast(t);
+        }
         beta = alpha;
-        rv0 = 1.0 / v0;
       }
       s_tau = tau;
       s_beta = beta;
@@ -188,9 +298,11 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     }
     __syncthreads();
     const double tau = s_tau, beta = s_beta, rv0 = s_rv0;
-    for (int r = 1 + tid; r < l - s; r += kThreads) s_v[r] *= rv0;
-    __syncthreads();
-    if (tid == 0) s_v[0] = 1.0;
+    for (int r = tid; r < l - s; r += kThreads) {
+      const double v = r == 0 ? 1.0 : s_v[r] * rv0;
+      s_v[r] = v;
+      s_vt[r] = tau * v;
+    }
     __syncthreads();
     if (b == 0) {
       for (int r = tid; r < l; r += kThreads) P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : s_v[r - s];
@@ -205,57 +317,87 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       for (int r = lane; r < l; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
       if (lane == 0) { pivoted[jw] = 1; nrm[jw] = -1.0; }
     }
-    // groups of 8 lanes per column, four columns per warp: the dot product
-    // needs a 3-level reduction, and each FP64 warp instruction works on four
-    // columns at once
+    // groups of 8 lanes per column, four columns per warp and two column
+    // sets per pass (independent chains): dot product with v, axpy with
+    // tau v, the downdated trailing norm (recomputed exactly when more than
+    // 99% of it has cancelled since the last exact value), and this warp's
+    // best candidate for step s + 1
+    double bn = -1.0;
+    int bi = -1;
     {
       const int sub = lane >> 3, gl = lane & 7;
-      for (int jb = warp * 4; jb < nc; jb += kWarps * 4) {
-        const int jj = jb + sub;
-        const bool act = jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi;
-        double *col = cols + (int64_t)(act ? jj : 0) * l;
-        double w = 0.0;
-        if (act && tau != 0.0)
-          for (int r = s + gl; r < l; r += 8) w = fma(s_v[r - s], col[r], w);
-        w += __shfl_xor_sync(0xffffffffu, w, 4);
-        w += __shfl_xor_sync(0xffffffffu, w, 2);
-        w += __shfl_xor_sync(0xffffffffu, w, 1);
-        if (act && tau != 0.0) {
-          w *= tau;
-          for (int r = s + gl; r < l; r += 8) col[r] = fma(-w, s_v[r - s], col[r]);
+      for (int jb = warp * 4; jb < nc; jb += kWarps * 8) {
+        int jj[2];
+        bool act[2];
+        double *col[2];
+        double w[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          jj[k] = jb + 32 * k + sub;
+          act[k] = jj[k] < nc && !pivoted[jj[k]] && (int)(c0 + jj[k]) != wi;
+          col[k] = cols + (int64_t)(act[k] ? jj[k] : 0) * l;
+          double a0 = 0.0, a1 = 0.0;
+          if (act[k]) {
+            int r = s + gl;
+            for (; r + 8 < l; r += 16) {
+              a0 = fma(s_v[r - s], col[k][r], a0);
+              a1 = fma(s_v[r + 8 - s], col[k][r + 8], a1);
+            }
+            if (r < l) a0 = fma(s_v[r - s], col[k][r], a0);
+          }
+          w[k] = a0 + a1;
         }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+          w[1] += __shfl_xor_sync(0xffffffffu, w[1], o);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (act[k])
+            for (int r = s + gl; r < l; r += 8) col[k][r] = fma(-w[k], s_vt[r - s], col[k][r]);
         __syncwarp();
-        // norm downdating: ||col(s+1:)||^2 = ||col(s:)||^2 - col(s)^2 (the
-        // reflector preserves ||col(s:)||); recomputed exactly when more than
-        // 99% of the norm has cancelled since the last exact value
-        int need = 0;
-        double nd = 0.0;
-        if (act && gl == 0) {
-          const double rsv = col[s];
-          nd = nrm[jj] - rsv * rsv;
-          need = !(nd > 0.01 * nrm0[jj]);
+        int need[2];
+        double nd[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          need[k] = 0;
+          nd[k] = 0.0;
+          if (act[k] && gl == 0) {
+            const double rsv = col[k][s];
+            nd[k] = fma(-rsv, rsv, nrm[jj[k]]);
+            need[k] = __double_as_longlong(nd[k]) <= __double_as_longlong(thr[jj[k]]);
+          }
+          need[k] = __shfl_sync(0xffffffffu, need[k], lane & ~7);
         }
-        need = __shfl_sync(0xffffffffu, need, lane & ~7);
-        double t = 0.0;
-        if (need)
-          for (int r = s + 1 + gl; r < l; r += 8) t = fma(col[r], col[r], t);
-        t += __shfl_xor_sync(0xffffffffu, t, 4);
-        t += __shfl_xor_sync(0xffffffffu, t, 2);
-        t += __shfl_xor_sync(0xffffffffu, t, 1);
-        if (act && gl == 0) {
-          if (need) {
-            nrm[jj] = t;
-            nrm0[jj] = t;
-          } else {
-            nrm[jj] = nd;
+        // warp-uniform branch: the shuffles inside need every lane
+        if (__any_sync(0xffffffffu, need[0] | need[1])) {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            double t = 0.0;
+            if (need[k])
+              for (int r = s + 1 + gl; r < l; r += 8) t = fma(col[k][r], col[k][r], t);
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            if (need[k]) nd[k] = t;
           }
         }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (act[k] && gl == 0) {
+            nrm[jj[k]] = nd[k];
+            if (need[k]) thr[jj[k]] = 0.01 * nd[k];
+            if (better(nd[k], (int)(c0 + jj[k]), bn, bi)) { bn = nd[k]; bi = (int)(c0 + jj[k]); }
+          }
       }
     }
-    __syncthreads();
     if (s + 1 < l) {
-      publish(buf ^ 1, s + 1);
-      if (!grid_barrier(P.ctrl, G, P.limit_ns, 0, 2)) return;
+      warp_best(bn, bi);
+      if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
+      __syncthreads();
+      publish_best(buf ^ 1, s + 1);
+      if (!step_sync(buf ^ 1, 2)) return;
     }
   }
 
@@ -265,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     for (int jj = 0; jj < nc; ++jj) mine += pivoted[jj] ? 0 : 1;
     P.counts[b] = mine;
   }
-  if (!grid_barrier(P.ctrl, G, P.limit_ns, 0, 3)) return;
+  if (!final_sync(3)) return;
   __shared__ int s_prefix;
   if (tid == 0) {
     int pre = 0;
@@ -281,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const int un = (jj < nc && !pivoted[jj]) ? 1 : 0;
       const unsigned mask = __ballot_sync(0xffffffffu, un);
       const int rank = __popc(mask & ((1u << lane) - 1u));
-      if (un) {
+      if (un && pos + rank < P.n) {
         P.piv[pos + rank] = (int32_t)(c0 + jj);
         pivoted[jj] = -(pos + rank) - 1;  // remember the destination row
       }
@@ -293,6 +435,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     const int code = pivoted[jj];
     if (code >= 0) continue;
     const int64_t dst = -(int64_t)code - 1;
+    if (dst >= P.n) continue;
     const double *col = cols + (int64_t)jj * l;
     for (int r = lane; r < l; r += 32) P.R0t[dst * P.ldr + r] = col[r];
   }
@@ -325,8 +468,8 @@ Plan plan_for(int64_t n, int l) {
 size_t cpqr_ws_bytes(int64_t n, int l) {
   const size_t G = kMaxGrid;
   size_t b = 0;
-  b += 2 * G * sizeof(double);
-  b += 2 * G * sizeof(int32_t);
+  b += 2 * G * sizeof(double2);
+  b += 256;  // winner records
   b += 2 * G * (size_t)l * sizeof(double);
   b += G * sizeof(int32_t);
   b += (size_t)(n + kMaxGrid) * l * sizeof(double);  // global slabs (fallback)
@@ -337,7 +480,7 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   const Plan pl = plan_for(n, l);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(2 * (size_t)pl.G * sizeof(double)) + up(2 * (size_t)pl.G * sizeof(int32_t)) +
+  return up(2 * (size_t)pl.G * sizeof(double2)) + up(2 * sizeof(int2)) +
          up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
 }
 
@@ -362,8 +505,8 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   CpqrParams P;
   P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
-  P.cand_norm = reinterpret_cast<double *>(take(2 * (size_t)pl.G * sizeof(double)));
-  P.cand_idx = reinterpret_cast<int32_t *>(take(2 * (size_t)pl.G * sizeof(int32_t)));
+  P.cand = reinterpret_cast<double2 *>(take(2 * (size_t)pl.G * sizeof(double2)));
+  P.win = reinterpret_cast<int2 *>(take(2 * sizeof(int2)));
   P.pcol = reinterpret_cast<double *>(take(2 * (size_t)pl.G * l * sizeof(double)));
   P.counts = reinterpret_cast<int32_t *>(take((size_t)pl.G * sizeof(int32_t)));
   P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));
@@ -374,6 +517,9 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   P.use_smem = pl.use_smem;
   // the permutation stays valid even if the kernel stops early on an error
   e = iota(piv, n, st);
+  if (e != cudaSuccess) return e;
+  // barrier counter of this launch
+  e = cudaMemsetAsync(&ctrl->cpqr_arrive, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   if (pl.G == 1) {
     // one CTA: its grid barrier never waits, no co-residency is needed

@@ -114,8 +114,10 @@ cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t row
 
 // ---- cholqr.cu: one CholeskyQR pass on a rows x l panel -------------------
 int64_t gram_chunks(int64_t rows);
+int64_t gram_chunks_max(int64_t rows_max);  // >= gram_chunks(r) for every r <= rows_max
 cudaError_t cholqr_init();  // kernel attributes, set before any stream capture
-// G = X^T X (symmetric, l x l, ld l); part: gram_chunks(rows) * l * l doubles
+// G = X^T X (symmetric, l x l, ld l); part: gram_chunks(rows) * l * l doubles (at most
+// gram_chunks_max of the largest rows)
 cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *part, double *G,
                      const int *skip_unless, cudaStream_t st);
 // G = R^T R (R upper, ld l) with shifted retry; Dinv: inverses of R's 16 x 16
