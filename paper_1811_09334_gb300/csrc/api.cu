@@ -64,23 +64,28 @@ void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBuf
 }
 
 // CholeskyQR2 (+ a third pass iff a pass needed the shift): Xq = X R^{-1}.
+// lowp_first: the first pass in FP32 (Gram and solve; the Cholesky stays FP64
+// with FP32's unit roundoff in its breakdown test and shift), then, when
+// passes >= 2, an FP64 pass always follows: Q is FP64-orthonormal and spans
+// range(X) to about FP32 accuracy.
 int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
               const OrthBufs &o, Ctrl *ctrl, int site, int passes, double again_tol,
-              cudaStream_t st) {
+              cudaStream_t st, bool lowp_first) {
   site %= kShiftSites;
   const int *flag = &ctrl->shift_flag[site];
   int ev;
   // one CholeskyQR pass: src -> dst, R_acc <- R_pass R_acc (skip: conditional pass)
   auto pass = [&](const double *src, int64_t lds, double *dst, int64_t ldd, bool first,
-                  const int *skip, double tol) -> int {
+                  const int *skip, double tol, bool lowp = false) -> int {
     ev = prof_start(kProfGram, st);
-    CK(gram_sym(src, rows, l, lds, o.gpart, o.G, skip, st));
+    CK(gram_sym(src, rows, l, lds, o.gpart, o.G, skip, st, lowp));
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
-    CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol));
+    CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol,
+                    lowp ? kEpsF32 : kEpsF64));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
-    CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st));
+    CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp));
     if (R) {
       if (first) {
         CK(copy2d(o.Rp, l, l, l, o.Racc, l, skip, st));
@@ -94,7 +99,14 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     return RQLP_OK;
   };
   int r;
-  if (passes >= 2 && again_tol >= 0.0) {
+  if (lowp_first && passes >= 2) {
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0, true);  // FP32 pass: X -> tmp
+    if (r != RQLP_OK) return r;
+    r = pass(o.tmp, l, Xq, ldq, false, nullptr, -1.0);      // FP64 pass: tmp -> Xq
+  } else if (lowp_first) {
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0, true);  // one FP32 pass
+    if (r == RQLP_OK) CK(copy2d(o.tmp, rows, l, l, Xq, ldq, nullptr, st));
+  } else if (passes >= 2 && again_tol >= 0.0) {
     // adaptive: the second pass runs only when the first one says it is needed
     r = pass(X, ldx, o.tmp, l, true, nullptr, again_tol);
     if (r != RQLP_OK) return r;
@@ -120,8 +132,8 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
 
 int orth(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
          const OrthBufs &o, Ctrl *ctrl, int site, cudaStream_t st, int passes = 2,
-         double again_tol = -1.0) {
-  return orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, passes, again_tol, st);
+         double again_tol = -1.0, bool lowp_first = false) {
+  return orth_impl(X, rows, l, ldx, Xq, ldq, R, o, ctrl, site, passes, again_tol, st, lowp_first);
 }
 
 // Mixed forms: a CholeskyQR pass leaves Q orthonormal to about eps cond(X)^2;
@@ -357,11 +369,14 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   // range finder (Section 2) with q power steps
   RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega, ldo, l, P.Y, st));
   // between power steps one CholeskyQR pass suffices: only the span of the
-  // intermediate bases matters; the final V is CholeskyQR2
+  // intermediate bases matters; the final V is CholeskyQR2.  In the mixed
+  // forms, whose products carry BF16-level errors, the power steps' passes
+  // run in FP32 (the span moves by about FP32 rounding).
+  const bool lowp = o.prec != RQLP_PREC_FP64;
   for (int i = 0; i < o.q; ++i) {
-    RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 1));
+    RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 1, -1.0, lowp));
     RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
-    RET(orth(P.Z, n, l, l, P.W, l, nullptr, P.ob, P.ctrl, site++, st, 1));
+    RET(orth(P.Z, n, l, l, P.W, l, nullptr, P.ob, P.ctrl, site++, st, 1, -1.0, lowp));
     RET(prod_nn(P, o, A, a_dtype, m, n, lda, P.W, l, l, P.Y, st));
   }
   RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 2, again_tol_of(o)));

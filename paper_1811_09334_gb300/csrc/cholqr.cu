@@ -32,24 +32,27 @@ namespace rqk {
 
 namespace {
 
-constexpr double kEps = 1.1102230246251565e-16;
 constexpr int kB = 16;       // block size of the Cholesky and the solve
 constexpr int kGramMaxRows = 32;  // rows of X per Gram chunk, at most
 constexpr int kGramThreads = 256;
 
 // Upper triangle of X_c^T X_c for the rc rows of chunk c = blockIdx.x, into
 // part[c] (l x l, only j >= i written).  Tiles of 4 x 4 over the triangle.
+// T = float: the chunk is rounded to FP32 and its products accumulate in FP32
+// over at most 32 rows (the chunks are summed in FP64).
+template <typename T>
 __global__ void __launch_bounds__(kGramThreads)
 k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int rc,
            double *__restrict__ part, const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  extern __shared__ double xs[];  // [rc][lp]
+  extern __shared__ double xs_raw[];
+  T *xs = reinterpret_cast<T *>(xs_raw);  // [rc][lp]
   const int lp = ((l + 3) / 4) * 4 + 1;
   const int64_t r0 = (int64_t)blockIdx.x * rc;
   const int nr = (int)min((int64_t)rc, rows - r0);
   for (int e = threadIdx.x; e < nr * lp; e += blockDim.x) {
     const int r = e / lp, c = e - r * lp;
-    xs[e] = (c < l) ? X[(r0 + r) * ldx + c] : 0.0;
+    xs[e] = (c < l) ? (T)X[(r0 + r) * ldx + c] : (T)0;
   }
   __syncthreads();
   const int nb = (l + 3) / 4;
@@ -63,14 +66,14 @@ k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int r
       ++bi;
     }
     const int bj = bi + rem;
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
     for (int r = 0; r < nr; ++r) {
-      const double *row = xs + r * lp;
-      double x[4], y[4];
+      const T *row = xs + r * lp;
+      T x[4], y[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) x[a] = row[4 * bi + a];
 #pragma unroll
@@ -87,23 +90,47 @@ k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int r
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int j = 4 * bj + b;
-        if (j < l && j >= i) out[(int64_t)i * l + j] = acc[a][b];
+        if (j < l && j >= i) out[(int64_t)i * l + j] = (double)acc[a][b];
       }
     }
   }
 }
 
-// G[i][j] = G[j][i] = sum_c part[c][i][j] for i <= j
-__global__ void k_gram_reduce(const double *__restrict__ part, int chunks, int l,
-                              double *__restrict__ G, const int *skip_unless) {
+// G[i][j] = G[j][i] = sum_c part[c][i][j] for i <= j.  Block (32, 8): 32
+// consecutive entries, the chunks split over threadIdx.y (two accumulators
+// each), then a fixed-order sum over y, so the result is deterministic and
+// no thread runs a long chain of dependent FP64 additions.
+constexpr int kReduceY = 8;
+__global__ void __launch_bounds__(32 * kReduceY)
+k_gram_reduce(const double *__restrict__ part, int chunks, int l, double *__restrict__ G,
+              const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  __shared__ double red[kReduceY][33];
   const int64_t ll = (int64_t)l * l;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ll;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / l), j = (int)(e - (int64_t)i * l);
-    if (j < i) continue;
-    double s = 0.0;
-    for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * ll + e];
+  const int64_t e = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int y = threadIdx.y;
+  int i = 0, j = 0;
+  bool want = false;
+  if (e < ll) {
+    i = (int)(e / l);
+    j = (int)(e - (int64_t)i * l);
+    want = j >= i;
+  }
+  double a0 = 0.0, a1 = 0.0;
+  if (want) {
+    int c = y;
+    for (; c + kReduceY < chunks; c += 2 * kReduceY) {
+      a0 += part[(int64_t)c * ll + e];
+      a1 += part[(int64_t)(c + kReduceY) * ll + e];
+    }
+    if (c < chunks) a0 += part[(int64_t)c * ll + e];
+  }
+  red[y][threadIdx.x] = a0 + a1;
+  __syncthreads();
+  if (y == 0 && want) {
+    double s = red[0][threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < kReduceY; ++k) s += red[k][threadIdx.x];
     G[(int64_t)i * l + j] = s;
     G[(int64_t)j * l + i] = s;
   }
@@ -116,7 +143,7 @@ __global__ void k_gram_reduce(const double *__restrict__ part, int chunks, int l
 __global__ void __launch_bounds__(512)
 k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
                double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless,
-               int use_smem, double again_tol) {
+               int use_smem, double again_tol, double eps) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   extern __shared__ double sm[];
   __shared__ double red[32];
@@ -130,7 +157,7 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
   tr = block_sum(tr, red);
   int fail = 0;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    const double shift = attempt ? 11.0 * (rows * l + (double)l * (l + 1)) * kEps * tr : 0.0;
+    const double shift = attempt ? 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr : 0.0;
     for (int e = tid; e < l * l; e += blockDim.x) {
       const int i = e / l, j = e - i * l;
       W[e] = G[e] + (i == j ? shift : 0.0);
@@ -146,7 +173,7 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
       const double g0 = s_gdiag[0];
       int f = 0;
       if (!isfinite(d) || !isfinite(g0)) f = 2;
-      else if (!(d > (double)l * 2.0 * kEps * g0) || !(d > 0.0)) f = 1;
+      else if (!(d > (double)l * 2.0 * eps * g0) || !(d > 0.0)) f = 1;
       s_fail = f;
       s_next = f ? 1.0 : rsqrt(d);
     }
@@ -169,7 +196,7 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
             const double g0 = s_gdiag[j + 1];
             int f = 0;
             if (!isfinite(dn) || !isfinite(g0)) f = 2;
-            else if (!(dn > (double)l * 2.0 * kEps * g0) || !(dn > 0.0)) f = 1;
+            else if (!(dn > (double)l * 2.0 * eps * g0) || !(dn > 0.0)) f = 1;
             if (f) s_fail = f;
             s_next = f ? 1.0 : rsqrt(dn);
           }
@@ -228,7 +255,7 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     }
     if (lane == 0) {
       const double c = (mn > 0.0) ? mx / mn : 1e300;
-      const int again = (fail != 0) || !(2.0 * kEps * c * c <= again_tol);
+      const int again = (fail != 0) || !(2.0 * eps * c * c <= again_tol);
       ctrl->again_flag[site] = again;
       ctrl->done_flag[site] = 1 - again;
     }
@@ -263,19 +290,22 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
 // Cluster Cholesky.  One SM does the l^3/6 FP64 FMAs of an l x l Cholesky at
 // about 2 FMA per clock, and every column adds a chain of dependent FP64
 // operations; here a cluster of C = 16 (or 8) CTAs shares the work.  Row a of
-// the trailing matrix belongs to CTA a % C; thread c of that CTA keeps column
-// c of its rows in registers.  Every finished row is also kept packed in each
-// CTA's shared memory (row j at off(j), entries j .. l-1): the owner pushes it
-// to the other CTAs with st.async stores that complete bytes on the
-// receiver's mbarrier for that row.  Every row is written once per attempt,
-// so no buffer is reused and nothing has to be acknowledged.  The owner of
-// row j + 1 applies row j to it first, scales it and sends it (look-ahead),
-// then updates its other rows.  A breakdown is sent in place of the diagonal
-// entry (-1: not positive enough, -2: not finite), so every CTA stops at the
-// same row; the shifted retry (as in the single-CTA kernel) uses a second set
-// of mbarriers.  The critical path per column (pivot test, reciprocal square
-// root, scaling) uses integer tests on the bit patterns and an FP32 estimate
-// refined in FP64, so few dependent FP64 operations sit on it.
+// the trailing matrix belongs to CTA a % C (round-robin: while one CTA forms
+// row j + 1, the owner of row j + 2 has already applied row j to it, so the
+// other updates stay off the column chain; contiguous row blocks measured
+// slower); thread c of that CTA keeps column c of its rows in registers.
+// Every finished row is also kept packed in each CTA's shared memory (row j
+// at off(j), entries j .. l-1): the owner pushes it to the other CTAs with
+// st.async stores that complete bytes on the receiver's mbarrier for that
+// row.  Every row is written once per attempt, so no buffer is reused and
+// nothing has to be acknowledged.  The owner of row j + 1 applies row j to it
+// first, scales it and sends it (look-ahead), then updates its other rows.  A
+// breakdown is sent in place of the diagonal entry (-1: not positive enough,
+// -2: not finite), so every CTA stops at the same row; the shifted retry (as
+// in the single-CTA kernel) uses a second set of mbarriers.  The critical
+// path per column (pivot test, reciprocal square root, scaling) uses integer
+// tests on the bit patterns and an FP32 estimate refined in FP64, so few
+// dependent FP64 operations sit on it.
 constexpr int kClusterMaxL = 224;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -347,7 +377,7 @@ template <int C, int RMAX>
 __global__ void __launch_bounds__(256)
 k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
                double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless,
-               double again_tol, unsigned long long limit_ns) {
+               double again_tol, double eps, unsigned long long limit_ns) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ntri = l * (l + 1) / 2;
@@ -386,14 +416,14 @@ k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restr
   double v[RMAX];  // v[i] = working entry (a_i, col(i))
   int fail = 0;
   for (int att = 0; att < 2; ++att) {
-    const double shift = att ? 11.0 * (rows * l + (double)l * (l + 1)) * kEps * tr : 0.0;
+    const double shift = att ? 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr : 0.0;
 #pragma unroll
     for (int i = 0; i < RMAX; ++i) {
       const int a = (int)me + i * C, c = col(i);
       v[i] = (a < l && c < l) ? G[(int64_t)a * l + c] + (c == a ? shift : 0.0) : 0.0;
     }
     for (int a = (int)me + tid * C; a < l; a += (int)blockDim.x * C)
-      thr[a] = (double)l * 2.0 * kEps * (G[(int64_t)a * l + a] + shift);
+      thr[a] = (double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift);
     if (tid == 0) s_code = 0;
     __syncthreads();
     const unsigned barA = bar0 + 8u * (unsigned)(att * l);
@@ -493,7 +523,7 @@ k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restr
     }
     if (lane == 0) {
       const double cn = (mn > 0.0) ? mx / mn : 1e300;
-      const int again = (fail != 0) || !(2.0 * kEps * cn * cn <= again_tol);
+      const int again = (fail != 0) || !(2.0 * eps * cn * cn <= again_tol);
       ctrl->again_flag[site] = again;
       ctrl->done_flag[site] = 1 - again;
     }
@@ -537,7 +567,7 @@ size_t chol_cluster_smem(int l) {
 template <int C, int RMAX>
 cudaError_t launch_chol_cluster(const double *G, int l, int64_t rows, double *R, double *Dinv,
                                 Ctrl *ctrl, int site, const int *skip_unless, cudaStream_t st,
-                                double again_tol) {
+                                double again_tol, double eps) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(l <= 128 ? 128 : 256);
@@ -551,7 +581,7 @@ cudaError_t launch_chol_cluster(const double *G, int l, int64_t rows, double *R,
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_cluster<C, RMAX>, G, l, (double)rows, R,
-                                           Dinv, ctrl, site, skip_unless, again_tol,
+                                           Dinv, ctrl, site, skip_unless, again_tol, eps,
                                            (unsigned long long)kDefaultSpinNs);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -603,21 +633,25 @@ constexpr int kApplyRows = 32;
 constexpr int kApplyThreads = 128;
 
 // Q (rows x l, ldq) = X R^{-1}, blocked over 16 columns; X and Q may not alias.
+// T = float: X, R and the block inverses are rounded to FP32 and the solve
+// runs in FP32 (Q is written in FP64).
+template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
              const double *__restrict__ R, const double *__restrict__ Dinv, double *__restrict__ Q,
              int64_t ldq, const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  extern __shared__ double sm[];
+  extern __shared__ double sm_raw[];
+  T *sm = reinterpret_cast<T *>(sm_raw);
   const int lp = l + 1;
-  double *qs = sm;                                  // [kApplyRows][lp]
-  double *rc = sm + kApplyRows * lp;                // [l][kB] block column of R
-  double *dv = rc + (int64_t)l * kB;                // [kB][kB] inverse diagonal block
+  T *qs = sm;                                  // [kApplyRows][lp]
+  T *rc = sm + kApplyRows * lp;                // [l][kB] block column of R
+  T *dv = rc + (int64_t)l * kB;                // [kB][kB] inverse diagonal block
   const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
   const int nr = (int)min((int64_t)kApplyRows, rows - r0);
   for (int e = threadIdx.x; e < kApplyRows * l; e += blockDim.x) {
     const int r = e / l, c = e - r * l;
-    qs[r * lp + c] = (r < nr) ? X[(r0 + r) * ldx + c] : 0.0;
+    qs[r * lp + c] = (r < nr) ? (T)X[(r0 + r) * ldx + c] : (T)0;
   }
   // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
   // warp needs the same rows of inv(R[b, b]), so the triangular product
@@ -628,18 +662,18 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     __syncthreads();
     for (int e = threadIdx.x; e < c0 * kB; e += blockDim.x) {
       const int t = e / kB, j = e - t * kB;
-      rc[e] = (j < bs) ? R[(int64_t)t * l + c0 + j] : 0.0;
+      rc[e] = (j < bs) ? (T)R[(int64_t)t * l + c0 + j] : (T)0;
     }
     for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) {
       const int i = e / kB, j = e - i * kB;
-      dv[e] = (i < bs && j < bs) ? Dinv[(int64_t)(c0 + i) * l + c0 + j] : 0.0;
+      dv[e] = (i < bs && j < bs) ? (T)Dinv[(int64_t)(c0 + i) * l + c0 + j] : (T)0;
     }
     __syncthreads();
-    double acc[4];
+    T acc[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a] = (j0 + a < bs) ? qs[r * lp + c0 + j0 + a] : 0.0;
+    for (int a = 0; a < 4; ++a) acc[a] = (j0 + a < bs) ? qs[r * lp + c0 + j0 + a] : (T)0;
     for (int t = 0; t < c0; ++t) {
-      const double qv = qs[r * lp + t];
+      const T qv = qs[r * lp + t];
 #pragma unroll
       for (int a = 0; a < 4; ++a) acc[a] = fma(-qv, rc[t * kB + j0 + a], acc[a]);
     }
@@ -649,10 +683,10 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     for (int a = 0; a < 4; ++a)
       if (j0 + a < bs) qs[r * lp + c0 + j0 + a] = acc[a];
     __syncthreads();
-    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    T out[4] = {(T)0, (T)0, (T)0, (T)0};
     const int iend = min(bs, j0 + 4);  // inv(R[b, b]) is upper triangular
     for (int i = 0; i < iend; ++i) {
-      const double v = qs[r * lp + c0 + i];
+      const T v = qs[r * lp + c0 + i];
 #pragma unroll
       for (int a = 0; a < 4; ++a) out[a] = fma(v, dv[i * kB + j0 + a], out[a]);
     }
@@ -664,7 +698,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   __syncthreads();
   for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
     const int rr = e / l, c = e - rr * l;
-    Q[(r0 + rr) * ldq + c] = qs[rr * lp + c];
+    Q[(r0 + rr) * ldq + c] = (double)qs[rr * lp + c];
   }
 }
 
@@ -678,13 +712,20 @@ inline int grid_for(int64_t total, int threads) {
 }  // namespace
 
 cudaError_t cholqr_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_gram_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       100 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_sym<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gram_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             100 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_chol_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_apply_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(k_apply_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
   if (e == cudaSuccess && chol_cluster_init() < 0) e = cudaErrorInvalidValue;
   return e;
 }
@@ -708,43 +749,52 @@ int64_t gram_chunks_max(int64_t rows_max) {
 }
 
 cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *part, double *G,
-                     const int *skip_unless, cudaStream_t st) {
+                     const int *skip_unless, cudaStream_t st, bool lowp) {
   const int rc = gram_rows_per_chunk(rows);
   const int64_t chunks = gram_chunks(rows);
   const int lp = ((l + 3) / 4) * 4 + 1;
-  const size_t smem = (size_t)rc * lp * sizeof(double);
+  const size_t smem = (size_t)rc * lp * (lowp ? sizeof(float) : sizeof(double));
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         100 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_gram_sym<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gram_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               100 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gram_sym<<<(unsigned)chunks, kGramThreads, smem, st>>>(X, rows, l, ldx, rc, part, skip_unless);
+  if (lowp)
+    k_gram_sym<float><<<(unsigned)chunks, kGramThreads, smem, st>>>(X, rows, l, ldx, rc, part,
+                                                                    skip_unless);
+  else
+    k_gram_sym<double><<<(unsigned)chunks, kGramThreads, smem, st>>>(X, rows, l, ldx, rc, part,
+                                                                     skip_unless);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gram_reduce<<<grid_for((int64_t)l * l, 256), 256, 0, st>>>(part, (int)chunks, l, G,
-                                                                skip_unless);
+  k_gram_reduce<<<(unsigned)(((int64_t)l * l + 31) / 32), dim3(32, kReduceY), 0, st>>>(
+      part, (int)chunks, l, G, skip_unless);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
-                         int site, const int *skip_unless, cudaStream_t st, double again_tol) {
+                         int site, const int *skip_unless, cudaStream_t st, double again_tol,
+                         double eps) {
   const int best = chol_cluster_init();
   if (best < 0) return cudaErrorInvalidValue;
   const int cc = l > kClusterMaxL ? 1 : (tuning().chol_ctas > 0 ? tuning().chol_ctas : best);
   if (cc == 16)
     return l <= 128 ? launch_chol_cluster<16, 8>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
-                                                 again_tol)
+                                                 again_tol, eps)
                     : launch_chol_cluster<16, 14>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
-                                                  again_tol);
+                                                  again_tol, eps);
   if (cc == 8)
     return l <= 128 ? launch_chol_cluster<8, 16>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
-                                                 again_tol)
+                                                 again_tol, eps)
                     : launch_chol_cluster<8, 28>(G, l, rows, R, Dinv, ctrl, site, skip_unless, st,
-                                                 again_tol);
+                                                 again_tol, eps);
   const size_t smem = (size_t)l * l * sizeof(double);
   const bool use_smem = smem <= 200 * 1024;
   static bool attr = false;
@@ -758,25 +808,33 @@ cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double
   threads = std::max(128, std::min(512, threads));
   k_chol_blocked<<<1, threads, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, Dinv, ctrl, site,
                                                           skip_unless, use_smem ? 1 : 0,
-                                                          again_tol);
+                                                          again_tol, eps);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
                        const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
-                       cudaStream_t st) {
-  const size_t smem = ((size_t)kApplyRows * (l + 1) + (size_t)l * kB + kB * kB) * sizeof(double);
+                       cudaStream_t st, bool lowp) {
+  const size_t smem = ((size_t)kApplyRows * (l + 1) + (size_t)l * kB + kB * kB) *
+                      (lowp ? sizeof(float) : sizeof(double));
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_trsm<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t tiles = (rows + kApplyRows - 1) / kApplyRows;
-  k_apply_trsm<<<(unsigned)tiles, kApplyThreads, smem, st>>>(X, rows, l, ldx, R, Dinv, Q, ldq,
-                                                              skip_unless);
+  if (lowp)
+    k_apply_trsm<float><<<(unsigned)tiles, kApplyThreads, smem, st>>>(X, rows, l, ldx, R, Dinv, Q,
+                                                                       ldq, skip_unless);
+  else
+    k_apply_trsm<double><<<(unsigned)tiles, kApplyThreads, smem, st>>>(X, rows, l, ldx, R, Dinv, Q,
+                                                                        ldq, skip_unless);
   count_launch();
   return cudaGetLastError();
 }

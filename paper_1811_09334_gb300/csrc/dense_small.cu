@@ -186,7 +186,7 @@ k_form_q(const double *__restrict__ Vh, int64_t ldv, const double *__restrict__ 
          int t, double *__restrict__ Q, int64_t ldq) {
   __shared__ double xs[8][kMaxL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x * 8 + warp;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= t) return;
   double *x = xs[warp];
   for (int i = lane; i < rows; i += 32) x[i] = (i == c) ? 1.0 : 0.0;
@@ -377,7 +377,9 @@ cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaS
 cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
                    double *Q, int64_t ldq, cudaStream_t st) {
   if (rows > kMaxL || t <= 0) return cudaErrorInvalidValue;
-  k_form_q<<<(t + 7) / 8, 256, 0, st>>>(Vh, ldv, tau, (int)rows, t, Q, ldq);
+  // one warp per CTA: each column is a chain of t reflector applications,
+  // so the columns are spread over as many SMs as possible
+  k_form_q<<<t, 32, 0, st>>>(Vh, ldv, tau, (int)rows, t, Q, ldq);
   count_launch();
   return cudaGetLastError();
 }

@@ -116,21 +116,27 @@ cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t row
 int64_t gram_chunks(int64_t rows);
 int64_t gram_chunks_max(int64_t rows_max);  // >= gram_chunks(r) for every r <= rows_max
 cudaError_t cholqr_init();  // kernel attributes, set before any stream capture
+// unit roundoffs of the two CholeskyQR pass precisions
+constexpr double kEpsF64 = 1.1102230246251565e-16;  // 2^-53
+constexpr double kEpsF32 = 5.9604644775390625e-08;  // 2^-24
 // G = X^T X (symmetric, l x l, ld l); part: gram_chunks(rows) * l * l doubles (at most
-// gram_chunks_max of the largest rows)
+// gram_chunks_max of the largest rows).  lowp: X rounded to FP32, products in FP32
+// over chunks of <= 32 rows, chunks summed in FP64 (error about kEpsF32 |X|^T |X|).
 cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *part, double *G,
-                     const int *skip_unless, cudaStream_t st);
+                     const int *skip_unless, cudaStream_t st, bool lowp = false);
 // G = R^T R (R upper, ld l) with shifted retry; Dinv: inverses of R's 16 x 16
-// diagonal blocks (block-diagonal, ld l)
+// diagonal blocks (block-diagonal, ld l).  eps: unit roundoff of the pass that
+// formed G (breakdown threshold l 2 eps G_jj, shift of shifted CholeskyQR).
 // again_tol >= 0: set ctrl->again_flag[site] (and done_flag = 1 - it) when
 // eps cond(R)^2 > again_tol, i.e. when one pass leaves Q less orthonormal
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st,
-                         double again_tol = -1.0);
-// Q = X R^{-1} by a blocked triangular solve (X and Q must not alias)
+                         double again_tol = -1.0, double eps = kEpsF64);
+// Q = X R^{-1} by a blocked triangular solve (X and Q must not alias); lowp:
+// the solve runs in FP32 (Q stored in FP64)
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
                        const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
-                       cudaStream_t st);
+                       cudaStream_t st, bool lowp = false);
 
 // ---- cpqr.cu ---------------------------------------------------------------
 size_t cpqr_ws_bytes(int64_t n, int l);
