@@ -137,8 +137,10 @@ k_gram_reduce(const double *__restrict__ part, int chunks, int l, double *__rest
 }
 
 // Upper Cholesky G = R^T R with 16-column blocks, breakdown detection and one
-// shifted retry (shifted CholeskyQR, Fukaya et al. 2020), as k_chol_upper in
-// dense_small.cu.  Also writes Dinv: the inverses of R's 16 x 16 diagonal
+// shifted retry: a pivot d_j <= l 2 eps G_jj means the Gram matrix is
+// numerically singular, and the factorization is redone once on G + s I with
+// the shift s = 11 (rows l + l (l + 1)) eps tr(G) of shifted CholeskyQR
+// (Fukaya et al. 2020).  Also writes Dinv: the inverses of R's 16 x 16 diagonal
 // blocks (block-diagonal l x l, ld l).
 __global__ void __launch_bounds__(512)
 k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restrict__ R,

@@ -1,6 +1,6 @@
 // Small dense FP64 kernels around the l x l matrices of the method: the
-// Cholesky factor and triangular inverse of CholeskyQR, explicit Q from
-// Householder reflectors, transposes, gathers and diagonals.
+// triangular inverse used by the adjoint, explicit Q from Householder
+// reflectors, transposes, gathers and diagonals.
 #include <cmath>
 
 #include "kernels.cuh"
@@ -8,86 +8,6 @@
 namespace rqk {
 
 namespace {
-
-constexpr double kEps = 1.1102230246251565e-16;  // unit roundoff of binary64
-
-// One CTA.  Upper Cholesky G = R^T R, right-looking, on the upper triangle.
-// A pivot d_j <= l * eps * G_jj means the Gram matrix is numerically
-// singular; the factorization is then redone once on G + s I with the shift
-// s = 11 (rows l + l (l + 1)) u ||X||_F^2 of shifted CholeskyQR (Fukaya,
-// Kannan, Nakatsukasa, Yamamoto and Yanagisawa, SIAM J. Sci. Comput. 2020),
-// and ctrl->shift_flag[site] is raised so that the caller's extra pass runs.
-__global__ void __launch_bounds__(1024)
-k_chol_upper(const double *__restrict__ G, int l, double rows, double *__restrict__ R, Ctrl *ctrl,
-             int site, const int *skip_unless, int use_smem) {
-  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  extern __shared__ double sm[];
-  __shared__ double red[32];
-  __shared__ int s_fail;
-  __shared__ double s_rjj, s_inv;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  double *W = use_smem ? sm : R;
-  double tr = 0.0;
-  for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
-  tr = block_sum(tr, red);
-  int fail = 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    const double shift = attempt ? 11.0 * (rows * l + (double)l * (l + 1)) * kEps * tr : 0.0;
-    for (int e = tid; e < l * l; e += blockDim.x) {
-      const int i = e / l, j = e - i * l;
-      W[e] = G[e] + (i == j ? shift : 0.0);
-    }
-    if (tid == 0) s_fail = 0;
-    __syncthreads();
-    for (int j = 0; j < l; ++j) {
-      // FP64 square roots and divisions are costly on this part: one thread
-      // takes them and the CTA reads the result.
-      if (tid == 0) {
-        const double d = W[(int64_t)j * l + j];
-        const double g0 = G[(int64_t)j * l + j] + shift;
-        int f = 0;
-        if (!isfinite(d) || !isfinite(g0)) f = 2;
-        else if (!(d > (double)l * 2.0 * kEps * g0) || !(d > 0.0)) f = 1;
-        s_fail = f;
-        if (!f) {
-          const double rjj = sqrt(d);
-          s_rjj = rjj;
-          s_inv = 1.0 / rjj;
-          W[(int64_t)j * l + j] = rjj;
-        }
-      }
-      __syncthreads();
-      if (s_fail) break;
-      const double inv = s_inv;
-      for (int c = j + 1 + tid; c < l; c += blockDim.x) W[(int64_t)j * l + c] *= inv;
-      __syncthreads();
-      for (int a = j + 1 + warp; a < l; a += nw) {
-        const double ra = W[(int64_t)j * l + a];
-        for (int c = a + lane; c < l; c += 32) W[(int64_t)a * l + c] -= ra * W[(int64_t)j * l + c];
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    fail = s_fail;
-    __syncthreads();
-    if (fail == 0) break;
-    if (fail == 2) break;
-    if (attempt == 0 && tid == 0) {
-      ctrl->shift_flag[site] = 1;
-      set_status(ctrl, RQLP_WARN_SHIFTED_CHOLQR);
-    }
-  }
-  if (fail == 2) {
-    if (tid == 0) set_status(ctrl, RQLP_ERR_NONFINITE);
-  } else if (fail == 1) {
-    if (tid == 0) set_status(ctrl, RQLP_ERR_RANK_DEFICIENT);
-  }
-  __syncthreads();
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e - i * l;
-    R[e] = (j >= i) ? W[e] : 0.0;
-  }
-}
 
 // Rinv = R^{-1}, R upper triangular l x l.  One warp per column c: row i of
 // the column solves R(i, i:c) x(i:c) = e_c(i) from the bottom up.
@@ -256,34 +176,7 @@ inline int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-cudaError_t chol_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(200 * 1024));
-  return e == cudaSuccess ? cholqr_init() : e;
-}
-
-cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
-                       const int *skip_unless, cudaStream_t st) {
-  const size_t smem = (size_t)l * l * sizeof(double);
-  const bool use_smem = smem <= 200 * 1024;
-  if (use_smem) {
-    static size_t set_to = 0;
-    if (smem > 48 * 1024 && smem > set_to) {
-      cudaError_t e = cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(200 * 1024));
-      if (e != cudaSuccess) return e;
-      set_to = 200 * 1024;
-    }
-  }
-  // enough threads for the first trailing update, no more: every column
-  // step ends in CTA barriers whose cost grows with the CTA size
-  int threads = ((l * l / 12) + 31) / 32 * 32;
-  threads = std::max(128, std::min(1024, threads));
-  k_chol_upper<<<1, threads, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, ctrl, site,
-                                                         skip_unless, use_smem ? 1 : 0);
-  count_launch();
-  return cudaGetLastError();
-}
+cudaError_t chol_init() { return cholqr_init(); }
 
 cudaError_t trinv_upper(const double *R, int l, double *Rinv, const int *skip_unless,
                         cudaStream_t st) {

@@ -72,11 +72,8 @@ cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const
                      const int *skip_unless, cudaStream_t st);
 
 // ---- dense_small.cu ------------------------------------------------------
-// Cholesky G = R^T R of an l x l SPD matrix (upper R, ld l), breakdown
-// detection, one shifted retry with Fukaya's shift for `rows` x l data.
+// kernel attributes of the CholeskyQR kernels (call before any stream capture)
 cudaError_t chol_init();
-cudaError_t chol_upper(const double *G, int l, int64_t rows, double *R, Ctrl *ctrl, int site,
-                       const int *skip_unless, cudaStream_t st);
 // Rinv = R^{-1} for upper triangular R (l x l, ld l).
 cudaError_t trinv_upper(const double *R, int l, double *Rinv, const int *skip_unless,
                         cudaStream_t st);
