@@ -82,7 +82,7 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
     CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol,
-                    lowp ? kEpsF32 : kEpsF64));
+                    lowp ? kEpsF32 : kEpsF64, lowp));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
     CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp));
@@ -123,9 +123,12 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
   }
   if (r != RQLP_OK) return r;
   // one more pass, only when the device raised the shift flag: Xq -> tmp -> Xq
-  r = pass(Xq, ldq, o.tmp, l, false, flag, -1.0);
-  if (r != RQLP_OK) return r;
-  CK(copy2d(o.tmp, rows, l, l, Xq, ldq, flag, st));
+  // (a lone FP32 pass never raises it: a shifted factor still spans range(X))
+  if (!(lowp_first && passes < 2)) {
+    r = pass(Xq, ldq, o.tmp, l, false, flag, -1.0);
+    if (r != RQLP_OK) return r;
+    CK(copy2d(o.tmp, rows, l, l, Xq, ldq, flag, st));
+  }
   if (R) CK(copy2d(o.Racc, l, l, l, R, l, nullptr, st));
   return RQLP_OK;
 }

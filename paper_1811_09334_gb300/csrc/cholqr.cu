@@ -141,7 +141,22 @@ k_gram_reduce(const double *__restrict__ part, int chunks, int l, double *__rest
 // numerically singular, and the factorization is redone once on G + s I with
 // the shift s = 11 (rows l + l (l + 1)) eps tr(G) of shifted CholeskyQR
 // (Fukaya et al. 2020).  Also writes Dinv: the inverses of R's 16 x 16 diagonal
-// blocks (block-diagonal l x l, ld l).
+// blocks (block-diagonal l x l, ld l).  T = float (use_smem only): the FP32
+// factorization of the FP32 CholeskyQR pass, ~20x faster per column than the
+// FP64 one on this GPU; R and Dinv are still written in FP64.
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rsqrtT(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x * y, y, 1.5f);  // one Newton step: FP32 accuracy
+}
+__device__ __forceinline__ double rsqrtT(double x) { return rsqrt(x); }
+
+template <typename T>
 __global__ void __launch_bounds__(512)
 k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
                double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless,
@@ -149,11 +164,12 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   extern __shared__ double sm[];
   __shared__ double red[32];
-  __shared__ double s_gdiag[kMaxL];
-  __shared__ double s_next;
+  __shared__ T s_gdiag[kMaxL];
+  __shared__ T s_next;
   __shared__ int s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  double *W = use_smem ? sm : R;
+  T *W = use_smem ? reinterpret_cast<T *>(sm) : reinterpret_cast<T *>(R);
+  const T thr_scale = (T)((double)l * 2.0 * eps);
   double tr = 0.0;
   for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
   tr = block_sum(tr, red);
@@ -162,27 +178,27 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     const double shift = attempt ? 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr : 0.0;
     for (int e = tid; e < l * l; e += blockDim.x) {
       const int i = e / l, j = e - i * l;
-      W[e] = G[e] + (i == j ? shift : 0.0);
+      W[e] = (T)(G[e] + (i == j ? shift : 0.0));
     }
-    for (int i = tid; i < l; i += blockDim.x) s_gdiag[i] = G[(int64_t)i * l + i] + shift;
+    for (int i = tid; i < l; i += blockDim.x) s_gdiag[i] = (T)(G[(int64_t)i * l + i] + shift);
     if (tid == 0) s_fail = 0;
     __syncthreads();
     // right-looking, one column per step, spread over every warp; warp 0
     // updates the next diagonal entry first and takes its reciprocal square
     // root while the other warps update the rest of the trailing triangle
     if (tid == 0) {
-      const double d = W[0];
-      const double g0 = s_gdiag[0];
+      const T d = W[0];
+      const T g0 = s_gdiag[0];
       int f = 0;
       if (!isfinite(d) || !isfinite(g0)) f = 2;
-      else if (!(d > (double)l * 2.0 * eps * g0) || !(d > 0.0)) f = 1;
+      else if (!(d > thr_scale * g0) || !(d > (T)0)) f = 1;
       s_fail = f;
-      s_next = f ? 1.0 : rsqrt(d);
+      s_next = f ? (T)1 : rsqrtT(d);
     }
     __syncthreads();
     for (int j = 0; j < l && !s_fail; ++j) {
-      const double rs = s_next;
-      double *Wj = W + j * l;  // l <= 256: 32-bit offsets
+      const T rs = s_next;
+      T *Wj = W + j * l;  // l <= 256: 32-bit offsets
       // only thread 0 reads and rewrites the pivot; s_next and row j were
       // written before the previous barrier
       for (int c = j + 1 + tid; c < l; c += blockDim.x) Wj[c] *= rs;
@@ -190,33 +206,33 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
       __syncthreads();
       if (warp == 0) {
         if (j + 1 < l) {
-          double *W1 = W + (j + 1) * l;
-          const double r1 = Wj[j + 1];
+          T *W1 = W + (j + 1) * l;
+          const T r1 = Wj[j + 1];
           if (lane == 0) {
-            const double dn = W1[j + 1] - r1 * r1;
+            const T dn = fmaT(-r1, r1, W1[j + 1]);
             W1[j + 1] = dn;
-            const double g0 = s_gdiag[j + 1];
+            const T g0 = s_gdiag[j + 1];
             int f = 0;
             if (!isfinite(dn) || !isfinite(g0)) f = 2;
-            else if (!(dn > (double)l * 2.0 * eps * g0) || !(dn > 0.0)) f = 1;
+            else if (!(dn > thr_scale * g0) || !(dn > (T)0)) f = 1;
             if (f) s_fail = f;
-            s_next = f ? 1.0 : rsqrt(dn);
+            s_next = f ? (T)1 : rsqrtT(dn);
           }
           // the rest of row j + 1 of the trailing triangle
-          for (int c = j + 2 + lane; c < l; c += 32) W1[c] = fma(-r1, Wj[c], W1[c]);
+          for (int c = j + 2 + lane; c < l; c += 32) W1[c] = fmaT(-r1, Wj[c], W1[c]);
         }
       } else {
         for (int a = j + 2 + (warp - 1); a < l; a += nw - 1) {
-          const double ra = Wj[a];
-          double *Wa = W + a * l;
+          const T ra = Wj[a];
+          T *Wa = W + a * l;
           int c = a + lane;
           for (; c + 32 < l; c += 64) {
-            const double x0 = fma(-ra, Wj[c], Wa[c]);
-            const double x1 = fma(-ra, Wj[c + 32], Wa[c + 32]);
+            const T x0 = fmaT(-ra, Wj[c], Wa[c]);
+            const T x1 = fmaT(-ra, Wj[c + 32], Wa[c + 32]);
             Wa[c] = x0;
             Wa[c + 32] = x1;
           }
-          if (c < l) Wa[c] = fma(-ra, Wj[c], Wa[c]);
+          if (c < l) Wa[c] = fmaT(-ra, Wj[c], Wa[c]);
         }
       }
       __syncthreads();
@@ -225,7 +241,9 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     fail = s_fail;
     __syncthreads();
     if (fail == 0 || fail == 2) break;
-    if (attempt == 0 && tid == 0) {
+    // the FP32 pass (power steps: only the span of the basis matters) shifts
+    // silently; an FP64 pass that needs the shift is reported
+    if (attempt == 0 && tid == 0 && sizeof(T) == sizeof(double)) {
       ctrl->shift_flag[site] = 1;
       set_status(ctrl, RQLP_WARN_SHIFTED_CHOLQR);
     }
@@ -238,7 +256,7 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
   __syncthreads();
   for (int e = tid; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e - i * l;
-    R[e] = (j >= i) ? W[e] : 0.0;
+    R[e] = (j >= i) ? (double)W[e] : 0.0;
   }
   __syncthreads();
   // a second pass is needed when eps * cond(R)^2, the loss of orthogonality
@@ -268,21 +286,21 @@ k_chol_blocked(const double *__restrict__ G, int l, double rows, double *__restr
     const int c0 = bk * kB, bs = min(kB, l - c0);
     const int c = lane;  // column of the block inverse
     if (c < kB) {
-      double x[kB];
+      T x[kB];
 #pragma unroll
-      for (int i = 0; i < kB; ++i) x[i] = 0.0;
+      for (int i = 0; i < kB; ++i) x[i] = (T)0;
       if (c < bs) {
-        const double *Rb = R + (int64_t)c0 * l + c0;
+        const T *Rb = W + (int64_t)c0 * l + c0;  // the factor, in the working precision
         // upper triangular U x = e_c, rows c .. 0
         for (int i = bs - 1; i >= 0; --i) {
           if (i > c) continue;
-          double s = (i == c) ? 1.0 : 0.0;
-          for (int t = i + 1; t <= c; ++t) s = fma(-Rb[(int64_t)i * l + t], x[t], s);
+          T s = (i == c) ? (T)1 : (T)0;
+          for (int t = i + 1; t <= c; ++t) s = fmaT(-Rb[(int64_t)i * l + t], x[t], s);
           x[i] = s / Rb[(int64_t)i * l + i];
         }
       }
       for (int i = 0; i < kB; ++i) {
-        if (i < bs && c < bs) Dinv[(int64_t)(c0 + i) * l + c0 + c] = x[i];
+        if (i < bs && c < bs) Dinv[(int64_t)(c0 + i) * l + c0 + c] = (double)x[i];
       }
     }
   }
@@ -562,6 +580,125 @@ k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restr
   cluster_sync_all();
 }
 
+// FP32 Cholesky for the FP32 CholeskyQR pass, l <= 128, one CTA of 1024
+// threads: thread t holds column c = t % 128 of rows 16 g .. 16 g + 15 of
+// the trailing matrix (g = t / 128) in registers.  Per column j: the pivot's
+// thread takes the reciprocal square root (FP32 MUFU estimate and one Newton
+// step), row j is scaled by its group and published in shared memory
+// (double-buffered by parity), and every thread applies it to its rows with
+// one broadcast row load per 4 rows.  Two barriers per column, no FP64 on
+// the chain; R and the block inverses are written in FP64.
+constexpr int kChol32MaxL = 128;
+__global__ void __launch_bounds__(1024)
+k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
+           double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless, double eps) {
+  if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
+  __shared__ __align__(16) float rowbuf[2][kChol32MaxL];
+  __shared__ float s_thr[kChol32MaxL];
+  __shared__ double red[32];
+  __shared__ float s_rs;
+  __shared__ int s_f;
+  const int tid = threadIdx.x, c = tid & 127, g = tid >> 7;
+  const int lane = tid & 31, warp = tid >> 5;
+  double tr = 0.0;
+  for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
+  tr = block_sum(tr, red);
+  float v[16];
+  int fail = 0;
+  for (int att = 0; att < 2; ++att) {
+    const double shift = att ? 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr : 0.0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int a = 16 * g + i;
+      v[i] = (a < l && c >= a && c < l) ? (float)(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
+                                        : 0.0f;
+    }
+    for (int a = tid; a < l; a += blockDim.x)
+      s_thr[a] = (float)((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
+    if (tid == 0) s_f = 0;
+    __syncthreads();
+    for (int jb = 0; jb * 16 < l; ++jb) {
+      bool stop = false;
+#pragma unroll
+      for (int ii = 0; ii < 16; ++ii) {
+        const int j = 16 * jb + ii;
+        if (j >= l) break;
+        const int buf = j & 1;
+        if (g == jb && c == j) {
+          const float d = v[ii], th = s_thr[j];
+          int f = 0;
+          if (!isfinite(d) || !isfinite(th)) f = 2;
+          else if (!(d > th) || !(d > 0.0f)) f = 1;
+          s_f = f;
+          s_rs = f ? 1.0f : rsqrtT(d);
+        }
+        __syncthreads();
+        if (s_f) { stop = true; break; }
+        if (g == jb && c >= j && c < l) {
+          const float y = v[ii] * s_rs;
+          rowbuf[buf][c] = y;
+          R[(int64_t)j * l + c] = (double)y;
+        }
+        __syncthreads();
+        const float rjc = (c >= j && c < l) ? rowbuf[buf][c] : 0.0f;
+        const float4 *rb4 = reinterpret_cast<const float4 *>(&rowbuf[buf][16 * g]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (16 * g + 4 * q + 3 <= j) continue;  // these four rows are finished
+          const float4 r4 = rb4[q];
+          const float ra[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = 4 * q + k, a = 16 * g + i;
+            if (a > j && a <= c) v[i] = fmaf(-ra[k], rjc, v[i]);
+          }
+        }
+      }
+      if (stop) break;
+    }
+    fail = s_f;
+    __syncthreads();
+    if (fail == 1 && att == 0) continue;  // the FP32 pass shifts silently
+    break;
+  }
+  if (tid == 0) {
+    if (fail == 2) set_status(ctrl, RQLP_ERR_NONFINITE);
+    else if (fail == 1) set_status(ctrl, RQLP_ERR_RANK_DEFICIENT);
+  }
+  // zeros below the diagonal (rows were written above it)
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e / l, jj = e - i * l;
+    if (jj < i) R[e] = 0.0;
+  }
+  __syncthreads();
+  // inverses of the 16 x 16 diagonal blocks in FP32, one warp per block
+  const int nblk = (l + kB - 1) / kB;
+  for (int bk = warp; bk < nblk; bk += (int)(blockDim.x >> 5)) {
+    const int c0 = bk * kB, bs = min(kB, l - c0);
+    const int cc = lane;
+    auto U = [&](int i, int t) { return (float)R[(int64_t)(c0 + i) * l + c0 + t]; };
+    const float dl = (lane < bs) ? 1.0f / U(lane, lane) : 0.0f;
+    float x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) x[i] = 0.0f;
+#pragma unroll
+    for (int i = kB - 1; i >= 0; --i) {
+      const float di = __shfl_sync(0xffffffffu, dl, i);
+      if (i < bs && cc < bs && i <= cc) {
+        float sacc = (i == cc) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int t = i + 1; t < kB; ++t)
+          if (t <= cc && t < bs) sacc = fmaf(-U(i, t), x[t], sacc);
+        x[i] = sacc * di;
+      }
+    }
+    if (cc < bs)
+#pragma unroll
+      for (int i = 0; i < kB; ++i)
+        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = (double)x[i];
+  }
+}
+
 size_t chol_cluster_smem(int l) {
   return (size_t)l * (l + 1) / 2 * sizeof(double) + 2 * (size_t)l * 8 + (size_t)l * sizeof(double);
 }
@@ -704,13 +841,6 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   }
 }
 
-inline int grid_for(int64_t total, int threads) {
-  int64_t b = (total + threads - 1) / threads;
-  if (b > 4LL * num_sms()) b = 4LL * num_sms();
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
 }  // namespace
 
 cudaError_t cholqr_init() {
@@ -720,7 +850,10 @@ cudaError_t cholqr_init() {
     e = cudaFuncSetAttribute(k_gram_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              100 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_chol_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_chol_blocked<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol_blocked<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_apply_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -783,7 +916,26 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
 
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st, double again_tol,
-                         double eps) {
+                         double eps, bool lowp) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_blocked<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_chol_blocked<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int threads = ((l * l / 24) + 31) / 32 * 32;
+  threads = std::max(128, std::min(512, threads));
+  // FP32 pass: one CTA, registers and FP32 only (its column chain is a few
+  // FP32 operations and two barriers)
+  if (lowp && l <= kChol32MaxL && again_tol < 0.0) {
+    k_chol_f32<<<1, 1024, 0, st>>>(G, l, (double)rows, R, Dinv, ctrl, site, skip_unless, eps);
+    count_launch();
+    return cudaGetLastError();
+  }
   const int best = chol_cluster_init();
   if (best < 0) return cudaErrorInvalidValue;
   const int cc = l > kClusterMaxL ? 1 : (tuning().chol_ctas > 0 ? tuning().chol_ctas : best);
@@ -799,18 +951,8 @@ cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double
                                                  again_tol, eps);
   const size_t smem = (size_t)l * l * sizeof(double);
   const bool use_smem = smem <= 200 * 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  int threads = ((l * l / 24) + 31) / 32 * 32;
-  threads = std::max(128, std::min(512, threads));
-  k_chol_blocked<<<1, threads, use_smem ? smem : 0, st>>>(G, l, (double)rows, R, Dinv, ctrl, site,
-                                                          skip_unless, use_smem ? 1 : 0,
-                                                          again_tol, eps);
+  k_chol_blocked<double><<<1, threads, use_smem ? smem : 0, st>>>(
+      G, l, (double)rows, R, Dinv, ctrl, site, skip_unless, use_smem ? 1 : 0, again_tol, eps);
   count_launch();
   return cudaGetLastError();
 }

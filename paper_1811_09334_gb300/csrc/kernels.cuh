@@ -126,9 +126,10 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
 // formed G (breakdown threshold l 2 eps G_jj, shift of shifted CholeskyQR).
 // again_tol >= 0: set ctrl->again_flag[site] (and done_flag = 1 - it) when
 // eps cond(R)^2 > again_tol, i.e. when one pass leaves Q less orthonormal
+// lowp: factor in FP32 on one CTA (the FP32 CholeskyQR pass; l <= 226)
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st,
-                         double again_tol = -1.0, double eps = kEpsF64);
+                         double again_tol = -1.0, double eps = kEpsF64, bool lowp = false);
 // Q = X R^{-1} by a blocked triangular solve (X and Q must not alias); lowp:
 // the solve runs in FP32 (Q stored in FP64)
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
