@@ -85,7 +85,12 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
                     lowp ? kEpsF32 : kEpsF64, lowp));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
-    CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp));
+    if (rows <= kMaxL && !lowp && skip == nullptr) {
+      // a few rows (the l x l QRs): one warp per row solves q R = x
+      CK(tri_rows(o.Rp, l, nullptr, l, src, lds, dst, ldd, (int)rows, false, st));
+    } else {
+      CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp));
+    }
     if (R) {
       if (first) {
         CK(copy2d(o.Rp, l, l, l, o.Racc, l, skip, st));
@@ -150,6 +155,7 @@ struct Plan {
   OrthBufs ob;
   double *Y, *V, *Z, *W, *X, *R0t;
   double *Q0, *QB, *Macc, *Racc, *Rt, *Tl, *Vh, *tau, *Qi, *Rprev, *Xs, *sm1;
+  double *utw;  // 2 l^2: scratch of the explicit Q from reflectors
   int32_t *piv0, *piv1;
   void *cpqr_scratch;
   MixedBufs mx;
@@ -181,6 +187,7 @@ Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
   p.Rprev = a.take<double>(ll);
   p.Xs = a.take<double>(ll);
   p.sm1 = a.take<double>(ll);
+  p.utw = a.take<double>(2 * ll);
   p.piv0 = a.take<int32_t>((size_t)n);
   p.piv1 = a.take<int32_t>((size_t)l);
   p.cpqr_scratch = a.take<char>(cpqr_ws_bytes(std::max<int64_t>(n, l), l));
@@ -241,6 +248,31 @@ int prod_tn(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64
     if (r_ != RQLP_OK) return r_; \
   } while (0)
 
+// A second stream for work that does not depend on its neighbours (the
+// explicit Q0 of the CPQR runs beside the QR of R0^T).  Not used while the
+// stream is being captured (the batched plan captures many problems, and a
+// shared side stream would tie their graphs together).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream *side_for(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return nullptr;
+  static thread_local SideStream sd;
+  if (!sd.s) {
+    if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess) {
+      sd.s = nullptr;
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  return &sd;
+}
+
 // The pivoted QLP of the small w x n matrix B, given as Bt = B^T (n x w,
 // ld w), followed by the assembly of Q and P (Algorithm 2.1 steps 5-7,
 // Algorithm 2.2 steps 5-9).  Vb is the m x w range basis (ld ldv); Q (m x w),
@@ -256,15 +288,31 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
   int ev = prof_start(kProfCpqr, st);
   CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st));
   prof_stop(kProfCpqr, ev, st);
-  ev = prof_start(kProfSmall, st);
-  CK(form_q(P.Vh, l, P.tau, l, l, P.Q0, l, st));
-  prof_stop(kProfSmall, ev, st);
+  // Q0 from the reflectors, beside the QR of R0^T (joined before Vh is
+  // overwritten or Q0 is used)
+  SideStream *sd = side_for(st);
+  cudaStream_t sq = sd ? sd->s : st;
+  if (sd) {
+    CK(cudaEventRecord(sd->fork, st));
+    CK(cudaStreamWaitEvent(sq, sd->fork, 0));
+  }
+  ev = prof_start(kProfSmall, sq);
+  CK(form_q(P.Vh, l, P.tau, l, l, P.Q0, l, sq, P.utw));
+  prof_stop(kProfSmall, ev, sq);
+  auto join = [&]() -> int {
+    if (sd) {
+      CK(cudaEventRecord(sd->join, sq));
+      CK(cudaStreamWaitEvent(st, sd->join, 0));
+    }
+    return RQLP_OK;
+  };
   if (o.pivot2) {
     RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
     CK(transpose(P.Racc, l, l, l, P.Rt, l, st));
+    RET(join());
     CK(cpqr_wide(P.Rt, l, l, l, P.Tl, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
     CK(copy2d(P.Tl, l, l, l, L, ldo, nullptr, st));
-    CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st));
+    CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st, P.utw));
     CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
     const int eva = prof_start(kProfAssembly, st);
     CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
@@ -283,6 +331,7 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
                   nullptr, st));
       CK(copy2d(P.sm1, l, l, l, acc, l, nullptr, st));
     }
+    RET(join());
     CK(gemm_f64(false, RQLP_F64, P.Q0, l, P.QB, l, P.sm1, l, l, l, l, 1.0, 0.0, P.ob.part, nullptr,
                 nullptr, st));
     CK(copy2d(P.sm1, l, l, l, P.QB, l, nullptr, st));

@@ -5,15 +5,20 @@
 // columns of B (each column l doubles), kept in shared memory when it fits
 // and in a global scratch copy otherwise.  Per pivot step s there is exactly
 // one grid barrier:
-//   1. every CTA reads the candidate table (one (norm^2, index) pair and one
-//      column per CTA, written before the barrier) and picks the same winner:
-//      the largest trailing norm, ties to the lowest original column index;
+//   1. the winner of step s (largest trailing norm, ties to the lowest
+//      original column index) was picked by the last CTA to arrive at the
+//      barrier; every CTA reads its record: the CTA that holds it and the
+//      exact ||x(s+1:)||^2 of its column;
 //   2. every CTA builds the same Householder reflector from the winner's
 //      column, mapping it to +alpha e_s (non-negative R(s, s));
-//   3. every CTA applies the reflector to its own unpivoted columns (one warp
-//      per column: a shuffle-reduced dot product, an axpy, and the exact new
-//      trailing norm^2 over rows s+1..l-1), the owner of the winner writes its
-//      final R column, and each CTA publishes its best candidate for s + 1.
+//   3. every CTA forms v^T col for its unpivoted columns (4 lanes per column)
+//      and the downdated norms ||col(s+1:)||^2 = ||col(s:)||^2 - col'(s)^2
+//      (recomputed exactly after more than 99 % cancellation);
+//   4. it updates its best column for step s + 1, publishes it (norm, index,
+//      exact trailing sigma, the column from row s + 1) and arrives at the
+//      barrier;
+//   5. the rest of its axpys col -= (v^T col) tau v run while the barrier
+//      completes.
 // Candidate tables are double-buffered by step parity, so one barrier per
 // step suffices.  After l steps the unchosen columns are written in their
 // original order behind the pivots.
@@ -39,8 +44,8 @@ struct CpqrParams {
   int32_t *piv;
   double *Vh;
   double *tau;
-  double2 *cand;      // [2][G] (norm^2, index as a 64-bit integer)
-  int2 *win;          // [2] (CTA, index) of the winner picked by the last arriver
+  double2 *cand;      // [2][G][2]: (norm^2, index as a 64-bit integer), (sigma, 0)
+  double2 *win;       // [2]: (CTA and index as two 32-bit integers, sigma) of the winner
   double *pcol;       // [2][G][l]
   int32_t *counts;    // [G]
   double *gcols;      // G * cpb * l when the slab does not fit in shared memory
@@ -109,12 +114,13 @@ __device__ __forceinline__ bool wait_count(Ctrl *c, unsigned target, unsigned lo
 
 __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   extern __shared__ double sm[];
-  __shared__ double red[32];
   __shared__ double s_v[kMaxL], s_vt[kMaxL];
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
+  __shared__ double s_sigma;
   __shared__ double s_tau, s_beta, s_rv0;
+  __shared__ int s_ok;
 
   const int G = gridDim.x, b = blockIdx.x, l = P.l;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -125,63 +131,71 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   // 1% of the norm^2 when it was last computed exactly: below that the
   // downdated value has lost too many digits and is recomputed
   double *thr = nrm + P.cpb;
-  int *pivoted = reinterpret_cast<int *>(thr + P.cpb);
-  __shared__ int s_ok;
-  unsigned nsteps = 0;  // step barriers passed
-  // step barrier: afterwards s_win_cta / s_win_idx name the winner of slot buf
-  auto step_sync = [&](int buf, int site) {
+  double *wdot = thr + P.cpb;                          // v^T col of this step
+  int *pivoted = reinterpret_cast<int *>(wdot + P.cpb);
+  int *axdone = pivoted + P.cpb;                       // column updated early this step
+
+  // Step barrier k (k = 1, 2, ...): G + 1 increments.  arrive(): after this
+  // CTA's candidate is published; the G-th arriver (it sees G - 1 earlier
+  // arrivals) reads the whole table, publishes the winner with its sigma and
+  // adds the last increment.  Called by warp 0.
+  unsigned nsteps = 0;
+  auto arrive = [&](int buf) {
     ++nsteps;
     const unsigned done = nsteps * (unsigned)(G + 1);
-    __syncthreads();
-    if (warp == 0) {
-      unsigned old = 0;
-      if (lane == 0) old = atom_add_acq_rel(&P.ctrl->cpqr_arrive, 1u);
-      old = __shfl_sync(0xffffffffu, old, 0);
-      __syncwarp();
-      if (old == done - 2u) {
-        // the last arriver: every candidate of this step is in the table
-        double bn = -1.0;
-        int bi = -1, bc = -1;
-        if (G <= 160) {
-          double2 e[5];
+    unsigned old = 0;
+    __syncwarp();
+    if (lane == 0) old = atom_add_acq_rel(&P.ctrl->cpqr_arrive, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    __syncwarp();
+    if (old != done - 2u) return;
+    double bn = -1.0;
+    int bi = -1, bc = -1;
+    if (G <= 160) {
+      double2 e[5];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            const int c = lane + 32 * k;
-            e[k] = c < G ? __ldcg(P.cand + buf * G + c)
-                         : make_double2(-1.0, __longlong_as_double(-1LL));
-          }
-#pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            const int ci = (int)__double_as_longlong(e[k].y);
-            if (better(e[k].x, ci, bn, bi)) { bn = e[k].x; bi = ci; bc = lane + 32 * k; }
-          }
-        } else {
-          for (int c = lane; c < G; c += 32) {
-            const double2 e = __ldcg(P.cand + buf * G + c);
-            const int ci = (int)__double_as_longlong(e.y);
-            if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; }
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const double on = __shfl_xor_sync(0xffffffffu, bn, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-          if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
-        }
-        if (lane == 0) {
-          P.win[buf] = make_int2(bc, bi);
-          red_add_release(&P.ctrl->cpqr_arrive, 1u);
-        }
+      for (int k = 0; k < 5; ++k) {
+        const int c = lane + 32 * k;
+        e[k] = c < G ? __ldcg(P.cand + 2 * (buf * G + c))
+                     : make_double2(-1.0, __longlong_as_double(-1LL));
       }
-      if (lane == 0) {
-        const bool ok = wait_count(P.ctrl, done + P.extra, P.limit_ns, site);
-        s_ok = ok;
-        if (ok) {
-          const int2 w = __ldcg(P.win + buf);
-          s_win_cta = w.x;
-          s_win_idx = w.y;
-        }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const int ci = (int)__double_as_longlong(e[k].y);
+        if (better(e[k].x, ci, bn, bi)) { bn = e[k].x; bi = ci; bc = lane + 32 * k; }
+      }
+    } else {
+      for (int c = lane; c < G; c += 32) {
+        const double2 e = __ldcg(P.cand + 2 * (buf * G + c));
+        const int ci = (int)__double_as_longlong(e.y);
+        if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
+    }
+    if (lane == 0) {
+      const double sig = bc >= 0 ? __ldcg(P.cand + 2 * (buf * G + bc) + 1).x : 0.0;
+      const long long packed = (long long)(unsigned)bc | ((long long)(unsigned)bi << 32);
+      P.win[buf] = make_double2(__longlong_as_double(packed), sig);
+      red_add_release(&P.ctrl->cpqr_arrive, 1u);
+    }
+  };
+  // thread 0: wait for step barrier nsteps, read its winner
+  auto wait_winner = [&](int buf, int site) {
+    if (tid == 0) {
+      const bool ok = wait_count(P.ctrl, nsteps * (unsigned)(G + 1) + P.extra, P.limit_ns, site);
+      s_ok = ok;
+      if (ok) {
+        const double2 w = __ldcg(P.win + buf);
+        const long long packed = __double_as_longlong(w.x);
+        s_win_cta = (int)(unsigned)(packed & 0xffffffffLL);
+        s_win_idx = (int)(unsigned)(packed >> 32);
+        s_sigma = w.y;
       }
     }
     __syncthreads();
@@ -197,6 +211,27 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     }
     __syncthreads();
     return s_ok != 0;
+  };
+  // warp 0: publish candidate jc (local index, key cn) of the next step,
+  // whose column is final through row r0 - 1: the record (cn, index), sigma =
+  // ||col(r0 + 1:)||^2 exactly, and the column from row r0 on
+  auto publish = [&](int buf, int jc, double cn, int r0) {
+    double sg = 0.0;
+    if (jc >= 0) {
+      const double *col = cols + (int64_t)jc * l;
+      double *dst = P.pcol + ((int64_t)buf * G + b) * l;
+      for (int r = r0 + lane; r < l; r += 32) {
+        const double x = col[r];
+        dst[r] = x;
+        if (r > r0) sg = fma(x, x, sg);
+      }
+      sg = warp_sum(sg);
+    }
+    if (lane == 0) {
+      P.cand[2 * (buf * G + b)] =
+          make_double2(jc >= 0 ? cn : -1.0, __longlong_as_double(jc >= 0 ? (long long)(c0 + jc) : -1LL));
+      P.cand[2 * (buf * G + b) + 1] = make_double2(sg, 0.0);
+    }
   };
 
   // nothing to do after an earlier error (its data may be garbage)
@@ -216,31 +251,12 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       nrm[jj] = s;
       thr[jj] = 0.01 * s;
       pivoted[jj] = 0;
+      axdone[jj] = 0;
       if (!isfinite(s)) set_status(P.ctrl, RQLP_ERR_NONFINITE);
     }
   }
   __syncthreads();
-
-  // this CTA's candidate (the per-warp bests in s_bn / s_bi) -> table slot
-  // `buf`, and its column from row from_row on
-  auto publish_best = [&](int buf, int from_row) {
-    if (tid == 0) {
-      double cn = -1.0;
-      int ci = -1;
-      for (int w = 0; w < kWarps; ++w)
-        if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
-      s_win_idx = ci;
-      P.cand[buf * G + b] = make_double2(cn, __longlong_as_double((long long)ci));
-    }
-    __syncthreads();
-    const int ci = s_win_idx;
-    if (ci >= 0) {
-      const double *col = cols + (int64_t)(ci - c0) * l;
-      double *dst = P.pcol + ((int64_t)buf * G + b) * l;
-      for (int r = from_row + tid; r < l; r += kThreads) dst[r] = col[r];
-    }
-  };
-
+  // ---- candidate for step 0 -----------------------------------------------
   {
     double bn = -1.0;
     int bi = -1;
@@ -249,29 +265,36 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     warp_best(bn, bi);
     if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
     __syncthreads();
-    publish_best(0, 0);
+    if (warp == 0) {
+      double cn = s_bn[0];
+      int ci = s_bi[0];
+      for (int w = 1; w < kWarps; ++w)
+        if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
+      publish(0, ci >= 0 ? (int)(ci - c0) : -1, cn, 0);
+      arrive(0);
+    }
   }
-  if (!step_sync(0, 1)) return;
+  if (!wait_winner(0, 1)) return;
 
+  const int sub = lane >> 2, gl = lane & 3;
   for (int s = 0; s < l; ++s) {
     const int buf = s & 1;
-    // ---- 1. winner: picked by the last CTA to arrive at the barrier ----
+    // ---- 1. winner (picked by the last CTA to arrive) and its sigma ----
     const int wc = s_win_cta, wi = s_win_idx;
-    if (wi < 0) { if (tid == 0) set_status(P.ctrl, RQLP_ERR_INVALID_ARG); return; }
+    if (wi < 0 || wc < 0 || wc >= G) {
+      if (tid == 0) set_status(P.ctrl, RQLP_ERR_INVALID_ARG);
+      return;
+    }
     // ---- 2. reflector from the winner's column, rows s..l-1 ----
     const double *xc = P.pcol + ((int64_t)buf * G + wc) * l;
-    double part = 0.0;
-    for (int r = s + tid; r < l; r += kThreads) {
-      const double v = __ldcg(xc + r);
-      s_v[r - s] = v;
-      if (r > s) part = fma(v, v, part);
-    }
-    const double sigma = block_sum(part, red);  // includes a __syncthreads
+    for (int r = s + tid; r < l; r += kThreads) s_v[r - s] = __ldcg(xc + r);
+    __syncthreads();
     // one thread forms H = I - tau v v^T with v(0) = 1 and H x = alpha e_1,
     // alpha = ||x|| >= 0: tau = 1 - x0/alpha, v(1:) = x(1:) / (x0 - alpha),
-    // where x0 > 0 uses x0 - alpha = -sigma / (x0 + alpha) (no cancellation)
+    // where x0 > 0 uses x0 - alpha = -sigma / (x0 + alpha) (no cancellation);
+    // sigma = ||x(1:)||^2 came with the winner's record
     if (tid == 0) {
-      const double x0 = s_v[0];
+      const double x0 = s_v[0], sigma = s_sigma;
       double tau, beta, rv0;
       if (sigma == 0.0) {
         if (x0 >= 0.0) { tau = 0.0; beta = x0; }
@@ -308,7 +331,6 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       for (int r = tid; r < l; r += kThreads) P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : s_v[r - s];
       if (tid == 0) { P.tau[s] = tau; P.piv[s] = wi; }
     }
-    // ---- 3. apply to the slab ----
     // the winner's column is final: rows < s from the slab, beta at s, zeros below
     if ((int)(wi - c0) >= 0 && (int)(wi - c0) < nc && warp == 0) {
       const int jw = (int)(wi - c0);
@@ -317,87 +339,89 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       for (int r = lane; r < l; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
       if (lane == 0) { pivoted[jw] = 1; nrm[jw] = -1.0; }
     }
-    // groups of 8 lanes per column, four columns per warp and two column
-    // sets per pass (independent chains): dot product with v, axpy with
-    // tau v, the downdated trailing norm (recomputed exactly when more than
-    // 99% of it has cancelled since the last exact value), and this warp's
-    // best candidate for step s + 1
+    // ---- 3. dot products v^T col and downdated norms (the axpys wait) ----
+    // groups of 4 lanes per column, eight columns per warp: every FP64 warp
+    // instruction costs the same issue slots whatever its active lanes, so
+    // the reductions are kept short (two levels).  A column whose norm has
+    // cancelled by more than 99 % since its last exact value is updated now
+    // and its norm recomputed.
     double bn = -1.0;
     int bi = -1;
-    {
-      const int sub = lane >> 3, gl = lane & 7;
-      for (int jb = warp * 4; jb < nc; jb += kWarps * 8) {
-        int jj[2];
-        bool act[2];
-        double *col[2];
-        double w[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          jj[k] = jb + 32 * k + sub;
-          act[k] = jj[k] < nc && !pivoted[jj[k]] && (int)(c0 + jj[k]) != wi;
-          col[k] = cols + (int64_t)(act[k] ? jj[k] : 0) * l;
-          double a0 = 0.0, a1 = 0.0;
-          if (act[k]) {
-            int r = s + gl;
-            for (; r + 8 < l; r += 16) {
-              a0 = fma(s_v[r - s], col[k][r], a0);
-              a1 = fma(s_v[r + 8 - s], col[k][r + 8], a1);
-            }
-            if (r < l) a0 = fma(s_v[r - s], col[k][r], a0);
-          }
-          w[k] = a0 + a1;
-        }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
-          w[1] += __shfl_xor_sync(0xffffffffu, w[1], o);
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-          if (act[k])
-            for (int r = s + gl; r < l; r += 8) col[k][r] = fma(-w[k], s_vt[r - s], col[k][r]);
+    for (int jb = warp * 8; jb < nc; jb += kWarps * 8) {
+      const int jj = jb + sub;
+      const bool act = jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi;
+      double *col = cols + (int64_t)(act ? jj : 0) * l;
+      double w = 0.0;
+      if (act)
+        for (int r = s + gl; r < l; r += 4) w = fma(s_v[r - s], col[r], w);
+      w += __shfl_xor_sync(0xffffffffu, w, 2);
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      int need = 0;
+      double nd = 0.0;
+      if (act && gl == 0) {
+        wdot[jj] = w;
+        axdone[jj] = 0;
+        const double rsv = fma(-w, s_vt[0], col[s]);  // new col(s)
+        nd = fma(-rsv, rsv, nrm[jj]);
+        need = __double_as_longlong(nd) <= __double_as_longlong(thr[jj]);
+      }
+      need = __shfl_sync(0xffffffffu, need, lane & ~3);
+      // warp-uniform branch: the shuffles inside need every lane
+      if (__any_sync(0xffffffffu, need)) {
+        if (need)
+          for (int r = s + gl; r < l; r += 4) col[r] = fma(-w, s_vt[r - s], col[r]);
         __syncwarp();
-        int need[2];
-        double nd[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          need[k] = 0;
-          nd[k] = 0.0;
-          if (act[k] && gl == 0) {
-            const double rsv = col[k][s];
-            nd[k] = fma(-rsv, rsv, nrm[jj[k]]);
-            need[k] = __double_as_longlong(nd[k]) <= __double_as_longlong(thr[jj[k]]);
-          }
-          need[k] = __shfl_sync(0xffffffffu, need[k], lane & ~7);
+        double t = 0.0;
+        if (need)
+          for (int r = s + 1 + gl; r < l; r += 4) t = fma(col[r], col[r], t);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (need) nd = t;
+      }
+      if (act && gl == 0) {
+        nrm[jj] = nd;
+        if (need) {
+          thr[jj] = 0.01 * nd;
+          axdone[jj] = 1;
         }
-        // warp-uniform branch: the shuffles inside need every lane
-        if (__any_sync(0xffffffffu, need[0] | need[1])) {
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            double t = 0.0;
-            if (need[k])
-              for (int r = s + 1 + gl; r < l; r += 8) t = fma(col[k][r], col[k][r], t);
-            t += __shfl_xor_sync(0xffffffffu, t, 4);
-            t += __shfl_xor_sync(0xffffffffu, t, 2);
-            t += __shfl_xor_sync(0xffffffffu, t, 1);
-            if (need[k]) nd[k] = t;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-          if (act[k] && gl == 0) {
-            nrm[jj[k]] = nd[k];
-            if (need[k]) thr[jj[k]] = 0.01 * nd[k];
-            if (better(nd[k], (int)(c0 + jj[k]), bn, bi)) { bn = nd[k]; bi = (int)(c0 + jj[k]); }
-          }
+        if (better(nd, (int)(c0 + jj), bn, bi)) { bn = nd; bi = (int)(c0 + jj); }
+      }
+    }
+    warp_best(bn, bi);
+    if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
+    __syncthreads();
+    // this CTA's candidate for step s + 1 (every thread reads the same table)
+    int jc = -1;
+    double cn = -1.0;
+    if (s + 1 < l) {
+      int ci = -1;
+      for (int w = 0; w < kWarps; ++w)
+        if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
+      jc = ci >= 0 ? (int)(ci - c0) : -1;
+    }
+    // ---- 4. warp 0: update the candidate, publish it, arrive ----
+    if (warp == 0 && s + 1 < l) {
+      if (jc >= 0 && !axdone[jc]) {
+        double *col = cols + (int64_t)jc * l;
+        const double wj = wdot[jc];
+        for (int r = s + lane; r < l; r += 32) col[r] = fma(-wj, s_vt[r - s], col[r]);
+        __syncwarp();
+      }
+      publish(buf ^ 1, jc, cn, s + 1);
+      arrive(buf ^ 1);
+    }
+    // ---- 5. the remaining axpys, while the barrier completes ----
+    for (int jb = warp * 8; jb < nc; jb += kWarps * 8) {
+      const int jj = jb + sub;
+      if (jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi && jj != jc && !axdone[jj]) {
+        double *col = cols + (int64_t)jj * l;
+        const double w = wdot[jj];
+        for (int r = s + gl; r < l; r += 4) col[r] = fma(-w, s_vt[r - s], col[r]);
       }
     }
     if (s + 1 < l) {
-      warp_best(bn, bi);
-      if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
       __syncthreads();
-      publish_best(buf ^ 1, s + 1);
-      if (!step_sync(buf ^ 1, 2)) return;
+      if (!wait_winner(buf ^ 1, 2)) return;
     }
   }
 
@@ -407,6 +431,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     for (int jj = 0; jj < nc; ++jj) mine += pivoted[jj] ? 0 : 1;
     P.counts[b] = mine;
   }
+  __syncthreads();
   if (!final_sync(3)) return;
   __shared__ int s_prefix;
   if (tid == 0) {
@@ -454,7 +479,7 @@ Plan plan_for(int64_t n, int l) {
   if (G < 1) G = 1;
   int cpb = (int)((n + G - 1) / G);
   G = (int)((n + cpb - 1) / cpb);
-  const size_t state = (size_t)cpb * (2 * sizeof(double) + sizeof(int));
+  const size_t state = (size_t)cpb * (3 * sizeof(double) + 2 * sizeof(int));
   const size_t slab = (size_t)cpb * l * sizeof(double);
   p.use_smem = (slab + state <= 190 * 1024) ? 1 : 0;
   p.smem = (p.use_smem ? slab : 0) + state;
@@ -468,7 +493,7 @@ Plan plan_for(int64_t n, int l) {
 size_t cpqr_ws_bytes(int64_t n, int l) {
   const size_t G = kMaxGrid;
   size_t b = 0;
-  b += 2 * G * sizeof(double2);
+  b += 4 * G * sizeof(double2);
   b += 256;  // winner records
   b += 2 * G * (size_t)l * sizeof(double);
   b += G * sizeof(int32_t);
@@ -480,7 +505,7 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   const Plan pl = plan_for(n, l);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(2 * (size_t)pl.G * sizeof(double2)) + up(2 * sizeof(int2)) +
+  return up(4 * (size_t)pl.G * sizeof(double2)) + up(2 * sizeof(double2)) +
          up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
 }
 
@@ -505,8 +530,8 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   CpqrParams P;
   P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
-  P.cand = reinterpret_cast<double2 *>(take(2 * (size_t)pl.G * sizeof(double2)));
-  P.win = reinterpret_cast<int2 *>(take(2 * sizeof(int2)));
+  P.cand = reinterpret_cast<double2 *>(take(4 * (size_t)pl.G * sizeof(double2)));
+  P.win = reinterpret_cast<double2 *>(take(2 * sizeof(double2)));
   P.pcol = reinterpret_cast<double *>(take(2 * (size_t)pl.G * l * sizeof(double)));
   P.counts = reinterpret_cast<int32_t *>(take((size_t)pl.G * sizeof(int32_t)));
   P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));

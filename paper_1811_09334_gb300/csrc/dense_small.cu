@@ -123,6 +123,89 @@ k_form_q(const double *__restrict__ Vh, int64_t ldv, const double *__restrict__ 
   for (int i = lane; i < rows; i += 32) Q[(int64_t)i * ldq + c] = x[i];
 }
 
+// Triangular solves for a batch of row vectors, one warp per vector x of
+// length n <= kMaxL (lane k holds entries k, k + 32, ...), right-looking so
+// that each step is one multiply and a few lane-parallel FMAs:
+//   backward = false: y U = x  (y_j = s_j / U_jj, then s_k -= y_j U_jk, k > j)
+//   backward = true:  U y = x  with U symmetric in storage, only its strictly
+//                     upper part used (y_t = s_t / U_tt, s_i -= U_ti y_t, i < t)
+// 1 / U_jj comes from `dinv` when given, else from U's diagonal.
+// U is staged in shared memory (n x n, ld n) when the launch gives it room
+// (dynamic smem >= n^2 doubles): every step then reads its row at shared-
+// memory latency instead of an L2 round trip.
+__global__ void __launch_bounds__(128)
+k_tri_rows(const double *__restrict__ Ug, int64_t ldug, const double *__restrict__ dinv, int n,
+           const double *__restrict__ X, int64_t ldx, double *__restrict__ Y, int64_t ldy,
+           int nvec, int backward, int staged) {
+  extern __shared__ double us[];
+  __shared__ double di[kMaxL];
+  const double *U = Ug;
+  int64_t ldu = ldug;
+  if (staged) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      us[e] = Ug[(int64_t)i * ldug + j];
+    }
+    U = us;
+    ldu = n;
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    di[j] = dinv ? dinv[j] : rcp_fast(Ug[(int64_t)j * ldug + j]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int vec = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (vec >= nvec) return;
+  constexpr int kSlots = kMaxL / 32;
+  double sv[kSlots];
+#pragma unroll
+  for (int q = 0; q < kSlots; ++q) {
+    const int k = 32 * q + lane;
+    sv[q] = k < n ? X[(int64_t)vec * ldx + k] : 0.0;
+  }
+  if (!backward) {
+#pragma unroll
+    for (int jb = 0; jb < kSlots; ++jb) {
+      if (32 * jb >= n) break;
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = 32 * jb + jj;
+        if (j >= n) break;
+        const double yj = __shfl_sync(0xffffffffu, sv[jb], jj) * di[j];
+        if (lane == jj) sv[jb] = yj;
+        const double *Uj = U + (int64_t)j * ldu;
+#pragma unroll
+        for (int q = jb; q < kSlots; ++q) {
+          if (32 * q >= n) break;  // warp-uniform: no FP64 issue for empty slots
+          const int k = 32 * q + lane;
+          if (k > j && k < n) sv[q] = fma(-yj, Uj[k], sv[q]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int tb = kSlots - 1; tb >= 0; --tb) {
+      if (32 * tb >= n) continue;
+      for (int tt = 31; tt >= 0; --tt) {
+        const int t = 32 * tb + tt;
+        if (t >= n) continue;
+        const double yt = __shfl_sync(0xffffffffu, sv[tb], tt) * di[t];
+        if (lane == tt) sv[tb] = yt;
+        const double *Ut = U + (int64_t)t * ldu;  // U_ti = U_it (symmetric storage)
+#pragma unroll
+        for (int q = 0; q <= tb; ++q) {
+          if (32 * q >= t) break;  // warp-uniform
+          const int i = 32 * q + lane;
+          if (i < t) sv[q] = fma(-Ut[i], yt, sv[q]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kSlots; ++q) {
+    const int k = 32 * q + lane;
+    if (k < n) Y[(int64_t)vec * ldy + k] = sv[q];
+  }
+}
+
 // S = tril(M) + tril(M, -1)^T
 __global__ void k_copyltu(const double *__restrict__ M, int l, double *__restrict__ S) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
@@ -176,7 +259,11 @@ inline int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-cudaError_t chol_init() { return cholqr_init(); }
+cudaError_t chol_init() {
+  const cudaError_t e = cudaFuncSetAttribute(k_tri_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             160 * 1024);
+  return e == cudaSuccess ? cholqr_init() : e;
+}
 
 cudaError_t trinv_upper(const double *R, int l, double *Rinv, const int *skip_unless,
                         cudaStream_t st) {
@@ -267,9 +354,44 @@ cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t tri_rows(const double *U, int64_t ldu, const double *dinv, int n, const double *X,
+                     int64_t ldx, double *Y, int64_t ldy, int nvec, bool backward,
+                     cudaStream_t st) {
+  if (n > kMaxL || n <= 0 || nvec <= 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)n * n * sizeof(double);
+  const bool staged = smem <= 160 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_tri_rows,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               160 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tri_rows<<<(unsigned)((nvec + 3) / 4), 128, staged ? smem : 0, st>>>(
+      U, ldu, dinv, n, X, ldx, Y, ldy, nvec, backward ? 1 : 0, staged ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
-                   double *Q, int64_t ldq, cudaStream_t st) {
+                   double *Q, int64_t ldq, cudaStream_t st, double *scratch) {
   if (rows > kMaxL || t <= 0) return cudaErrorInvalidValue;
+  if (scratch && rows == t) {
+    // compact WY (UT transform): H_0 ... H_{t-1} = I - V T V^T with
+    // T^{-1} = diag(1 / tau) + striu(V^T V), so Q = I - V W, W = T V^T:
+    // S = V^T V, row c of W^T solves T^{-1} w = (row c of V)^T, then one
+    // small product.  A handful of short launches instead of t dependent
+    // reflector applications per column.
+    double *S = scratch, *Wt = scratch + (int64_t)t * t;
+    cudaError_t e = gemm_small(true, false, Vh, ldv, Vh, ldv, S, t, t, t, rows, 1.0, 0.0, nullptr,
+                               st);
+    if (e == cudaSuccess) e = tri_rows(S, t, tau, t, Vh, ldv, Wt, t, t, true, st);
+    if (e == cudaSuccess) e = set_identity(Q, rows, t, ldq, st);
+    if (e == cudaSuccess)
+      e = gemm_small(false, true, Vh, ldv, Wt, t, Q, ldq, rows, t, t, -1.0, 1.0, nullptr, st);
+    return e;
+  }
   // one warp per CTA: each column is a chain of t reflector applications,
   // so the columns are spread over as many SMs as possible
   k_form_q<<<t, 32, 0, st>>>(Vh, ldv, tau, (int)rows, t, Q, ldq);

@@ -134,7 +134,10 @@ __global__ void k_reduce_parts(const double *__restrict__ part, int S, int64_t p
 // Small products (M N <= kSmallMN): one thread per entry of C, four
 // independent accumulators over K.  An l x l x l product (l ~ 100) on the
 // tiled kernel occupies a handful of SMs; here it spreads over ~50 CTAs.
+// op(A)(i, k) = A[i lda + k] or, with TA, A[k lda + i]; op(B)(k, j) =
+// B[k ldb + j] or, with TB, B[j ldb + k].
 constexpr int64_t kSmallMN = 128 * 128;
+template <bool TA, bool TB>
 __global__ void __launch_bounds__(256)
 k_gemm_small(const double *__restrict__ A, int64_t lda, const double *__restrict__ B, int64_t ldb,
              double *__restrict__ C, int64_t ldc, int64_t M, int64_t N, int64_t K, double alpha,
@@ -143,16 +146,17 @@ k_gemm_small(const double *__restrict__ A, int64_t lda, const double *__restrict
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * N) return;
   const int64_t i = e / N, j = e - i * N;
-  const double *a = A + i * lda;
+  auto a = [&](int64_t k) { return TA ? A[k * lda + i] : A[i * lda + k]; };
+  auto bb = [&](int64_t k) { return TB ? B[j * ldb + k] : B[k * ldb + j]; };
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int64_t k = 0;
   for (; k + 3 < K; k += 4) {
-    s0 = fma(a[k], B[k * ldb + j], s0);
-    s1 = fma(a[k + 1], B[(k + 1) * ldb + j], s1);
-    s2 = fma(a[k + 2], B[(k + 2) * ldb + j], s2);
-    s3 = fma(a[k + 3], B[(k + 3) * ldb + j], s3);
+    s0 = fma(a(k), bb(k), s0);
+    s1 = fma(a(k + 1), bb(k + 1), s1);
+    s2 = fma(a(k + 2), bb(k + 2), s2);
+    s3 = fma(a(k + 3), bb(k + 3), s3);
   }
-  for (; k < K; ++k) s0 = fma(a[k], B[k * ldb + j], s0);
+  for (; k < K; ++k) s0 = fma(a(k), bb(k), s0);
   double v = alpha * ((s0 + s1) + (s2 + s3));
   if (beta != 0.0) v = fma(beta, C[i * ldc + j], v);
   C[i * ldc + j] = v;
@@ -190,18 +194,32 @@ size_t gemm_f64_part_bytes(int64_t M, int64_t N, int64_t K) {
   return s > 1 ? (size_t)s * M * N * sizeof(double) : 0;
 }
 
+cudaError_t gemm_small(bool transA, bool transB, const double *A, int64_t lda, const double *B,
+                       int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                       double alpha, double beta, const int *skip_unless, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((M * N + 255) / 256);
+#define LAUNCH_SMALL(TA, TB)                                                                      \
+  k_gemm_small<TA, TB><<<blocks, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, alpha, beta,     \
+                                               skip_unless)
+  if (transA) {
+    if (transB) LAUNCH_SMALL(true, true); else LAUNCH_SMALL(true, false);
+  } else {
+    if (transB) LAUNCH_SMALL(false, true); else LAUNCH_SMALL(false, false);
+  }
+#undef LAUNCH_SMALL
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const double *B,
                      int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                      double alpha, double beta, double *part, const int32_t *rowmap,
                      const int *skip_unless, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (!transA && a_dtype == RQLP_F64 && rowmap == nullptr && M * N <= kSmallMN) {
-    k_gemm_small<<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(
-        reinterpret_cast<const double *>(A), lda, B, ldb, C, ldc, M, N, K, alpha, beta,
-        skip_unless);
-    count_launch();
-    return cudaGetLastError();
-  }
+  if (a_dtype == RQLP_F64 && rowmap == nullptr && M * N <= kSmallMN)
+    return gemm_small(transA, false, reinterpret_cast<const double *>(A), lda, B, ldb, C, ldc, M,
+                      N, K, alpha, beta, skip_unless, st);
   int64_t S = part ? gemm_f64_splits(M, N, K) : 1;
   const bool use_part = (S > 1) || (rowmap != nullptr);
   if (use_part && !part) return cudaErrorInvalidValue;

@@ -66,6 +66,11 @@ size_t gemm_f64_part_bytes(int64_t M, int64_t N, int64_t K);
 // split-K scratch of gemm_f64_part_bytes(M, N, K) bytes (M * N doubles at
 // least when rowmap is used).  skip_unless: the kernels return at once when
 // *skip_unless == 0 (device-side conditional passes); may be null.
+// C = alpha op(A) op(B) + beta C for small products (one thread per entry of C;
+// meant for M N <= 16384), FP64
+cudaError_t gemm_small(bool transA, bool transB, const double *A, int64_t lda, const double *B,
+                       int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                       double alpha, double beta, const int *skip_unless, cudaStream_t st);
 cudaError_t gemm_f64(bool transA, int a_dtype, const void *A, int64_t lda, const double *B,
                      int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                      double alpha, double beta, double *part, const int32_t *rowmap,
@@ -107,7 +112,13 @@ cudaError_t zero_triangle(double *T, int l, int64_t ld, bool strict_lower, cudaS
 // Form Q = H_0 H_1 ... H_{t-1} [I; 0] (rows x t, ld ldq) from reflectors stored
 // as columns of Vh (rows x t, ld ldv; v_s[s] = 1 implicit, zeros above) and tau.
 cudaError_t form_q(const double *Vh, int64_t ldv, const double *tau, int64_t rows, int t,
-                   double *Q, int64_t ldq, cudaStream_t st);
+                   double *Q, int64_t ldq, cudaStream_t st, double *scratch = nullptr);
+// Row-vector triangular solves (one warp per vector, n <= kMaxL): y U = x, or
+// with backward U y = x using only U's strictly upper part and U symmetric in
+// storage; 1 / U_jj from dinv (length n) when given, else from U.
+cudaError_t tri_rows(const double *U, int64_t ldu, const double *dinv, int n, const double *X,
+                     int64_t ldx, double *Y, int64_t ldy, int nvec, bool backward,
+                     cudaStream_t st);
 
 // ---- cholqr.cu: one CholeskyQR pass on a rows x l panel -------------------
 int64_t gram_chunks(int64_t rows);
