@@ -288,6 +288,25 @@ int rqlp_profile_begin(void);
  * regions (count[c]).  Either array may be NULL. */
 int rqlp_profile_end(double *ms, long long *count, int nclass);
 
+/* ------------------------------------------------------------------------
+ * Self-test of the device arithmetic helpers (a diagnostic; the paper has no
+ * counterpart).  The kernels round FP64 to FP32 and back with integer
+ * operations (a conversion instruction would occupy the scarce FP64 unit)
+ * and take reciprocals and reciprocal square roots from an FP32 estimate
+ * refined in FP64.  This entry point checks them on the device against
+ * CUDA's own operations over `count` pseudo-random inputs each:
+ *   fails[0]: FP64 -> FP32 round-to-nearest-even, bit-exact (inputs in the
+ *             FP32 normal range);
+ *   fails[1]: FP32 -> FP64, bit-exact (normal floats);
+ *   fails[2]: reciprocal, relative error above 2^-51 (4 units of roundoff);
+ *   fails[3]: reciprocal square root, relative error above 2^-51.
+ * fails: host array of 4 ints, written on return (the call synchronizes the
+ * stream).  count in [1, 2^24].  Returns RQLP_OK, RQLP_ERR_INVALID_ARG or
+ * RQLP_ERR_CUDA.  Uses a 16-byte static device counter, so concurrent calls
+ * race; serialize them.
+ */
+int rqlp_selftest(int32_t count, int32_t *fails, rqlp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

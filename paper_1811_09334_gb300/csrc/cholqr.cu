@@ -52,7 +52,7 @@ k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int r
   const int nr = (int)min((int64_t)rc, rows - r0);
   for (int e = threadIdx.x; e < nr * lp; e += blockDim.x) {
     const int r = e / lp, c = e - r * lp;
-    xs[e] = (c < l) ? (T)X[(r0 + r) * ldx + c] : (T)0;
+    xs[e] = (c < l) ? from_f64<T>(X[(r0 + r) * ldx + c]) : (T)0;
   }
   __syncthreads();
   const int nb = (l + 3) / 4;
@@ -90,7 +90,7 @@ k_gram_sym(const double *__restrict__ X, int64_t rows, int l, int64_t ldx, int r
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int j = 4 * bj + b;
-        if (j < l && j >= i) out[(int64_t)i * l + j] = (double)acc[a][b];
+        if (j < l && j >= i) out[(int64_t)i * l + j] = to_f64(acc[a][b]);
       }
     }
   }
@@ -610,11 +610,11 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int a = 16 * g + i;
-      v[i] = (a < l && c >= a && c < l) ? (float)(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
+      v[i] = (a < l && c >= a && c < l) ? d2f_rn(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
                                         : 0.0f;
     }
     for (int a = tid; a < l; a += blockDim.x)
-      s_thr[a] = (float)((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
+      s_thr[a] = d2f_rn((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
     if (tid == 0) s_f = 0;
     __syncthreads();
     for (int jb = 0; jb * 16 < l; ++jb) {
@@ -637,7 +637,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
         if (g == jb && c >= j && c < l) {
           const float y = v[ii] * s_rs;
           rowbuf[buf][c] = y;
-          R[(int64_t)j * l + c] = (double)y;
+          R[(int64_t)j * l + c] = f2d(y);
         }
         __syncthreads();
         const float rjc = (c >= j && c < l) ? rowbuf[buf][c] : 0.0f;
@@ -676,7 +676,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
   for (int bk = warp; bk < nblk; bk += (int)(blockDim.x >> 5)) {
     const int c0 = bk * kB, bs = min(kB, l - c0);
     const int cc = lane;
-    auto U = [&](int i, int t) { return (float)R[(int64_t)(c0 + i) * l + c0 + t]; };
+    auto U = [&](int i, int t) { return d2f_rn(R[(int64_t)(c0 + i) * l + c0 + t]); };
     const float dl = (lane < bs) ? 1.0f / U(lane, lane) : 0.0f;
     float x[kB];
 #pragma unroll
@@ -695,7 +695,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
     if (cc < bs)
 #pragma unroll
       for (int i = 0; i < kB; ++i)
-        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = (double)x[i];
+        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = f2d(x[i]);
   }
 }
 
@@ -790,7 +790,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   const int nr = (int)min((int64_t)kApplyRows, rows - r0);
   for (int e = threadIdx.x; e < kApplyRows * l; e += blockDim.x) {
     const int r = e / l, c = e - r * l;
-    qs[r * lp + c] = (r < nr) ? (T)X[(r0 + r) * ldx + c] : (T)0;
+    qs[r * lp + c] = (r < nr) ? from_f64<T>(X[(r0 + r) * ldx + c]) : (T)0;
   }
   // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
   // warp needs the same rows of inv(R[b, b]), so the triangular product
@@ -801,11 +801,11 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     __syncthreads();
     for (int e = threadIdx.x; e < c0 * kB; e += blockDim.x) {
       const int t = e / kB, j = e - t * kB;
-      rc[e] = (j < bs) ? (T)R[(int64_t)t * l + c0 + j] : (T)0;
+      rc[e] = (j < bs) ? from_f64<T>(R[(int64_t)t * l + c0 + j]) : (T)0;
     }
     for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) {
       const int i = e / kB, j = e - i * kB;
-      dv[e] = (i < bs && j < bs) ? (T)Dinv[(int64_t)(c0 + i) * l + c0 + j] : (T)0;
+      dv[e] = (i < bs && j < bs) ? from_f64<T>(Dinv[(int64_t)(c0 + i) * l + c0 + j]) : (T)0;
     }
     __syncthreads();
     T acc[4];
@@ -837,7 +837,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   __syncthreads();
   for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
     const int rr = e / l, c = e - rr * l;
-    Q[(r0 + rr) * ldq + c] = (double)qs[rr * lp + c];
+    Q[(r0 + rr) * ldq + c] = to_f64(qs[rr * lp + c]);
   }
 }
 

@@ -137,6 +137,53 @@ __device__ __forceinline__ double rsqrt_fast(double x) {
   return fma(y0, r * fma(0.375, r, 0.5), y0);       // y0 (1 + r/2 + 3 r^2 / 8)
 }
 
+// FP64 <-> FP32 conversions on the integer pipe: a conversion instruction
+// would occupy the FP64 unit (~64 clocks per warp instruction here), which
+// dominates kernels that round every element.  d2f_rn rounds to nearest,
+// ties to even (IEEE 754 roundTiesToEven on the 29 dropped significand
+// bits); results below the FP32 normal range flush to signed zero, results
+// beyond it become infinity, NaN stays NaN.  f2d is exact for normal floats
+// and zero (FP32 subnormals flush to zero).
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0x7ff)
+    return __uint_as_float(sign | 0x7f800000u |
+                           ((b & 0xfffffffffffffULL) != 0 ? 0x400000u : 0u));
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7f800000u);
+  unsigned f = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned rest = (unsigned)(b & 0x1fffffffULL), half = 0x10000000u;
+  if (rest > half || (rest == half && (f & 1u))) f += 1u;  // a carry into the exponent is right
+  return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 0xffu) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ULL | m));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | m));
+}
+
+template <typename T>
+__device__ __forceinline__ float as_f32(T x);
+template <>
+__device__ __forceinline__ float as_f32<double>(double x) { return d2f_rn(x); }
+template <>
+__device__ __forceinline__ float as_f32<float>(float x) { return x; }
+// FP64 data into the working precision T of a kernel, and back
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return d2f_rn(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d(x); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

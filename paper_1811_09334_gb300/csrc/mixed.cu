@@ -322,8 +322,8 @@ __global__ void k_sum_parts_f32(const float *__restrict__ part, int S, int64_t s
     const int64_t i = e / ncols;
     const int j = (int)(e - i * ncols);
     double s = 0.0;
-    for (int z = 0; z < S; ++z) s += (double)part[(int64_t)z * split_stride + i * ldp + j];
-    if (rscale) s /= (double)rscale[i] * (double)cscale[j];
+    for (int z = 0; z < S; ++z) s += f2d(part[(int64_t)z * split_stride + i * ldp + j]);
+    if (rscale) s /= f2d(rscale[i]) * f2d(cscale[j]);
     C[i * ldc + j] = s;
   }
 }
@@ -345,7 +345,7 @@ k_absmax(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, float *__re
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       if (r < nr) {
-        const float v = fabsf((float)A[(i0 + r) * lda + j]);
+        const float v = fabsf(as_f32(A[(i0 + r) * lda + j]));
         cm = fmaxf(cm, v);
         rmx[r] = fmaxf(rmx[r], v);
       }
@@ -395,7 +395,7 @@ k_quant_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, const floa
   for (int k = ty; k < 32; k += 8) {
     const int64_t i = i0 + k, j = j0 + tx;
     if (i < m && j < n) {
-      const float v = (float)A[i * lda + j];
+      const float v = as_f32(A[i * lda + j]);
       A8[i * ld1 + j] = __nv_cvt_float_to_fp8(v * rscale[i], __NV_SATFINITE, __NV_E4M3);
       t[k][tx] = __nv_cvt_float_to_fp8(v * cscale[j], __NV_SATFINITE, __NV_E4M3);
     }
@@ -415,7 +415,7 @@ __global__ void k_quant_skinny_t(const double *__restrict__ S, int64_t K, int l,
   __shared__ float s_sc;
   for (int c = blockIdx.x; c < l; c += gridDim.x) {
     float mx = 0.f;
-    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, fabsf((float)S[k * lds + c]));
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, fabsf(d2f_rn(S[k * lds + c])));
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -428,7 +428,7 @@ __global__ void k_quant_skinny_t(const double *__restrict__ S, int64_t K, int l,
     __syncthreads();
     const float sc = s_sc;
     for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
-      S8[(int64_t)c * ldk + k] = __nv_cvt_float_to_fp8((float)S[k * lds + c] * sc, __NV_SATFINITE,
+      S8[(int64_t)c * ldk + k] = __nv_cvt_float_to_fp8(d2f_rn(S[k * lds + c]) * sc, __NV_SATFINITE,
                                                        __NV_E4M3);
     __syncthreads();
   }
@@ -453,28 +453,27 @@ k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloa
   for (int k = 0; k < 4; ++k) {
     const int r = ty + 8 * k;
     const int64_t i = i0 + r, j = j0 + 2 * tx;
-    double v0 = 0.0, v1 = 0.0;  // FP64 or FP32 source values
+    // one FP64 -> FP32 rounding per element (on the integer pipe), the split
+    // in FP32 (FP64 arithmetic runs at 2 operations per clock per SM on this
+    // part): f - h is exact in FP32, and the FP32 rounding of v (2^-24) is far
+    // below the precision of the pair (about 2^-17)
+    float f0 = 0.0f, f1 = 0.0f;
     if (i < m) {
       if (vec && j + 1 < n) {
         if (sizeof(T) == 8) {
           const double2 p = *reinterpret_cast<const double2 *>(A + i * lda + j);
-          v0 = p.x;
-          v1 = p.y;
+          f0 = d2f_rn(p.x);
+          f1 = d2f_rn(p.y);
         } else {
           const float2 p = *reinterpret_cast<const float2 *>(A + i * lda + j);
-          v0 = p.x;
-          v1 = p.y;
+          f0 = p.x;
+          f1 = p.y;
         }
       } else {
-        if (j < n) v0 = (double)A[i * lda + j];
-        if (j + 1 < n) v1 = (double)A[i * lda + j + 1];
+        if (j < n) f0 = as_f32(A[i * lda + j]);
+        if (j + 1 < n) f1 = as_f32(A[i * lda + j + 1]);
       }
     }
-    // one FP64 -> FP32 conversion per element, the split in FP32 (FP64
-    // arithmetic runs at 2 operations per clock per SM on this part): f - h
-    // is exact in FP32, and the FP32 rounding of v (2^-24) is far below the
-    // precision of the pair (about 2^-17)
-    const float f0 = (float)v0, f1 = (float)v1;
     const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
     const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
     const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
@@ -530,10 +529,11 @@ __global__ void k_split_skinny_t(const double *__restrict__ S, int64_t K, int l,
        e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / K);
     const int64_t k = e - (int64_t)c * K;
-    const double v = S[k * lds + c];
-    const __nv_bfloat16 h = __double2bfloat16(v);
+    // the pair split in FP32, as for A
+    const float f = d2f_rn(S[k * lds + c]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
     Sh[(int64_t)c * ldk + k] = h;
-    if (with_lo) Sl[(int64_t)c * ldk + k] = __double2bfloat16(v - (double)__bfloat162float(h));
+    if (with_lo) Sl[(int64_t)c * ldk + k] = __float2bfloat16_rn(f - __bfloat162float(h));
   }
 }
 

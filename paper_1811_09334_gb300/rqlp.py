@@ -73,6 +73,7 @@ _SIGS = {
     "rqlp_orth": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_i64, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr_static": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_i32, _c_p]),
+    "rqlp_selftest": (_c_i32, [_c_i32, _c_p, _c_p]),
     "rqlp_batched_workspace_size": (_c_sz, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
                                             ctypes.POINTER(BatchTuning)]),
     "rqlp_batched_create": (_c_i32, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
@@ -96,6 +97,15 @@ PROFILE_CLASSES = ("products_with_A", "cpqr_of_B", "cholqr_gram", "cholqr_choles
 
 def launch_count() -> int:
     return int(lib().rqlp_launch_count())
+
+
+def selftest(count: int = 1 << 20, stream=None):
+    """Device arithmetic helpers against CUDA's operations (include/rqlp.h,
+    rqlp_selftest): mismatches for FP64->FP32, FP32->FP64, reciprocal and
+    reciprocal square root."""
+    fails = (ctypes.c_int32 * 4)()
+    _check(lib().rqlp_selftest(count, ctypes.cast(fails, _c_p), _stream(stream)), "rqlp_selftest")
+    return list(fails)
 
 
 def profile_begin():

@@ -231,3 +231,10 @@ def test_brqlp_large_blocks_bf16x3(R):
     ref = O.brqlp(pr.A, pr.k, pr.p, 20, Om, pivot2=True)
     lv = out["Lvalues"].cpu().numpy()
     assert np.max(np.abs(lv - ref["Lvalues"]) / ref["Lvalues"]) <= 1e-3
+
+
+# ------------------------------------------------------------------ device helpers
+def test_device_arithmetic_helpers_match_cuda(R):
+    # integer-pipe FP64/FP32 roundings bit-exact, FP32-seeded reciprocal and
+    # reciprocal square root within 2^-51 relative, on 2^20 inputs each
+    assert R.selftest(1 << 20) == [0, 0, 0, 0]
