@@ -131,9 +131,11 @@ __global__ void k_reduce_parts(const double *__restrict__ part, int S, int64_t p
     C[oi * ldc + j] = v;
   }
 }
-// Small products (M N <= kSmallMN): one thread per entry of C, four
-// independent accumulators over K.  An l x l x l product (l ~ 100) on the
-// tiled kernel occupies a handful of SMs; here it spreads over ~50 CTAs.
+// Small products (M N <= kSmallMN): four consecutive threads per entry of C
+// split K among themselves (k = g, g + 4, ...) and combine with two shuffles.
+// Every FP64 warp instruction costs ~64 clocks of an SM sub-partition here,
+// so the work per warp, not the thread count, sets the time: an l x l x l
+// product (l ~ 100) runs ~K/4 dependent FMAs per thread over ~200 CTAs.
 // op(A)(i, k) = A[i lda + k] or, with TA, A[k lda + i]; op(B)(k, j) =
 // B[k ldb + j] or, with TB, B[j ldb + k].
 constexpr int64_t kSmallMN = 128 * 128;
@@ -143,23 +145,29 @@ k_gemm_small(const double *__restrict__ A, int64_t lda, const double *__restrict
              double *__restrict__ C, int64_t ldc, int64_t M, int64_t N, int64_t K, double alpha,
              double beta, const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M * N) return;
-  const int64_t i = e / N, j = e - i * N;
-  auto a = [&](int64_t k) { return TA ? A[k * lda + i] : A[i * lda + k]; };
-  auto bb = [&](int64_t k) { return TB ? B[j * ldb + k] : B[k * ldb + j]; };
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t k = 0;
-  for (; k + 3 < K; k += 4) {
-    s0 = fma(a(k), bb(k), s0);
-    s1 = fma(a(k + 1), bb(k + 1), s1);
-    s2 = fma(a(k + 2), bb(k + 2), s2);
-    s3 = fma(a(k + 3), bb(k + 3), s3);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = (int)(t & 3);
+  const int64_t e = t >> 2;
+  const bool valid = e < M * N;
+  const int64_t i = valid ? e / N : 0, j = valid ? e - i * N : 0;
+  double s0 = 0.0, s1 = 0.0;
+  if (valid) {
+    int64_t k = g;
+    for (; k + 4 < K; k += 8) {
+      s0 = fma(TA ? A[k * lda + i] : A[i * lda + k], TB ? B[j * ldb + k] : B[k * ldb + j], s0);
+      const int64_t k1 = k + 4;
+      s1 = fma(TA ? A[k1 * lda + i] : A[i * lda + k1], TB ? B[j * ldb + k1] : B[k1 * ldb + j], s1);
+    }
+    if (k < K) s0 = fma(TA ? A[k * lda + i] : A[i * lda + k], TB ? B[j * ldb + k] : B[k * ldb + j], s0);
   }
-  for (; k < K; ++k) s0 = fma(a(k), bb(k), s0);
-  double v = alpha * ((s0 + s1) + (s2 + s3));
-  if (beta != 0.0) v = fma(beta, C[i * ldc + j], v);
-  C[i * ldc + j] = v;
+  double s = s0 + s1;
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (valid && g == 0) {
+    double v = alpha * s;
+    if (beta != 0.0) v = fma(beta, C[i * ldc + j], v);
+    C[i * ldc + j] = v;
+  }
 }
 }  // namespace
 
@@ -198,7 +206,7 @@ cudaError_t gemm_small(bool transA, bool transB, const double *A, int64_t lda, c
                        int64_t ldb, double *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                        double alpha, double beta, const int *skip_unless, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((M * N + 255) / 256);
+  const unsigned blocks = (unsigned)((4 * M * N + 255) / 256);
 #define LAUNCH_SMALL(TA, TB)                                                                      \
   k_gemm_small<TA, TB><<<blocks, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, alpha, beta,     \
                                                skip_unless)
