@@ -7,8 +7,8 @@
 // one grid barrier:
 //   1. the winner of step s (largest trailing norm, ties to the lowest
 //      original column index) was picked by the last CTA to arrive at the
-//      barrier; every CTA reads its record: the CTA that holds it and the
-//      exact ||x(s+1:)||^2 of its column;
+//      barrier; every CTA reads its record: the CTA that holds it, x0 and
+//      the exact ||x(s+1:)||^2 of its column;
 //   2. every CTA builds the same Householder reflector from the winner's
 //      column, mapping it to +alpha e_s (non-negative R(s, s));
 //   3. every CTA forms v^T col for its unpivoted columns (4 lanes per column)
@@ -44,8 +44,8 @@ struct CpqrParams {
   int32_t *piv;
   double *Vh;
   double *tau;
-  double2 *cand;      // [2][G][2]: (norm^2, index as a 64-bit integer), (sigma, 0)
-  double2 *win;       // [2]: (CTA and index as two 32-bit integers, sigma) of the winner
+  double2 *cand;      // [2][G][2]: (norm^2, index as a 64-bit integer), (sigma, x0)
+  double2 *win;       // [2][2]: (CTA and index as two 32-bit integers, sigma), (x0, 0)
   double *pcol;       // [2][G][l]
   int32_t *counts;    // [G]
   double *gcols;      // G * cpb * l when the slab does not fit in shared memory
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
-  __shared__ double s_sigma;
+  __shared__ double s_sigma, s_x0;
   __shared__ double s_tau, s_beta, s_rv0;
   __shared__ int s_ok;
 
@@ -149,26 +149,32 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     old = __shfl_sync(0xffffffffu, old, 0);
     __syncwarp();
     if (old != done - 2u) return;
-    double bn = -1.0;
+    // both halves of every record in one round of loads: the winner's sigma
+    // and x0 travel with it through the reduction
+    double bn = -1.0, bs = 0.0, bx = 0.0;
     int bi = -1, bc = -1;
     if (G <= 160) {
-      double2 e[5];
+      double2 e[5], f[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
         const int c = lane + 32 * k;
         e[k] = c < G ? __ldcg(P.cand + 2 * (buf * G + c))
                      : make_double2(-1.0, __longlong_as_double(-1LL));
+        f[k] = c < G ? __ldcg(P.cand + 2 * (buf * G + c) + 1) : make_double2(0.0, 0.0);
       }
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
         const int ci = (int)__double_as_longlong(e[k].y);
-        if (better(e[k].x, ci, bn, bi)) { bn = e[k].x; bi = ci; bc = lane + 32 * k; }
+        if (better(e[k].x, ci, bn, bi)) {
+          bn = e[k].x; bi = ci; bc = lane + 32 * k; bs = f[k].x; bx = f[k].y;
+        }
       }
     } else {
       for (int c = lane; c < G; c += 32) {
         const double2 e = __ldcg(P.cand + 2 * (buf * G + c));
+        const double2 f = __ldcg(P.cand + 2 * (buf * G + c) + 1);
         const int ci = (int)__double_as_longlong(e.y);
-        if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; }
+        if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; bs = f.x; bx = f.y; }
       }
     }
 #pragma unroll
@@ -176,12 +182,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const double on = __shfl_xor_sync(0xffffffffu, bn, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
+      const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+      const double ox = __shfl_xor_sync(0xffffffffu, bx, o);
+      if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; bs = os; bx = ox; }
     }
     if (lane == 0) {
-      const double sig = bc >= 0 ? __ldcg(P.cand + 2 * (buf * G + bc) + 1).x : 0.0;
       const long long packed = (long long)(unsigned)bc | ((long long)(unsigned)bi << 32);
-      P.win[buf] = make_double2(__longlong_as_double(packed), sig);
+      P.win[2 * buf] = make_double2(__longlong_as_double(packed), bs);
+      P.win[2 * buf + 1] = make_double2(bx, 0.0);
       red_add_release(&P.ctrl->cpqr_arrive, 1u);
     }
   };
@@ -191,11 +199,12 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const bool ok = wait_count(P.ctrl, nsteps * (unsigned)(G + 1) + P.extra, P.limit_ns, site);
       s_ok = ok;
       if (ok) {
-        const double2 w = __ldcg(P.win + buf);
+        const double2 w = __ldcg(P.win + 2 * buf), w2 = __ldcg(P.win + 2 * buf + 1);
         const long long packed = __double_as_longlong(w.x);
         s_win_cta = (int)(unsigned)(packed & 0xffffffffLL);
         s_win_idx = (int)(unsigned)(packed >> 32);
         s_sigma = w.y;
+        s_x0 = w2.x;
       }
     }
     __syncthreads();
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   };
   // warp 0: publish candidate jc (local index, key cn) of the next step,
   // whose column is final through row r0 - 1: the record (cn, index), sigma =
-  // ||col(r0 + 1:)||^2 exactly, and the column from row r0 on
+  // ||col(r0 + 1:)||^2 exactly and x0 = col(r0), and the column from row r0 on
   auto publish = [&](int buf, int jc, double cn, int r0) {
     double sg = 0.0;
     if (jc >= 0) {
@@ -230,7 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     if (lane == 0) {
       P.cand[2 * (buf * G + b)] =
           make_double2(jc >= 0 ? cn : -1.0, __longlong_as_double(jc >= 0 ? (long long)(c0 + jc) : -1LL));
-      P.cand[2 * (buf * G + b) + 1] = make_double2(sg, 0.0);
+      P.cand[2 * (buf * G + b) + 1] =
+          make_double2(sg, jc >= 0 ? cols[(int64_t)jc * l + r0] : 0.0);
     }
   };
 
@@ -286,15 +296,13 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       return;
     }
     // ---- 2. reflector from the winner's column, rows s..l-1 ----
-    const double *xc = P.pcol + ((int64_t)buf * G + wc) * l;
-    for (int r = s + tid; r < l; r += kThreads) s_v[r - s] = __ldcg(xc + r);
-    __syncthreads();
     // one thread forms H = I - tau v v^T with v(0) = 1 and H x = alpha e_1,
     // alpha = ||x|| >= 0: tau = 1 - x0/alpha, v(1:) = x(1:) / (x0 - alpha),
     // where x0 > 0 uses x0 - alpha = -sigma / (x0 + alpha) (no cancellation);
-    // sigma = ||x(1:)||^2 came with the winner's record
+    // x0 and sigma = ||x(1:)||^2 came with the winner's record, so this runs
+    // while the other threads load the column
     if (tid == 0) {
-      const double x0 = s_v[0], sigma = s_sigma;
+      const double x0 = s_x0, sigma = s_sigma;
       double tau, beta, rv0;
       if (sigma == 0.0) {
         if (x0 >= 0.0) { tau = 0.0; beta = x0; }
@@ -319,6 +327,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       s_beta = beta;
       s_rv0 = rv0;
     }
+    const double *xc = P.pcol + ((int64_t)buf * G + wc) * l;
+    for (int r = s + tid; r < l; r += kThreads) s_v[r - s] = __ldcg(xc + r);
     __syncthreads();
     const double tau = s_tau, beta = s_beta, rv0 = s_rv0;
     for (int r = tid; r < l - s; r += kThreads) {
@@ -505,7 +515,7 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   const Plan pl = plan_for(n, l);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(4 * (size_t)pl.G * sizeof(double2)) + up(2 * sizeof(double2)) +
+  return up(4 * (size_t)pl.G * sizeof(double2)) + up(4 * sizeof(double2)) +
          up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
 }
 
@@ -531,7 +541,7 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
   P.cand = reinterpret_cast<double2 *>(take(4 * (size_t)pl.G * sizeof(double2)));
-  P.win = reinterpret_cast<double2 *>(take(2 * sizeof(double2)));
+  P.win = reinterpret_cast<double2 *>(take(4 * sizeof(double2)));
   P.pcol = reinterpret_cast<double *>(take(2 * (size_t)pl.G * l * sizeof(double)));
   P.counts = reinterpret_cast<int32_t *>(take((size_t)pl.G * sizeof(int32_t)));
   P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));
