@@ -610,11 +610,11 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int a = 16 * g + i;
-      v[i] = (a < l && c >= a && c < l) ? d2f_rn(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
+      v[i] = (a < l && c >= a && c < l) ? (float)(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
                                         : 0.0f;
     }
     for (int a = tid; a < l; a += blockDim.x)
-      s_thr[a] = d2f_rn((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
+      s_thr[a] = (float)((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
     if (tid == 0) s_f = 0;
     __syncthreads();
     for (int jb = 0; jb * 16 < l; ++jb) {
@@ -637,7 +637,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
         if (g == jb && c >= j && c < l) {
           const float y = v[ii] * s_rs;
           rowbuf[buf][c] = y;
-          R[(int64_t)j * l + c] = f2d(y);
+          R[(int64_t)j * l + c] = (double)y;
         }
         __syncthreads();
         const float rjc = (c >= j && c < l) ? rowbuf[buf][c] : 0.0f;
@@ -676,7 +676,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
   for (int bk = warp; bk < nblk; bk += (int)(blockDim.x >> 5)) {
     const int c0 = bk * kB, bs = min(kB, l - c0);
     const int cc = lane;
-    auto U = [&](int i, int t) { return d2f_rn(R[(int64_t)(c0 + i) * l + c0 + t]); };
+    auto U = [&](int i, int t) { return (float)R[(int64_t)(c0 + i) * l + c0 + t]; };
     const float dl = (lane < bs) ? 1.0f / U(lane, lane) : 0.0f;
     float x[kB];
 #pragma unroll
@@ -695,7 +695,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
     if (cc < bs)
 #pragma unroll
       for (int i = 0; i < kB; ++i)
-        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = f2d(x[i]);
+        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = (double)x[i];
   }
 }
 
@@ -773,8 +773,11 @@ constexpr int kApplyThreads = 128;
 
 // Q (rows x l, ldq) = X R^{-1}, blocked over 16 columns; X and Q may not alias.
 // T = float: X, R and the block inverses are rounded to FP32 and the solve
-// runs in FP32 (Q is written in FP64).
-template <typename T>
+// runs in FP32 (Q is written in FP64).  PRE: R (padded to lpad = a multiple of
+// 16 columns) and the diagonal block inverses are staged in shared memory
+// once, instead of one block column per step (FP32 is latency-bound on those
+// loads, FP64 on its FMAs).
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
              const double *__restrict__ R, const double *__restrict__ Dinv, double *__restrict__ Q,
@@ -783,14 +786,25 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   extern __shared__ double sm_raw[];
   T *sm = reinterpret_cast<T *>(sm_raw);
   const int lp = l + 1;
+  const int lpad = (l + kB - 1) / kB * kB;
   T *qs = sm;                                  // [kApplyRows][lp]
-  T *rc = sm + kApplyRows * lp;                // [l][kB] block column of R
-  T *dv = rc + (int64_t)l * kB;                // [kB][kB] inverse diagonal block
+  T *rc = sm + kApplyRows * lp;                // [l][kB] block column of R, or PRE: R [l][lpad]
+  T *dv = PRE ? rc + (int64_t)l * lpad : rc + (int64_t)l * kB;  // [kB][kB], or PRE: [lpad][kB]
+  if (PRE) {
+    for (int e = threadIdx.x; e < l * lpad; e += blockDim.x) {
+      const int t = e / lpad, j = e - t * lpad;
+      rc[e] = j < l ? (T)R[(int64_t)t * l + j] : (T)0;
+    }
+    for (int e = threadIdx.x; e < lpad * kB; e += blockDim.x) {
+      const int i = e / kB, j = e - i * kB, c0 = i / kB * kB;
+      dv[e] = (i < l && c0 + j < l) ? (T)Dinv[(int64_t)i * l + c0 + j] : (T)0;
+    }
+  }
   const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
   const int nr = (int)min((int64_t)kApplyRows, rows - r0);
   for (int e = threadIdx.x; e < kApplyRows * l; e += blockDim.x) {
     const int r = e / l, c = e - r * l;
-    qs[r * lp + c] = (r < nr) ? from_f64<T>(X[(r0 + r) * ldx + c]) : (T)0;
+    qs[r * lp + c] = (r < nr) ? (T)X[(r0 + r) * ldx + c] : (T)0;
   }
   // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
   // warp needs the same rows of inv(R[b, b]), so the triangular product
@@ -799,22 +813,27 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   for (int c0 = 0; c0 < l; c0 += kB) {
     const int bs = min(kB, l - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < c0 * kB; e += blockDim.x) {
-      const int t = e / kB, j = e - t * kB;
-      rc[e] = (j < bs) ? from_f64<T>(R[(int64_t)t * l + c0 + j]) : (T)0;
+    if (!PRE) {
+      for (int e = threadIdx.x; e < c0 * kB; e += blockDim.x) {
+        const int t = e / kB, j = e - t * kB;
+        rc[e] = (j < bs) ? (T)R[(int64_t)t * l + c0 + j] : (T)0;
+      }
+      for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) {
+        const int i = e / kB, j = e - i * kB;
+        dv[e] = (i < bs && j < bs) ? (T)Dinv[(int64_t)(c0 + i) * l + c0 + j] : (T)0;
+      }
+      __syncthreads();
     }
-    for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) {
-      const int i = e / kB, j = e - i * kB;
-      dv[e] = (i < bs && j < bs) ? from_f64<T>(Dinv[(int64_t)(c0 + i) * l + c0 + j]) : (T)0;
-    }
-    __syncthreads();
+    const T *rcb = PRE ? rc + c0 : rc;           // rcb[t * rstride + j] = R(t, c0 + j)
+    const int rstride = PRE ? lpad : kB;
+    const T *dvb = PRE ? dv + (int64_t)c0 * kB : dv;  // dvb[i * kB + j] = inv(R_bb)(i, j)
     T acc[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) acc[a] = (j0 + a < bs) ? qs[r * lp + c0 + j0 + a] : (T)0;
     for (int t = 0; t < c0; ++t) {
       const T qv = qs[r * lp + t];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a] = fma(-qv, rc[t * kB + j0 + a], acc[a]);
+      for (int a = 0; a < 4; ++a) acc[a] = fma(-qv, rcb[t * rstride + j0 + a], acc[a]);
     }
     // share the 16 residuals of row r, then multiply by the inverse block
     __syncthreads();
@@ -827,7 +846,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     for (int i = 0; i < iend; ++i) {
       const T v = qs[r * lp + c0 + i];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) out[a] = fma(v, dv[i * kB + j0 + a], out[a]);
+      for (int a = 0; a < 4; ++a) out[a] = fma(v, dvb[i * kB + j0 + a], out[a]);
     }
     __syncthreads();
 #pragma unroll
@@ -837,7 +856,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   __syncthreads();
   for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
     const int rr = e / l, c = e - rr * l;
-    Q[(r0 + rr) * ldq + c] = to_f64(qs[rr * lp + c]);
+    Q[(r0 + rr) * ldq + c] = (double)qs[rr * lp + c];
   }
 }
 
@@ -856,11 +875,14 @@ cudaError_t cholqr_init() {
     e = cudaFuncSetAttribute(k_chol_blocked<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_apply_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
+    e = cudaFuncSetAttribute(k_apply_trsm<double, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_apply_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
+    e = cudaFuncSetAttribute(k_apply_trsm<float, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_trsm<float, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess && chol_cluster_init() < 0) e = cudaErrorInvalidValue;
   return e;
 }
@@ -960,25 +982,36 @@ cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
                        const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
                        cudaStream_t st, bool lowp) {
-  const size_t smem = ((size_t)kApplyRows * (l + 1) + (size_t)l * kB + kB * kB) *
-                      (lowp ? sizeof(float) : sizeof(double));
+  const int lpad = (l + kB - 1) / kB * kB;
+  const size_t base = (size_t)kApplyRows * (l + 1);
+  const size_t smem_pre = (base + (size_t)l * lpad + (size_t)lpad * kB) * sizeof(float);
+  const bool pre = lowp && smem_pre <= 150 * 1024;
+  const size_t smem = pre ? smem_pre
+                          : (base + (size_t)l * kB + kB * kB) * (lowp ? sizeof(float)
+                                                                       : sizeof(double));
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_trsm<double>,
+    cudaError_t e = cudaFuncSetAttribute(k_apply_trsm<double, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_apply_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024);
+      e = cudaFuncSetAttribute(k_apply_trsm<float, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_trsm<float, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t tiles = (rows + kApplyRows - 1) / kApplyRows;
-  if (lowp)
-    k_apply_trsm<float><<<(unsigned)tiles, kApplyThreads, smem, st>>>(X, rows, l, ldx, R, Dinv, Q,
-                                                                       ldq, skip_unless);
+  if (pre)
+    k_apply_trsm<float, true><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
+  else if (lowp)
+    k_apply_trsm<float, false><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
   else
-    k_apply_trsm<double><<<(unsigned)tiles, kApplyThreads, smem, st>>>(X, rows, l, ldx, R, Dinv, Q,
-                                                                        ldq, skip_unless);
+    k_apply_trsm<double, false><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
   count_launch();
   return cudaGetLastError();
 }

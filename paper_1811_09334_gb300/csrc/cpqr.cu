@@ -112,6 +112,9 @@ __device__ __forceinline__ bool wait_count(Ctrl *c, unsigned target, unsigned lo
   return true;
 }
 
+// USE_SMEM (the slab in shared memory) is a template argument so that the
+// compiler addresses the columns as shared memory, not through generic loads.
+template <bool USE_SMEM>
 __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   extern __shared__ double sm[];
   __shared__ double s_v[kMaxL], s_vt[kMaxL];
@@ -126,8 +129,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c0 = (int64_t)b * P.cpb;
   const int nc = (int)max((int64_t)0, min(P.n, c0 + P.cpb) - c0);
-  double *cols = P.use_smem ? sm : P.gcols + (int64_t)b * P.cpb * l;
-  double *nrm = P.use_smem ? sm + (int64_t)P.cpb * l : reinterpret_cast<double *>(sm);
+  double *cols = USE_SMEM ? sm : P.gcols + (int64_t)b * P.cpb * l;
+  double *nrm = USE_SMEM ? sm + (int64_t)P.cpb * l : sm;
   // 1% of the norm^2 when it was last computed exactly: below that the
   // downdated value has lost too many digits and is recomputed
   double *thr = nrm + P.cpb;
@@ -525,13 +528,12 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   if (n <= 0 || l <= 0 || l > kMaxL || l > n) return cudaErrorInvalidValue;
   Plan pl = plan_for(n, l);
   if (pl.G > kMaxGrid) return cudaErrorInvalidValue;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaError_t e = cudaFuncSetAttribute(k_cpqr_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  void *kfn = pl.use_smem ? (void *)k_cpqr_wide<true> : (void *)k_cpqr_wide<false>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)std::max<size_t>(pl.smem, 1));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpqr_wide, kThreads, pl.smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, pl.smem);
   if (e != cudaSuccess) return e;
   if ((int64_t)per_sm * num_sms() < pl.G) return cudaErrorCooperativeLaunchTooLarge;
 
@@ -558,13 +560,16 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   if (e != cudaSuccess) return e;
   if (pl.G == 1) {
     // one CTA: its grid barrier never waits, no co-residency is needed
-    k_cpqr_wide<<<1, kThreads, pl.smem, st>>>(P);
+    if (pl.use_smem)
+      k_cpqr_wide<true><<<1, kThreads, pl.smem, st>>>(P);
+    else
+      k_cpqr_wide<false><<<1, kThreads, pl.smem, st>>>(P);
     count_launch();
     return cudaGetLastError();
   }
   void *args[] = {&P};
-  e = cudaLaunchCooperativeKernel((const void *)k_cpqr_wide, dim3(pl.G), dim3(kThreads), args,
-                                  pl.smem, st);
+  e = cudaLaunchCooperativeKernel((const void *)kfn, dim3(pl.G), dim3(kThreads), args, pl.smem,
+                                  st);
   count_launch();
   return e;
 }

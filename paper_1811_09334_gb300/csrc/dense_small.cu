@@ -133,15 +133,18 @@ k_form_q(const double *__restrict__ Vh, int64_t ldv, const double *__restrict__ 
 // U is staged in shared memory (n x n, ld n) when the launch gives it room
 // (dynamic smem >= n^2 doubles): every step then reads its row at shared-
 // memory latency instead of an L2 round trip.
+// STAGED is a template argument so that the compiler addresses the staged
+// copy as shared memory (a run-time choice would make every access generic).
+template <bool STAGED>
 __global__ void __launch_bounds__(128)
 k_tri_rows(const double *__restrict__ Ug, int64_t ldug, const double *__restrict__ dinv, int n,
            const double *__restrict__ X, int64_t ldx, double *__restrict__ Y, int64_t ldy,
-           int nvec, int backward, int staged) {
+           int nvec, int backward) {
   extern __shared__ double us[];
   __shared__ double di[kMaxL];
   const double *U = Ug;
   int64_t ldu = ldug;
-  if (staged) {
+  if (STAGED) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int i = e / n, j = e - i * n;
       us[e] = Ug[(int64_t)i * ldug + j];
@@ -260,8 +263,8 @@ inline int grid_for(int64_t total, int threads) {
 }  // namespace
 
 cudaError_t chol_init() {
-  const cudaError_t e = cudaFuncSetAttribute(k_tri_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             160 * 1024);
+  const cudaError_t e = cudaFuncSetAttribute(
+      k_tri_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   return e == cudaSuccess ? cholqr_init() : e;
 }
 
@@ -362,14 +365,19 @@ cudaError_t tri_rows(const double *U, int64_t ldu, const double *dinv, int n, co
   const bool staged = smem <= 160 * 1024;
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_tri_rows,
+    const cudaError_t e = cudaFuncSetAttribute(k_tri_rows<true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                160 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tri_rows<<<(unsigned)((nvec + 3) / 4), 128, staged ? smem : 0, st>>>(
-      U, ldu, dinv, n, X, ldx, Y, ldy, nvec, backward ? 1 : 0, staged ? 1 : 0);
+  const unsigned grid = (unsigned)((nvec + 3) / 4);
+  if (staged)
+    k_tri_rows<true><<<grid, 128, smem, st>>>(U, ldu, dinv, n, X, ldx, Y, ldy, nvec,
+                                              backward ? 1 : 0);
+  else
+    k_tri_rows<false><<<grid, 128, 0, st>>>(U, ldu, dinv, n, X, ldx, Y, ldy, nvec,
+                                            backward ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }

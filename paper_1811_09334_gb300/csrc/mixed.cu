@@ -453,7 +453,7 @@ k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloa
   for (int k = 0; k < 4; ++k) {
     const int r = ty + 8 * k;
     const int64_t i = i0 + r, j = j0 + 2 * tx;
-    // one FP64 -> FP32 rounding per element (on the integer pipe), the split
+    // one FP64 -> FP32 rounding per element, the split
     // in FP32 (FP64 arithmetic runs at 2 operations per clock per SM on this
     // part): f - h is exact in FP32, and the FP32 rounding of v (2^-24) is far
     // below the precision of the pair (about 2^-17)
@@ -462,8 +462,8 @@ k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloa
       if (vec && j + 1 < n) {
         if (sizeof(T) == 8) {
           const double2 p = *reinterpret_cast<const double2 *>(A + i * lda + j);
-          f0 = d2f_rn(p.x);
-          f1 = d2f_rn(p.y);
+          f0 = (float)p.x;
+          f1 = (float)p.y;
         } else {
           const float2 p = *reinterpret_cast<const float2 *>(A + i * lda + j);
           f0 = p.x;
