@@ -791,21 +791,34 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   T *rc = sm + kApplyRows * lp;                // [l][kB] block column of R, or PRE: R [l][lpad]
   T *dv = PRE ? rc + (int64_t)l * lpad : rc + (int64_t)l * kB;  // [kB][kB], or PRE: [lpad][kB]
   if (PRE) {
-    for (int e = threadIdx.x; e < l * lpad; e += blockDim.x) {
-      const int t = e / lpad, j = e - t * lpad;
-      rc[e] = j < l ? (T)R[(int64_t)t * l + j] : (T)0;
-    }
-    for (int e = threadIdx.x; e < lpad * kB; e += blockDim.x) {
-      const int i = e / kB, j = e - i * kB, c0 = i / kB * kB;
-      dv[e] = (i < l && c0 + j < l) ? (T)Dinv[(int64_t)i * l + c0 + j] : (T)0;
-    }
+    stage_smem<T>(
+        l * lpad, R,
+        [&](int e) -> const double * {
+          const int t = e / lpad, j = e - t * lpad;
+          return j < l ? R + (int64_t)t * l + j : nullptr;
+        },
+        [&](int e) { return rc + e; });
+    stage_smem<T>(
+        lpad * kB, R,
+        [&](int e) -> const double * {
+          const int i = e / kB, j = e - i * kB, c0 = i / kB * kB;
+          return (i < l && c0 + j < l) ? Dinv + (int64_t)i * l + c0 + j : nullptr;
+        },
+        [&](int e) { return dv + e; });
   }
   const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
   const int nr = (int)min((int64_t)kApplyRows, rows - r0);
-  for (int e = threadIdx.x; e < kApplyRows * l; e += blockDim.x) {
-    const int r = e / l, c = e - r * l;
-    qs[r * lp + c] = (r < nr) ? (T)X[(r0 + r) * ldx + c] : (T)0;
-  }
+  stage_smem<T>(
+      kApplyRows * l, X,
+      [&](int e) -> const double * {
+        const int r = e / l, c = e - r * l;
+        return r < nr ? X + (r0 + r) * ldx + c : nullptr;
+      },
+      [&](int e) {
+        const int r = e / l, c = e - r * l;
+        return qs + r * lp + c;
+      });
+  if (PRE && sizeof(T) == 8) cp_async_wait_all();  // the loop's first barrier follows
   // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
   // warp needs the same rows of inv(R[b, b]), so the triangular product
   // stops at row j0 + 3 for the whole warp
@@ -814,14 +827,22 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
     const int bs = min(kB, l - c0);
     __syncthreads();
     if (!PRE) {
-      for (int e = threadIdx.x; e < c0 * kB; e += blockDim.x) {
-        const int t = e / kB, j = e - t * kB;
-        rc[e] = (j < bs) ? (T)R[(int64_t)t * l + c0 + j] : (T)0;
-      }
-      for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) {
-        const int i = e / kB, j = e - i * kB;
-        dv[e] = (i < bs && j < bs) ? (T)Dinv[(int64_t)(c0 + i) * l + c0 + j] : (T)0;
-      }
+      stage_smem<T>(
+          c0 * kB, R,
+          [&](int e) -> const double * {
+            const int t = e / kB, j = e - t * kB;
+            return j < bs ? R + (int64_t)t * l + c0 + j : nullptr;
+          },
+          [&](int e) { return rc + e; });
+      stage_smem<T>(
+          kB * kB, R,
+          [&](int e) -> const double * {
+            const int i = e / kB, j = e - i * kB;
+            return (i < bs && j < bs) ? Dinv + (int64_t)(c0 + i) * l + c0 + j : nullptr;
+          },
+          [&](int e) { return dv + e; });
+      // (the FP64 copies of this block and, at c0 = 0, of the X tile)
+      if (sizeof(T) == 8) cp_async_wait_all();
       __syncthreads();
     }
     const T *rcb = PRE ? rc + c0 : rc;           // rcb[t * rstride + j] = R(t, c0 + j)

@@ -17,8 +17,7 @@ struct Ctrl {
   unsigned bar_count;       // grid barrier: arrivals in the current generation
   unsigned bar_gen;         // grid barrier: generation counter
   int timeout_site;         // diagnostics: which wait gave up
-  unsigned cpqr_arrive;     // CPQR grid barriers: arrivals since the launch began
-  int pad[12];
+  int pad[13];
   int again_flag[16];       // per CholeskyQR site: 1 when a second pass is needed
   int done_flag[16];        // per CholeskyQR site: 1 when one pass was enough
 };
@@ -183,6 +182,48 @@ template <>
 __device__ __forceinline__ float from_f64<float>(double x) { return d2f_rn(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d(x); }
+
+// Shared-memory staging with many global loads in flight.  A plain loop
+// `dst[e] = src[e]` waits one L2 round trip per element and thread; these
+// keep every element of a thread (FP64: asynchronous copies, no registers)
+// or K of them (a conversion to FP32 on the way) in flight.  src(e) gives
+// the global address of element e, or nullptr for a zero; dst(e) its shared
+// slot.  The FP64 form needs cp_async_wait_all() and a block barrier before
+// other threads read the copies.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+template <typename T, typename Src, typename Dst>
+__device__ __forceinline__ void stage_smem(int n, const double *any, Src src, Dst dst) {
+  if constexpr (sizeof(T) == 8) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const double *p = src(e);
+      cp_async8(dst(e), p ? p : any, p != nullptr);
+    }
+  } else {
+    constexpr int K = 8;
+    for (int e0 = threadIdx.x; e0 < n; e0 += K * blockDim.x) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int e = e0 + k * (int)blockDim.x;
+        const double *p = e < n ? src(e) : nullptr;
+        v[k] = p ? __ldg(p) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int e = e0 + k * (int)blockDim.x;
+        if (e < n) *dst(e) = (T)v[k];
+      }
+    }
+  }
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

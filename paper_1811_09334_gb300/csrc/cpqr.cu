@@ -7,20 +7,24 @@
 // one grid barrier:
 //   1. the winner of step s (largest trailing norm, ties to the lowest
 //      original column index) was picked by the last CTA to arrive at the
-//      barrier; every CTA reads its record: the CTA that holds it, x0 and
-//      the exact ||x(s+1:)||^2 of its column;
+//      barrier; every CTA polls its two tagged records: the CTA that holds
+//      it, x0 and the exact ||x(s+1:)||^2 of its column;
 //   2. every CTA builds the same Householder reflector from the winner's
-//      column, mapping it to +alpha e_s (non-negative R(s, s));
+//      column, mapping it to +alpha e_s (non-negative R(s, s)), while it
+//      loads that column;
 //   3. every CTA forms v^T col for its unpivoted columns (4 lanes per column)
-//      and the downdated norms ||col(s+1:)||^2 = ||col(s:)||^2 - col'(s)^2
-//      (recomputed exactly after more than 99 % cancellation);
+//      from the unscaled column, v^T col = col(s) + (x(s+1:)^T col(s+1:)) /
+//      (x0 - alpha), and the downdated norms ||col(s+1:)||^2 =
+//      ||col(s:)||^2 - col'(s)^2 (recomputed exactly after more than 99 %
+//      cancellation);
 //   4. it updates its best column for step s + 1, publishes it (norm, index,
 //      exact trailing sigma, the column from row s + 1) and arrives at the
 //      barrier;
 //   5. the rest of its axpys col -= (v^T col) tau v run while the barrier
 //      completes.
-// Candidate tables are double-buffered by step parity, so one barrier per
-// step suffices.  After l steps the unchosen columns are written in their
+// Candidate tables and columns are double-buffered by step parity, so one
+// barrier per step suffices.  The winner records need one copy: the record
+// of barrier k + 1 is written only after every CTA has read that of k.  After l steps the unchosen columns are written in their
 // original order behind the pivots.
 #include <cmath>
 
@@ -45,7 +49,8 @@ struct CpqrParams {
   double *Vh;
   double *tau;
   double2 *cand;      // [2][G][2]: (norm^2, index as a 64-bit integer), (sigma, x0)
-  double2 *win;       // [2][2]: (CTA and index as two 32-bit integers, sigma), (x0, 0)
+  unsigned *arrive;   // barrier counter, alone in its 128-byte line
+  unsigned long long *rec;  // [G][16]: CTA c's winner records in line c
   double *pcol;       // [2][G][l]
   int32_t *counts;    // [G]
   double *gcols;      // G * cpb * l when the slab does not fit in shared memory
@@ -77,13 +82,17 @@ __device__ __forceinline__ void warp_best(double &bn, int &bi) {
   }
 }
 
-// Grid barriers count arrivals on one counter that the host zeroes before
-// every launch.  A step barrier takes G + 1 increments: the G-th arriver
-// (it sees G - 1 earlier arrivals) reads the whole candidate table, picks the
-// winner, publishes it and adds the last increment, so the other CTAs read
-// one record instead of the table.  Every wait is bounded by limit_ns; an
-// error recorded by another CTA ends it.  `extra` (only the timeout test sets
-// it) makes the first wait need arrivals that never come.
+// Grid barriers count arrivals on one counter that the host zeroes, with the
+// winner records, before every launch.  At step barrier k (k = 1, 2, ...)
+// the k G-th arriver reads the whole candidate table, picks the winner and
+// writes it to every CTA as two 128-bit records tagged with k, one with sigma
+// and one with x0, in a 128-byte line of that CTA's own.  Each CTA polls its
+// records (a 128-bit access is a single access, so a record whose tag
+// matches carries that barrier's data): no second round trip after polling a
+// counter, and no line that all CTAs poll while the arrivals' atomics hit it.
+// Every wait is bounded by limit_ns; an error recorded by another CTA ends
+// it.  `extra` (only the timeout test sets it) makes the first wait need a
+// tag or arrivals that never come.
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
   unsigned old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -92,11 +101,58 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
 __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// (a fence.acq_rel.gpu before these stores makes them releases)
+__device__ __forceinline__ void st_relaxed_b128(unsigned long long *p, unsigned long long lo,
+                                                unsigned long long hi) {
+  asm volatile("{\n .reg .b128 t;\n mov.b128 t, {%1, %2};\n st.relaxed.gpu.global.b128 [%0], t;\n}"
+               ::"l"(p), "l"(lo), "l"(hi) : "memory");
+}
+__device__ __forceinline__ void ld_acquire_b128(const unsigned long long *p, unsigned long long &lo,
+                                                unsigned long long &hi) {
+  asm volatile("{\n .reg .b128 t;\n ld.acquire.gpu.global.b128 t, [%2];\n mov.b128 {%0, %1}, t;\n}"
+               : "=l"(lo), "=l"(hi) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_b128(const unsigned long long *p, unsigned long long &lo,
+                                                unsigned long long &hi) {
+  asm volatile("{\n .reg .b128 t;\n ld.relaxed.gpu.global.b128 t, [%2];\n mov.b128 {%0, %1}, t;\n}"
+               : "=l"(lo), "=l"(hi) : "l"(p) : "memory");
+}
+// one thread: wait until both records at rec (A at rec, B at rec + 2) carry
+// tag (bits 48..63 of their first words).  B is loaded (relaxed) beside each
+// acquire load of A, so both are in flight at once; its tag vouches for its
+// data, A's acquire for everything the winner's column needs.  False on
+// timeout or error.
+__device__ __forceinline__ bool wait_records(Ctrl *c, const unsigned long long *rec, unsigned tag,
+                                             unsigned long long &a0, unsigned long long &a1,
+                                             unsigned long long &b1, unsigned long long limit_ns,
+                                             int site) {
+  unsigned long long t0 = 0, b0 = 0;
+  bool have_a = false;
+  for (unsigned it = 0;; ++it) {
+    ld_relaxed_b128(rec + 2, b0, b1);
+    if (!have_a) {
+      ld_acquire_b128(rec, a0, a1);
+      have_a = (unsigned)(a0 >> 48) == tag;
+    }
+    if (have_a && (unsigned)(b0 >> 48) == tag) return true;
+    if ((it & 15) == 15) {
+      if (ld_volatile_i32(&c->status) < 0) return false;
+      const unsigned long long t = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > limit_ns) {
+        set_status(c, RQLP_ERR_TIMEOUT);
+        atomicExch(&c->timeout_site, site);
+        return false;
+      }
+    }
+  }
+}
 // lane-0 wait until the counter reaches target; false on timeout or error
-__device__ __forceinline__ bool wait_count(Ctrl *c, unsigned target, unsigned long long limit_ns,
-                                           int site) {
+__device__ __forceinline__ bool wait_count(Ctrl *c, const unsigned *counter, unsigned target,
+                                           unsigned long long limit_ns, int site) {
   unsigned long long t0 = 0;
-  for (unsigned it = 0; (int)(ld_acquire_u32(&c->cpqr_arrive) - target) < 0; ++it) {
+  for (unsigned it = 0; (int)(ld_acquire_u32(counter) - target) < 0; ++it) {
     if ((it & 15) == 15) {
       if (ld_volatile_i32(&c->status) < 0) return false;
       const unsigned long long t = globaltimer_ns();
@@ -117,12 +173,12 @@ __device__ __forceinline__ bool wait_count(Ctrl *c, unsigned target, unsigned lo
 template <bool USE_SMEM>
 __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   extern __shared__ double sm[];
-  __shared__ double s_v[kMaxL], s_vt[kMaxL];
+  __shared__ double s_v[kMaxL];
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
   __shared__ double s_sigma, s_x0;
-  __shared__ double s_tau, s_beta, s_rv0;
+  __shared__ double s_tau, s_beta, s_rv0, s_trv;
   __shared__ int s_ok;
 
   const int G = gridDim.x, b = blockIdx.x, l = P.l;
@@ -134,26 +190,30 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   // 1% of the norm^2 when it was last computed exactly: below that the
   // downdated value has lost too many digits and is recomputed
   double *thr = nrm + P.cpb;
-  double *wdot = thr + P.cpb;                          // v^T col of this step
+  double *wdot = thr + P.cpb;  // this step's axpy multiple of x(s+1:) per column
   int *pivoted = reinterpret_cast<int *>(wdot + P.cpb);
   int *axdone = pivoted + P.cpb;                       // column updated early this step
 
-  // Step barrier k (k = 1, 2, ...): G + 1 increments.  arrive(): after this
-  // CTA's candidate is published; the G-th arriver (it sees G - 1 earlier
-  // arrivals) reads the whole table, publishes the winner with its sigma and
-  // adds the last increment.  Called by warp 0.
+  // Step barrier k (k = 1, 2, ...): G increments.  arrive(): after this
+  // CTA's candidate is published; the k G-th arriver reads the whole table
+  // and writes the winner records.  Called by warp 0.
   unsigned nsteps = 0;
+  // the last arriver of barrier `won` keeps the winner it wrote (lane 0)
+  unsigned won = 0;
+  unsigned long long won_w0 = 0;
+  double won_sigma = 0.0, won_x0 = 0.0;
   auto arrive = [&](int buf) {
     ++nsteps;
-    const unsigned done = nsteps * (unsigned)(G + 1);
+    const unsigned done = nsteps * (unsigned)G;
     unsigned old = 0;
     __syncwarp();
-    if (lane == 0) old = atom_add_acq_rel(&P.ctrl->cpqr_arrive, 1u);
+    if (lane == 0) old = atom_add_acq_rel(P.arrive, 1u);
     old = __shfl_sync(0xffffffffu, old, 0);
     __syncwarp();
-    if (old != done - 2u) return;
-    // both halves of every record in one round of loads: the winner's sigma
-    // and x0 travel with it through the reduction
+    if (old != done - 1u) return;
+    // both halves of every record in one round of loads; the reduction
+    // carries (norm, index, CTA), and sigma and x0 come from the lane that
+    // holds the winning entry
     double bn = -1.0, bs = 0.0, bx = 0.0;
     int bi = -1, bc = -1;
     if (G <= 160) {
@@ -185,65 +245,83 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const double on = __shfl_xor_sync(0xffffffffu, bn, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-      const double ox = __shfl_xor_sync(0xffffffffu, bx, o);
-      if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; bs = os; bx = ox; }
+      if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
     }
-    if (lane == 0) {
-      const long long packed = (long long)(unsigned)bc | ((long long)(unsigned)bi << 32);
-      P.win[2 * buf] = make_double2(__longlong_as_double(packed), bs);
-      P.win[2 * buf + 1] = make_double2(bx, 0.0);
-      red_add_release(&P.ctrl->cpqr_arrive, 1u);
+    // entry c sits in lane c mod 32, whose own best it is
+    bs = __shfl_sync(0xffffffffu, bs, bc & 31);
+    bx = __shfl_sync(0xffffffffu, bx, bc & 31);
+    const unsigned long long w0 = (unsigned long long)(unsigned)bi |
+                                  ((unsigned long long)((unsigned)bc & 0xffffu) << 32) |
+                                  ((unsigned long long)(nsteps & 0xffffu) << 48);
+    // every lane is ordered after lane 0's acquire (the warp barrier above),
+    // so its fence releases what that acquire made visible
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    for (int c = lane; c < G; c += 32) {
+      if (c == b) continue;  // this CTA takes the winner from registers
+      st_relaxed_b128(P.rec + 16 * (int64_t)c + 2, w0, (unsigned long long)__double_as_longlong(bx));
+      st_relaxed_b128(P.rec + 16 * (int64_t)c, w0, (unsigned long long)__double_as_longlong(bs));
     }
+    won = nsteps;
+    won_w0 = w0;
+    won_sigma = bs;
+    won_x0 = bx;
   };
-  // thread 0: wait for step barrier nsteps, read its winner
-  auto wait_winner = [&](int buf, int site) {
+  // thread 0: the winner of step barrier k (given here: nsteps counts only
+  // in warp 0), from its own registers when this CTA arrived last, else
+  // from this CTA's records
+  auto wait_winner = [&](int site, unsigned k) {
     if (tid == 0) {
-      const bool ok = wait_count(P.ctrl, nsteps * (unsigned)(G + 1) + P.extra, P.limit_ns, site);
+      unsigned long long a0 = won_w0, a1 = (unsigned long long)__double_as_longlong(won_sigma),
+                         b1 = (unsigned long long)__double_as_longlong(won_x0);
+      bool ok = true;
+      if (won != k || P.extra != 0)
+        ok = wait_records(P.ctrl, P.rec + 16 * (int64_t)b, (k + P.extra) & 0xffffu, a0, a1, b1,
+                          P.limit_ns, site);
       s_ok = ok;
-      if (ok) {
-        const double2 w = __ldcg(P.win + 2 * buf), w2 = __ldcg(P.win + 2 * buf + 1);
-        const long long packed = __double_as_longlong(w.x);
-        s_win_cta = (int)(unsigned)(packed & 0xffffffffLL);
-        s_win_idx = (int)(unsigned)(packed >> 32);
-        s_sigma = w.y;
-        s_x0 = w2.x;
-      }
+      s_win_idx = (int)(unsigned)(a0 & 0xffffffffULL);
+      s_win_cta = (int)((a0 >> 32) & 0xffffULL);
+      s_sigma = __longlong_as_double((long long)a1);
+      s_x0 = __longlong_as_double((long long)b1);
     }
     __syncthreads();
     return s_ok != 0;
   };
-  // plain barrier after the last step
+  // plain barrier after the l step barriers
   auto final_sync = [&](int site) {
     __syncthreads();
     if (tid == 0) {
-      red_add_release(&P.ctrl->cpqr_arrive, 1u);
-      s_ok = wait_count(P.ctrl, nsteps * (unsigned)(G + 1) + (unsigned)G + P.extra, P.limit_ns,
+      red_add_release(P.arrive, 1u);
+      s_ok = wait_count(P.ctrl, P.arrive, (unsigned)(l + 1) * (unsigned)G + P.extra, P.limit_ns,
                         site);
     }
     __syncthreads();
     return s_ok != 0;
   };
   // warp 0: publish candidate jc (local index, key cn) of the next step,
-  // whose column is final through row r0 - 1: the record (cn, index), sigma =
+  // whose column is final through row r0 - 1 once cj x(r0:) (cj != 0: the
+  // step's axpy, applied here) is subtracted: the record (cn, index), sigma =
   // ||col(r0 + 1:)||^2 exactly and x0 = col(r0), and the column from row r0 on
-  auto publish = [&](int buf, int jc, double cn, int r0) {
-    double sg = 0.0;
+  auto publish = [&](int buf, int jc, double cn, int r0, double cj) {
+    double sg = 0.0, x0 = 0.0;
     if (jc >= 0) {
-      const double *col = cols + (int64_t)jc * l;
+      double *col = cols + (int64_t)jc * l;
       double *dst = P.pcol + ((int64_t)buf * G + b) * l;
       for (int r = r0 + lane; r < l; r += 32) {
-        const double x = col[r];
+        double x = col[r];
+        if (cj != 0.0) {
+          x = fma(-cj, s_v[r - r0 + 1], x);
+          col[r] = x;
+        }
         dst[r] = x;
         if (r > r0) sg = fma(x, x, sg);
+        else x0 = x;  // lane 0
       }
       sg = warp_sum(sg);
     }
     if (lane == 0) {
       P.cand[2 * (buf * G + b)] =
           make_double2(jc >= 0 ? cn : -1.0, __longlong_as_double(jc >= 0 ? (long long)(c0 + jc) : -1LL));
-      P.cand[2 * (buf * G + b) + 1] =
-          make_double2(sg, jc >= 0 ? cols[(int64_t)jc * l + r0] : 0.0);
+      P.cand[2 * (buf * G + b) + 1] = make_double2(sg, x0);
     }
   };
 
@@ -283,11 +361,11 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       int ci = s_bi[0];
       for (int w = 1; w < kWarps; ++w)
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
-      publish(0, ci >= 0 ? (int)(ci - c0) : -1, cn, 0);
+      publish(0, ci >= 0 ? (int)(ci - c0) : -1, cn, 0, 0.0);
       arrive(0);
     }
   }
-  if (!wait_winner(0, 1)) return;
+  if (!wait_winner(1, 1u)) return;
 
   const int sub = lane >> 2, gl = lane & 3;
   for (int s = 0; s < l; ++s) {
@@ -329,21 +407,15 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       s_tau = tau;
       s_beta = beta;
       s_rv0 = rv0;
+      s_trv = tau * rv0;
     }
+    // warps 1.. load the column meanwhile
     const double *xc = P.pcol + ((int64_t)buf * G + wc) * l;
-    for (int r = s + tid; r < l; r += kThreads) s_v[r - s] = __ldcg(xc + r);
+    if (warp > 0)
+      for (int r = s + tid - 32; r < l; r += kThreads - 32) s_v[r - s] = __ldcg(xc + r);
     __syncthreads();
-    const double tau = s_tau, beta = s_beta, rv0 = s_rv0;
-    for (int r = tid; r < l - s; r += kThreads) {
-      const double v = r == 0 ? 1.0 : s_v[r] * rv0;
-      s_v[r] = v;
-      s_vt[r] = tau * v;
-    }
-    __syncthreads();
-    if (b == 0) {
-      for (int r = tid; r < l; r += kThreads) P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : s_v[r - s];
-      if (tid == 0) { P.tau[s] = tau; P.piv[s] = wi; }
-    }
+    // s_v holds the winner's column x(s:) unscaled; v = (1, x(s+1:) rv0)
+    const double tau = s_tau, beta = s_beta, rv0 = s_rv0, trv = s_trv;
     // the winner's column is final: rows < s from the slab, beta at s, zeros below
     if ((int)(wi - c0) >= 0 && (int)(wi - c0) < nc && warp == 0) {
       const int jw = (int)(wi - c0);
@@ -355,34 +427,41 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     // ---- 3. dot products v^T col and downdated norms (the axpys wait) ----
     // groups of 4 lanes per column, eight columns per warp: every FP64 warp
     // instruction costs the same issue slots whatever its active lanes, so
-    // the reductions are kept short (two levels).  A column whose norm has
-    // cancelled by more than 99 % since its last exact value is updated now
-    // and its norm recomputed.
+    // the reductions are kept short (two levels).  v^T col = col(s) +
+    // rv0 x(s+1:)^T col(s+1:); the new col(s) is stored at once, and the
+    // axpy of rows s+1.. is col -= ((v^T col) tau rv0) x, with that multiple
+    // kept in wdot.  A column whose norm has cancelled by more than 99 % since
+    // its last exact value is updated now and its norm recomputed.
     double bn = -1.0;
     int bi = -1;
     for (int jb = warp * 8; jb < nc; jb += kWarps * 8) {
       const int jj = jb + sub;
       const bool act = jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi;
       double *col = cols + (int64_t)(act ? jj : 0) * l;
-      double w = 0.0;
+      double d = 0.0;
       if (act)
-        for (int r = s + gl; r < l; r += 4) w = fma(s_v[r - s], col[r], w);
-      w += __shfl_xor_sync(0xffffffffu, w, 2);
-      w += __shfl_xor_sync(0xffffffffu, w, 1);
+        for (int r = s + 1 + gl; r < l; r += 4) d = fma(s_v[r - s], col[r], d);
+      d += __shfl_xor_sync(0xffffffffu, d, 2);
+      d += __shfl_xor_sync(0xffffffffu, d, 1);
       int need = 0;
-      double nd = 0.0;
+      double nd = 0.0, cf = 0.0;
       if (act && gl == 0) {
-        wdot[jj] = w;
+        const double cs = col[s];
+        const double w = fma(rv0, d, cs);     // v^T col
+        const double rsv = fma(-w, tau, cs);  // new col(s)
+        col[s] = rsv;
+        cf = w * trv;
+        wdot[jj] = cf;
         axdone[jj] = 0;
-        const double rsv = fma(-w, s_vt[0], col[s]);  // new col(s)
         nd = fma(-rsv, rsv, nrm[jj]);
         need = __double_as_longlong(nd) <= __double_as_longlong(thr[jj]);
       }
       need = __shfl_sync(0xffffffffu, need, lane & ~3);
       // warp-uniform branch: the shuffles inside need every lane
       if (__any_sync(0xffffffffu, need)) {
+        cf = __shfl_sync(0xffffffffu, cf, lane & ~3);
         if (need)
-          for (int r = s + gl; r < l; r += 4) col[r] = fma(-w, s_vt[r - s], col[r]);
+          for (int r = s + 1 + gl; r < l; r += 4) col[r] = fma(-cf, s_v[r - s], col[r]);
         __syncwarp();
         double t = 0.0;
         if (need)
@@ -414,28 +493,28 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     }
     // ---- 4. warp 0: update the candidate, publish it, arrive ----
     if (warp == 0 && s + 1 < l) {
-      if (jc >= 0 && !axdone[jc]) {
-        double *col = cols + (int64_t)jc * l;
-        const double wj = wdot[jc];
-        for (int r = s + lane; r < l; r += 32) col[r] = fma(-wj, s_vt[r - s], col[r]);
-        __syncwarp();
-      }
-      publish(buf ^ 1, jc, cn, s + 1);
+      publish(buf ^ 1, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0);
       arrive(buf ^ 1);
     }
     // ---- 5. the remaining axpys, while the barrier completes ----
-    for (int jb = warp * 8; jb < nc; jb += kWarps * 8) {
+    // (warps 1..: warp 0 goes from its arrival, and the last arriver's
+    // scan, straight to the next wait)
+    if (b == 0 && warp == kWarps - 1) {
+      // this step's reflector, off the path to the barrier
+      for (int r = lane; r < l; r += 32)
+        P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : (r == s ? 1.0 : s_v[r - s] * rv0);
+      if (lane == 0) { P.tau[s] = tau; P.piv[s] = wi; }
+    }
+    for (int jb = (warp - 1) * 8; warp > 0 && jb < nc; jb += (kWarps - 1) * 8) {
       const int jj = jb + sub;
       if (jj < nc && !pivoted[jj] && (int)(c0 + jj) != wi && jj != jc && !axdone[jj]) {
         double *col = cols + (int64_t)jj * l;
-        const double w = wdot[jj];
-        for (int r = s + gl; r < l; r += 4) col[r] = fma(-w, s_vt[r - s], col[r]);
+        const double cf = wdot[jj];
+        for (int r = s + 1 + gl; r < l; r += 4) col[r] = fma(-cf, s_v[r - s], col[r]);
       }
     }
-    if (s + 1 < l) {
-      __syncthreads();
-      if (!wait_winner(buf ^ 1, 2)) return;
-    }
+    // (the wait's own barrier orders these axpys before the next column load)
+    if (s + 1 < l && !wait_winner(2, (unsigned)(s + 2))) return;
   }
 
   // ---- unchosen columns keep their order behind the l pivots ----
@@ -506,8 +585,8 @@ Plan plan_for(int64_t n, int l) {
 size_t cpqr_ws_bytes(int64_t n, int l) {
   const size_t G = kMaxGrid;
   size_t b = 0;
+  b += 128 + 128 * G;  // counter line, one record line per CTA
   b += 4 * G * sizeof(double2);
-  b += 256;  // winner records
   b += 2 * G * (size_t)l * sizeof(double);
   b += G * sizeof(int32_t);
   b += (size_t)(n + kMaxGrid) * l * sizeof(double);  // global slabs (fallback)
@@ -518,7 +597,7 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   const Plan pl = plan_for(n, l);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(4 * (size_t)pl.G * sizeof(double2)) + up(4 * sizeof(double2)) +
+  return up(128 + 128 * (size_t)pl.G) + up(4 * (size_t)pl.G * sizeof(double2)) +
          up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
 }
 
@@ -542,8 +621,11 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   CpqrParams P;
   P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
+  const size_t sync_bytes = 128 + 128 * (size_t)pl.G;
+  char *sync = take(sync_bytes);
+  P.arrive = reinterpret_cast<unsigned *>(sync);
+  P.rec = reinterpret_cast<unsigned long long *>(sync + 128);
   P.cand = reinterpret_cast<double2 *>(take(4 * (size_t)pl.G * sizeof(double2)));
-  P.win = reinterpret_cast<double2 *>(take(4 * sizeof(double2)));
   P.pcol = reinterpret_cast<double *>(take(2 * (size_t)pl.G * l * sizeof(double)));
   P.counts = reinterpret_cast<int32_t *>(take((size_t)pl.G * sizeof(int32_t)));
   P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));
@@ -555,8 +637,8 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   // the permutation stays valid even if the kernel stops early on an error
   e = iota(piv, n, st);
   if (e != cudaSuccess) return e;
-  // barrier counter of this launch
-  e = cudaMemsetAsync(&ctrl->cpqr_arrive, 0, sizeof(unsigned), st);
+  // barrier counter and winner records of this launch
+  e = cudaMemsetAsync(sync, 0, sync_bytes, st);
   if (e != cudaSuccess) return e;
   if (pl.G == 1) {
     // one CTA: its grid barrier never waits, no co-residency is needed

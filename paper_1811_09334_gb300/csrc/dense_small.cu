@@ -145,15 +145,19 @@ k_tri_rows(const double *__restrict__ Ug, int64_t ldug, const double *__restrict
   const double *U = Ug;
   int64_t ldu = ldug;
   if (STAGED) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      us[e] = Ug[(int64_t)i * ldug + j];
-    }
+    stage_smem<double>(
+        n * n, Ug,
+        [&](int e) -> const double * {
+          const int i = e / n, j = e - i * n;
+          return Ug + (int64_t)i * ldug + j;
+        },
+        [&](int e) { return us + e; });
     U = us;
     ldu = n;
   }
   for (int j = threadIdx.x; j < n; j += blockDim.x)
     di[j] = dinv ? dinv[j] : rcp_fast(Ug[(int64_t)j * ldug + j]);
+  if (STAGED) cp_async_wait_all();
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int vec = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
