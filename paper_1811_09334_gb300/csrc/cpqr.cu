@@ -4,28 +4,38 @@
 // One persistent cooperative kernel.  CTA b owns a contiguous slab of
 // columns of B (each column l doubles), kept in shared memory when it fits
 // and in a global scratch copy otherwise.  Per pivot step s there is exactly
-// one grid barrier:
-//   1. the winner of step s (largest trailing norm, ties to the lowest
-//      original column index) was picked by the last CTA to arrive at the
-//      barrier; every CTA polls its two tagged records: the CTA that holds
-//      it, x0 and the exact ||x(s+1:)||^2 of its column;
+// one grid-wide exchange:
+//   1. every CTA has published its best column for step s: a record (norm,
+//      index), the exact ||x(s+1:)||^2 of that column (sigma), x0 = x(s) and
+//      the column itself; the last CTA to arrive picked the winner (largest
+//      trailing norm, ties to the lowest original index) and sent it to all;
 //   2. every CTA builds the same Householder reflector from the winner's
-//      column, mapping it to +alpha e_s (non-negative R(s, s)), while it
-//      loads that column;
+//      x0 and sigma, mapping its column to +alpha e_s (non-negative
+//      R(s, s)), while it loads that column;
 //   3. every CTA forms v^T col for its unpivoted columns (4 lanes per column)
 //      from the unscaled column, v^T col = col(s) + (x(s+1:)^T col(s+1:)) /
 //      (x0 - alpha), and the downdated norms ||col(s+1:)||^2 =
 //      ||col(s:)||^2 - col'(s)^2 (recomputed exactly after more than 99 %
 //      cancellation);
-//   4. it updates its best column for step s + 1, publishes it (norm, index,
-//      exact trailing sigma, the column from row s + 1) and arrives at the
-//      barrier;
-//   5. the rest of its axpys col -= (v^T col) tau v run while the barrier
-//      completes.
-// Candidate tables and columns are double-buffered by step parity, so one
-// barrier per step suffices.  The winner records need one copy: the record
-// of barrier k + 1 is written only after every CTA has read that of k.  After l steps the unchosen columns are written in their
-// original order behind the pivots.
+//   4. warp 0 updates the CTA's best column for step s + 1, publishes it and
+//      arrives (the last arrival picks the winner);
+//   5. meanwhile the other warps apply the rest of the axpys
+//      col -= (v^T col) tau v.
+// After l steps the unchosen columns are written in their original order
+// behind the pivots.
+//
+// The exchange needs no fences: every value a CTA publishes is stored as one
+// 128-bit word together with the number k of the exchange it belongs to, and
+// readers re-read a word until it carries k.  A 128-bit access is a single
+// memory access, so a word that carries k holds exchange k's value, whatever
+// order the stores arrive in.  Each CTA then counts itself in with a relaxed
+// atomic; the last of the G reads the G candidate records, picks the winner
+// and writes it into one 128-byte line per CTA, which that CTA polls alone.
+// Candidate records and columns are double-buffered by exchange parity: a CTA
+// overwrites exchange k's buffers (for k + 2) only after exchange k + 1's
+// winner exists, which needed every CTA's exchange k + 1 arrival, made after
+// it had read exchange k.  The host zeroes the exchange state before every
+// launch, so no word of an earlier launch matches.
 #include <cmath>
 
 #include "kernels.cuh"
@@ -37,6 +47,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxGrid = 1024;
+// 16-byte words per CTA record: (norm, index | k << 32), (sigma, k << 32),
+// (x0, k << 32), unused
+constexpr int kRecWords = 4;
 
 struct CpqrParams {
   const double *Bt;
@@ -48,11 +61,10 @@ struct CpqrParams {
   int32_t *piv;
   double *Vh;
   double *tau;
-  double2 *cand;      // [2][G][2]: (norm^2, index as a 64-bit integer), (sigma, x0)
-  unsigned *arrive;   // barrier counter, alone in its 128-byte line
-  unsigned long long *rec;  // [G][16]: CTA c's winner records in line c
-  double *pcol;       // [2][G][l]
-  int32_t *counts;    // [G]
+  unsigned *arrive;   // arrivals since the launch began, alone in its 128-byte line
+  ulonglong2 *win;    // [G][8]: CTA c's winner words in line c
+  ulonglong2 *rec;    // [2][G][kRecWords] tagged candidate records
+  ulonglong2 *pcol;   // [2][G][l] tagged words (value, k << 32)
   double *gcols;      // G * cpb * l when the slab does not fit in shared memory
   Ctrl *ctrl;
   unsigned long long limit_ns;
@@ -82,90 +94,47 @@ __device__ __forceinline__ void warp_best(double &bn, int &bi) {
   }
 }
 
-// Grid barriers count arrivals on one counter that the host zeroes, with the
-// winner records, before every launch.  At step barrier k (k = 1, 2, ...)
-// the k G-th arriver reads the whole candidate table, picks the winner and
-// writes it to every CTA as two 128-bit records tagged with k, one with sigma
-// and one with x0, in a 128-byte line of that CTA's own.  Each CTA polls its
-// records (a 128-bit access is a single access, so a record whose tag
-// matches carries that barrier's data): no second round trip after polling a
-// counter, and no line that all CTAs poll while the arrivals' atomics hit it.
-// Every wait is bounded by limit_ns; an error recorded by another CTA ends
-// it.  `extra` (only the timeout test sets it) makes the first wait need a
-// tag or arrivals that never come.
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+// tagged words: relaxed 128-bit stores and loads at GPU scope
+__device__ __forceinline__ void st_word(ulonglong2 *p, unsigned long long v, unsigned long long t) {
+  asm volatile("{\n .reg .b128 q;\n mov.b128 q, {%1, %2};\n st.relaxed.gpu.global.b128 [%0], q;\n}"
+               ::"l"(p), "l"(v), "l"(t) : "memory");
 }
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ ulonglong2 ld_word(const ulonglong2 *p) {
+  ulonglong2 w;
+  asm volatile("{\n .reg .b128 q;\n ld.relaxed.gpu.global.b128 q, [%2];\n mov.b128 {%0, %1}, q;\n}"
+               : "=l"(w.x), "=l"(w.y) : "l"(p) : "memory");
+  return w;
 }
-// (a fence.acq_rel.gpu before these stores makes them releases)
-__device__ __forceinline__ void st_relaxed_b128(unsigned long long *p, unsigned long long lo,
-                                                unsigned long long hi) {
-  asm volatile("{\n .reg .b128 t;\n mov.b128 t, {%1, %2};\n st.relaxed.gpu.global.b128 [%0], t;\n}"
-               ::"l"(p), "l"(lo), "l"(hi) : "memory");
+__device__ __forceinline__ unsigned tag_of(const ulonglong2 &w) { return (unsigned)(w.y >> 32); }
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
 }
-__device__ __forceinline__ void ld_acquire_b128(const unsigned long long *p, unsigned long long &lo,
-                                                unsigned long long &hi) {
-  asm volatile("{\n .reg .b128 t;\n ld.acquire.gpu.global.b128 t, [%2];\n mov.b128 {%0, %1}, t;\n}"
-               : "=l"(lo), "=l"(hi) : "l"(p) : "memory");
+__device__ __forceinline__ double dval(unsigned long long b) {
+  return __longlong_as_double((long long)b);
 }
-__device__ __forceinline__ void ld_relaxed_b128(const unsigned long long *p, unsigned long long &lo,
-                                                unsigned long long &hi) {
-  asm volatile("{\n .reg .b128 t;\n ld.relaxed.gpu.global.b128 t, [%2];\n mov.b128 {%0, %1}, t;\n}"
-               : "=l"(lo), "=l"(hi) : "l"(p) : "memory");
-}
-// one thread: wait until both records at rec (A at rec, B at rec + 2) carry
-// tag (bits 48..63 of their first words).  B is loaded (relaxed) beside each
-// acquire load of A, so both are in flight at once; its tag vouches for its
-// data, A's acquire for everything the winner's column needs.  False on
-// timeout or error.
-__device__ __forceinline__ bool wait_records(Ctrl *c, const unsigned long long *rec, unsigned tag,
-                                             unsigned long long &a0, unsigned long long &a1,
-                                             unsigned long long &b1, unsigned long long limit_ns,
-                                             int site) {
-  unsigned long long t0 = 0, b0 = 0;
-  bool have_a = false;
-  for (unsigned it = 0;; ++it) {
-    ld_relaxed_b128(rec + 2, b0, b1);
-    if (!have_a) {
-      ld_acquire_b128(rec, a0, a1);
-      have_a = (unsigned)(a0 >> 48) == tag;
-    }
-    if (have_a && (unsigned)(b0 >> 48) == tag) return true;
-    if ((it & 15) == 15) {
-      if (ld_volatile_i32(&c->status) < 0) return false;
-      const unsigned long long t = globaltimer_ns();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > limit_ns) {
-        set_status(c, RQLP_ERR_TIMEOUT);
-        atomicExch(&c->timeout_site, site);
-        return false;
-      }
-    }
-  }
-}
-// lane-0 wait until the counter reaches target; false on timeout or error
-__device__ __forceinline__ bool wait_count(Ctrl *c, const unsigned *counter, unsigned target,
-                                           unsigned long long limit_ns, int site) {
+
+// A bounded wait, checked by one thread every 16th round: true once an error
+// is recorded (here or by another CTA) or limit_ns has passed since the first
+// check; a timeout is recorded with its site.
+struct Deadline {
   unsigned long long t0 = 0;
-  for (unsigned it = 0; (int)(ld_acquire_u32(counter) - target) < 0; ++it) {
-    if ((it & 15) == 15) {
-      if (ld_volatile_i32(&c->status) < 0) return false;
-      const unsigned long long t = globaltimer_ns();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > limit_ns) {
-        set_status(c, RQLP_ERR_TIMEOUT);
-        atomicExch(&c->timeout_site, site);
-        return false;
-      }
-    }
+  unsigned it = 0;
+};
+__device__ __forceinline__ bool expired(Ctrl *c, Deadline &d, unsigned long long limit_ns,
+                                        int site) {
+  if ((++d.it & 15u) != 0) return false;
+  if (ld_volatile_i32(&c->status) < 0) return true;
+  const unsigned long long t = globaltimer_ns();
+  if (d.t0 == 0) {
+    d.t0 = t;
+    return false;
   }
-  return true;
+  if (t - d.t0 > limit_ns) {
+    set_status(c, RQLP_ERR_TIMEOUT);
+    atomicExch(&c->timeout_site, site);
+    return true;
+  }
+  return false;
 }
 
 // USE_SMEM (the slab in shared memory) is a template argument so that the
@@ -179,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   __shared__ int s_win_cta, s_win_idx;
   __shared__ double s_sigma, s_x0;
   __shared__ double s_tau, s_beta, s_rv0, s_trv;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_err, s_prefix;
 
   const int G = gridDim.x, b = blockIdx.x, l = P.l;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -194,50 +163,89 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   int *pivoted = reinterpret_cast<int *>(wdot + P.cpb);
   int *axdone = pivoted + P.cpb;                       // column updated early this step
 
-  // Step barrier k (k = 1, 2, ...): G increments.  arrive(): after this
-  // CTA's candidate is published; the k G-th arriver reads the whole table
-  // and writes the winner records.  Called by warp 0.
-  unsigned nsteps = 0;
-  // the last arriver of barrier `won` keeps the winner it wrote (lane 0)
+  // warp 0: publish candidate jc (local index, key cn) for exchange k into
+  // buffer buf; its column is final through row r0 - 1 once cj x(r0:)
+  // (cj != 0: the step's axpy, applied here) is subtracted.  The record is
+  // (cn, index), sigma = ||col(r0 + 1:)||^2 exactly and x0 = col(r0); the
+  // column goes out from row r0 on.
+  auto publish = [&](int buf, unsigned k, int jc, double cn, int r0, double cj) {
+    const unsigned long long t = (unsigned long long)k << 32;
+    double sg = 0.0, x0 = 0.0;
+    if (jc >= 0) {
+      double *col = cols + (int64_t)jc * l;
+      ulonglong2 *dst = P.pcol + ((int64_t)buf * G + b) * l;
+      for (int r = r0 + lane; r < l; r += 32) {
+        double x = col[r];
+        if (cj != 0.0) {
+          x = fma(-cj, s_v[r - r0 + 1], x);
+          col[r] = x;
+        }
+        st_word(dst + r, dbits(x), t);
+        if (r > r0) sg = fma(x, x, sg);
+        else x0 = x;  // lane 0
+      }
+      sg = warp_sum(sg);
+    }
+    if (lane == 0) {
+      ulonglong2 *rc = P.rec + ((int64_t)buf * G + b) * kRecWords;
+      st_word(rc + 1, dbits(sg), t);
+      st_word(rc + 2, dbits(x0), t);
+      st_word(rc, dbits(jc >= 0 ? cn : -1.0),
+              (unsigned long long)(unsigned)(jc >= 0 ? (int)(c0 + jc) : -1) | t);
+    }
+  };
+  // Exchange k: warp 0 publishes, then counts itself in (a relaxed atomic:
+  // everything it published is tagged); the k G-th arrival reads all G
+  // records (re-reading any whose words do not carry k yet), picks the
+  // winner and writes it to every other CTA's line as two words tagged in
+  // bits 48..63 of their first halves: (index | CTA << 32 | k << 48, sigma)
+  // and (same, x0).  It keeps the winner in registers itself.
   unsigned won = 0;
   unsigned long long won_w0 = 0;
   double won_sigma = 0.0, won_x0 = 0.0;
-  auto arrive = [&](int buf) {
-    ++nsteps;
-    const unsigned done = nsteps * (unsigned)G;
+  auto arrive = [&](int buf, unsigned k, int site) -> bool {
     unsigned old = 0;
-    __syncwarp();
-    if (lane == 0) old = atom_add_acq_rel(P.arrive, 1u);
+    if (lane == 0) old = atomicAdd(P.arrive, 1u);
     old = __shfl_sync(0xffffffffu, old, 0);
-    __syncwarp();
-    if (old != done - 1u) return;
-    // both halves of every record in one round of loads; the reduction
-    // carries (norm, index, CTA), and sigma and x0 come from the lane that
-    // holds the winning entry
+    if (old != k * (unsigned)G - 1u) return true;
+    const ulonglong2 *rb = P.rec + (int64_t)buf * G * kRecWords;
     double bn = -1.0, bs = 0.0, bx = 0.0;
     int bi = -1, bc = -1;
-    if (G <= 160) {
-      double2 e[5], f[5];
+    Deadline dl;
+    for (int cb = 0; cb < G; cb += 32 * 5) {
+      ulonglong2 w0[5], w1[5], w2[5];
+      unsigned pend = 0;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const int c = lane + 32 * k;
-        e[k] = c < G ? __ldcg(P.cand + 2 * (buf * G + c))
-                     : make_double2(-1.0, __longlong_as_double(-1LL));
-        f[k] = c < G ? __ldcg(P.cand + 2 * (buf * G + c) + 1) : make_double2(0.0, 0.0);
+      for (int j = 0; j < 5; ++j) {
+        w0[j] = w1[j] = w2[j] = make_ulonglong2(0ull, 0ull);
+        if (cb + lane + 32 * j < G) pend |= 1u << j;
+      }
+      while (true) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+          if (pend & (1u << j)) {
+            const ulonglong2 *rc = rb + (int64_t)(cb + lane + 32 * j) * kRecWords;
+            w0[j] = ld_word(rc);
+            w1[j] = ld_word(rc + 1);
+            w2[j] = ld_word(rc + 2);
+          }
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+          if ((pend & (1u << j)) && tag_of(w0[j]) == k && tag_of(w1[j]) == k && tag_of(w2[j]) == k)
+            pend &= ~(1u << j);
+        if (!__any_sync(0xffffffffu, pend != 0)) break;
+        int give_up = 0;
+        if (lane == 0) give_up = expired(P.ctrl, dl, P.limit_ns, site) ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const int ci = (int)__double_as_longlong(e[k].y);
-        if (better(e[k].x, ci, bn, bi)) {
-          bn = e[k].x; bi = ci; bc = lane + 32 * k; bs = f[k].x; bx = f[k].y;
+      for (int j = 0; j < 5; ++j) {
+        const int c = cb + lane + 32 * j;
+        const double nv = dval(w0[j].x);
+        const int iv = (int)(unsigned)(w0[j].y & 0xffffffffull);
+        if (c < G && better(nv, iv, bn, bi)) {
+          bn = nv; bi = iv; bc = c; bs = dval(w1[j].x); bx = dval(w2[j].x);
         }
-      }
-    } else {
-      for (int c = lane; c < G; c += 32) {
-        const double2 e = __ldcg(P.cand + 2 * (buf * G + c));
-        const double2 f = __ldcg(P.cand + 2 * (buf * G + c) + 1);
-        const int ci = (int)__double_as_longlong(e.y);
-        if (better(e.x, ci, bn, bi)) { bn = e.x; bi = ci; bc = c; bs = f.x; bx = f.y; }
       }
     }
 #pragma unroll
@@ -247,86 +255,69 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
       if (better(on, oi, bn, bi)) { bn = on; bi = oi; bc = oc; }
     }
-    // entry c sits in lane c mod 32, whose own best it is
+    // record c was read by lane c mod 32, whose own best it is
     bs = __shfl_sync(0xffffffffu, bs, bc & 31);
     bx = __shfl_sync(0xffffffffu, bx, bc & 31);
-    const unsigned long long w0 = (unsigned long long)(unsigned)bi |
-                                  ((unsigned long long)((unsigned)bc & 0xffffu) << 32) |
-                                  ((unsigned long long)(nsteps & 0xffffu) << 48);
-    // every lane is ordered after lane 0's acquire (the warp barrier above),
-    // so its fence releases what that acquire made visible
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    const unsigned long long w = (unsigned long long)(unsigned)bi |
+                                 ((unsigned long long)((unsigned)bc & 0xffffu) << 32) |
+                                 ((unsigned long long)(k & 0xffffu) << 48);
     for (int c = lane; c < G; c += 32) {
-      if (c == b) continue;  // this CTA takes the winner from registers
-      st_relaxed_b128(P.rec + 16 * (int64_t)c + 2, w0, (unsigned long long)__double_as_longlong(bx));
-      st_relaxed_b128(P.rec + 16 * (int64_t)c, w0, (unsigned long long)__double_as_longlong(bs));
+      if (c == b) continue;
+      st_word(P.win + 8 * (int64_t)c + 1, w, dbits(bx));
+      st_word(P.win + 8 * (int64_t)c, w, dbits(bs));
     }
-    won = nsteps;
-    won_w0 = w0;
+    won = k;
+    won_w0 = w;
     won_sigma = bs;
     won_x0 = bx;
+    return true;
   };
-  // thread 0: the winner of step barrier k (given here: nsteps counts only
-  // in warp 0), from its own registers when this CTA arrived last, else
-  // from this CTA's records
-  auto wait_winner = [&](int site, unsigned k) {
+  // thread 0: the winner of exchange k, from registers when this CTA
+  // arrived last, else from the two words in its line; all threads return
+  // whether it succeeded.  `extra` > 0 (the timeout test) asks for a tag
+  // that never comes.
+  auto wait_winner = [&](unsigned k, int site) {
     if (tid == 0) {
-      unsigned long long a0 = won_w0, a1 = (unsigned long long)__double_as_longlong(won_sigma),
-                         b1 = (unsigned long long)__double_as_longlong(won_x0);
+      unsigned long long a0 = won_w0, a1 = dbits(won_sigma), b0 = won_w0, b1 = dbits(won_x0);
       bool ok = true;
-      if (won != k || P.extra != 0)
-        ok = wait_records(P.ctrl, P.rec + 16 * (int64_t)b, (k + P.extra) & 0xffffu, a0, a1, b1,
-                          P.limit_ns, site);
-      s_ok = ok;
-      s_win_idx = (int)(unsigned)(a0 & 0xffffffffULL);
-      s_win_cta = (int)((a0 >> 32) & 0xffffULL);
-      s_sigma = __longlong_as_double((long long)a1);
-      s_x0 = __longlong_as_double((long long)b1);
-    }
-    __syncthreads();
-    return s_ok != 0;
-  };
-  // plain barrier after the l step barriers
-  auto final_sync = [&](int site) {
-    __syncthreads();
-    if (tid == 0) {
-      red_add_release(P.arrive, 1u);
-      s_ok = wait_count(P.ctrl, P.arrive, (unsigned)(l + 1) * (unsigned)G + P.extra, P.limit_ns,
-                        site);
-    }
-    __syncthreads();
-    return s_ok != 0;
-  };
-  // warp 0: publish candidate jc (local index, key cn) of the next step,
-  // whose column is final through row r0 - 1 once cj x(r0:) (cj != 0: the
-  // step's axpy, applied here) is subtracted: the record (cn, index), sigma =
-  // ||col(r0 + 1:)||^2 exactly and x0 = col(r0), and the column from row r0 on
-  auto publish = [&](int buf, int jc, double cn, int r0, double cj) {
-    double sg = 0.0, x0 = 0.0;
-    if (jc >= 0) {
-      double *col = cols + (int64_t)jc * l;
-      double *dst = P.pcol + ((int64_t)buf * G + b) * l;
-      for (int r = r0 + lane; r < l; r += 32) {
-        double x = col[r];
-        if (cj != 0.0) {
-          x = fma(-cj, s_v[r - r0 + 1], x);
-          col[r] = x;
+      if (won != k || P.extra != 0) {
+        const unsigned want = (k + P.extra) & 0xffffu;
+        const ulonglong2 *wa = P.win + 8 * (int64_t)b;
+        Deadline dl;
+        bool ha = false, hb = false;
+        while (true) {
+          if (!ha) {
+            const ulonglong2 w = ld_word(wa);
+            a0 = w.x;
+            a1 = w.y;
+            ha = (unsigned)(a0 >> 48) == want;
+          }
+          if (!hb) {
+            const ulonglong2 w = ld_word(wa + 1);
+            b0 = w.x;
+            b1 = w.y;
+            hb = (unsigned)(b0 >> 48) == want;
+          }
+          if (ha && hb) break;
+          if (expired(P.ctrl, dl, P.limit_ns, site)) {
+            ok = false;
+            break;
+          }
         }
-        dst[r] = x;
-        if (r > r0) sg = fma(x, x, sg);
-        else x0 = x;  // lane 0
       }
-      sg = warp_sum(sg);
+      s_ok = ok ? 1 : 0;
+      s_win_idx = (int)(unsigned)(a0 & 0xffffffffull);
+      s_win_cta = (int)((a0 >> 32) & 0xffffull);
+      s_sigma = dval(a1);
+      s_x0 = dval(b1);
     }
-    if (lane == 0) {
-      P.cand[2 * (buf * G + b)] =
-          make_double2(jc >= 0 ? cn : -1.0, __longlong_as_double(jc >= 0 ? (long long)(c0 + jc) : -1LL));
-      P.cand[2 * (buf * G + b) + 1] = make_double2(sg, x0);
-    }
+    __syncthreads();
+    return s_ok != 0;
   };
 
   // nothing to do after an earlier error (its data may be garbage)
   if (ld_volatile_i32(&P.ctrl->status) < 0) return;
+  if (tid == 0) s_err = 0;
 
   // ---- load the slab, exact initial norms ------------------------------
   for (int jj = warp; jj < nc; jj += kWarps) {
@@ -361,16 +352,16 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       int ci = s_bi[0];
       for (int w = 1; w < kWarps; ++w)
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
-      publish(0, ci >= 0 ? (int)(ci - c0) : -1, cn, 0, 0.0);
-      arrive(0);
+      publish(0, 1u, ci >= 0 ? (int)(ci - c0) : -1, cn, 0, 0.0);
+      if (!arrive(0, 1u, 1)) s_err = 1;
     }
   }
-  if (!wait_winner(1, 1u)) return;
+  if (!wait_winner(1u, 1) || s_err) return;
 
   const int sub = lane >> 2, gl = lane & 3;
   for (int s = 0; s < l; ++s) {
     const int buf = s & 1;
-    // ---- 1. winner (picked by the last CTA to arrive) and its sigma ----
+    // ---- 1. winner (every CTA picked the same one) and its sigma ----
     const int wc = s_win_cta, wi = s_win_idx;
     if (wi < 0 || wc < 0 || wc >= G) {
       if (tid == 0) set_status(P.ctrl, RQLP_ERR_INVALID_ARG);
@@ -381,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     // alpha = ||x|| >= 0: tau = 1 - x0/alpha, v(1:) = x(1:) / (x0 - alpha),
     // where x0 > 0 uses x0 - alpha = -sigma / (x0 + alpha) (no cancellation);
     // x0 and sigma = ||x(1:)||^2 came with the winner's record, so this runs
-    // while the other threads load the column
+    // while warps 1.. load the column
     if (tid == 0) {
       const double x0 = s_x0, sigma = s_sigma;
       double tau, beta, rv0;
@@ -409,11 +400,23 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       s_rv0 = rv0;
       s_trv = tau * rv0;
     }
-    // warps 1.. load the column meanwhile
-    const double *xc = P.pcol + ((int64_t)buf * G + wc) * l;
+    // warps 1.. load the column (published for exchange s + 1) meanwhile
+    const ulonglong2 *xc = P.pcol + ((int64_t)buf * G + wc) * l;
     if (warp > 0)
-      for (int r = s + tid - 32; r < l; r += kThreads - 32) s_v[r - s] = __ldcg(xc + r);
+      for (int r = s + tid - 32; r < l; r += kThreads - 32) {
+        ulonglong2 w = ld_word(xc + r);
+        Deadline dl;
+        while (tag_of(w) != (unsigned)(s + 1)) {
+          if (expired(P.ctrl, dl, P.limit_ns, 4)) {
+            s_err = 1;
+            break;
+          }
+          w = ld_word(xc + r);
+        }
+        s_v[r - s] = dval(w.x);
+      }
     __syncthreads();
+    if (s_err) return;
     // s_v holds the winner's column x(s:) unscaled; v = (1, x(s+1:) rv0)
     const double tau = s_tau, beta = s_beta, rv0 = s_rv0, trv = s_trv;
     // the winner's column is final: rows < s from the slab, beta at s, zeros below
@@ -491,14 +494,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
       jc = ci >= 0 ? (int)(ci - c0) : -1;
     }
-    // ---- 4. warp 0: update the candidate, publish it, arrive ----
+    // ---- 4. warp 0: update the candidate and publish it ----
     if (warp == 0 && s + 1 < l) {
-      publish(buf ^ 1, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0);
-      arrive(buf ^ 1);
+      const unsigned k = (unsigned)(s + 2);
+      publish(buf ^ 1, k, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0);
+      if (!arrive(buf ^ 1, k, 5) && lane == 0) s_err = 1;
     }
-    // ---- 5. the remaining axpys, while the barrier completes ----
-    // (warps 1..: warp 0 goes from its arrival, and the last arriver's
-    // scan, straight to the next wait)
+    // ---- 5. the remaining axpys, while warp 0 arrives (and, if last, picks
+    // the winner) ----
     if (b == 0 && warp == kWarps - 1) {
       // this step's reflector, off the path to the barrier
       for (int r = lane; r < l; r += 32)
@@ -513,25 +516,53 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
         for (int r = s + 1 + gl; r < l; r += 4) col[r] = fma(-cf, s_v[r - s], col[r]);
       }
     }
-    // (the wait's own barrier orders these axpys before the next column load)
-    if (s + 1 < l && !wait_winner(2, (unsigned)(s + 2))) return;
+    // (the wait's block barrier orders these axpys before the next column load)
+    if (s + 1 < l && (!wait_winner((unsigned)(s + 2), 2) || s_err)) return;
   }
 
   // ---- unchosen columns keep their order behind the l pivots ----
-  int mine = 0;
-  if (tid == 0) {
-    for (int jj = 0; jj < nc; ++jj) mine += pivoted[jj] ? 0 : 1;
-    P.counts[b] = mine;
-  }
-  __syncthreads();
-  if (!final_sync(3)) return;
-  __shared__ int s_prefix;
-  if (tid == 0) {
+  // one more exchange (l + 1, record word 0): the number of unchosen columns
+  // of every CTA; CTA b needs those of CTAs 0..b-1
+  if (warp == 0) {
+    const unsigned kf = (unsigned)(l + 1);
+    const int fb = l & 1;
+    int mine = 0;
+    for (int jj = lane; jj < nc; jj += 32) mine += pivoted[jj] ? 0 : 1;
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0)
+      st_word(P.rec + ((int64_t)fb * G + b) * kRecWords, (unsigned long long)mine,
+              (unsigned long long)kf << 32);
     int pre = 0;
-    for (int c = 0; c < b; ++c) pre += __ldcg(P.counts + c);
-    s_prefix = pre;
+    bool ok = true;
+    Deadline dl;
+    for (int cb = 0; cb < b && ok; cb += 32) {
+      const int c = cb + lane;
+      bool pend = c < b;
+      while (true) {
+        if (pend) {
+          const ulonglong2 w = ld_word(P.rec + ((int64_t)fb * G + c) * kRecWords);
+          if (tag_of(w) == kf) {
+            pend = false;
+            pre += (int)w.x;
+          }
+        }
+        if (!__any_sync(0xffffffffu, pend)) break;
+        int give_up = 0;
+        if (lane == 0) give_up = expired(P.ctrl, dl, P.limit_ns, 3) ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, give_up, 0)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    pre = __reduce_add_sync(0xffffffffu, pre);
+    if (lane == 0) {
+      s_prefix = pre;
+      s_ok = ok ? 1 : 0;
+    }
   }
   __syncthreads();
+  if (!s_ok) return;
   if (warp == 0) {
     // rank of each unpivoted column within the slab, in index order
     int pos = l + s_prefix;
@@ -582,13 +613,16 @@ Plan plan_for(int64_t n, int l) {
 
 }  // namespace
 
+// per-launch exchange state, zeroed before every launch: the arrival
+// counter (one 128-byte line), the winner lines (one per CTA), the tagged
+// candidate records and the tagged published columns (both double-buffered)
+static size_t tagged_bytes(int G, int l) {
+  return 128 + 128 * (size_t)G + 2 * (size_t)G * kRecWords * sizeof(ulonglong2) +
+         2 * (size_t)G * l * sizeof(ulonglong2);
+}
+
 size_t cpqr_ws_bytes(int64_t n, int l) {
-  const size_t G = kMaxGrid;
-  size_t b = 0;
-  b += 128 + 128 * G;  // counter line, one record line per CTA
-  b += 4 * G * sizeof(double2);
-  b += 2 * G * (size_t)l * sizeof(double);
-  b += G * sizeof(int32_t);
+  size_t b = (tagged_bytes(kMaxGrid, l) + 255) / 256 * 256;
   b += (size_t)(n + kMaxGrid) * l * sizeof(double);  // global slabs (fallback)
   return b + 8192;
 }
@@ -596,9 +630,7 @@ size_t cpqr_ws_bytes(int64_t n, int l) {
 size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   const Plan pl = plan_for(n, l);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
-  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(128 + 128 * (size_t)pl.G) + up(4 * (size_t)pl.G * sizeof(double2)) +
-         up(2 * (size_t)pl.G * l * sizeof(double)) + up((size_t)pl.G * sizeof(int32_t));
+  return (tagged_bytes(pl.G, l) + 255) / 256 * 256;
 }
 
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
@@ -621,13 +653,12 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   CpqrParams P;
   P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
-  const size_t sync_bytes = 128 + 128 * (size_t)pl.G;
-  char *sync = take(sync_bytes);
-  P.arrive = reinterpret_cast<unsigned *>(sync);
-  P.rec = reinterpret_cast<unsigned long long *>(sync + 128);
-  P.cand = reinterpret_cast<double2 *>(take(4 * (size_t)pl.G * sizeof(double2)));
-  P.pcol = reinterpret_cast<double *>(take(2 * (size_t)pl.G * l * sizeof(double)));
-  P.counts = reinterpret_cast<int32_t *>(take((size_t)pl.G * sizeof(int32_t)));
+  const size_t tb = tagged_bytes(pl.G, l);
+  char *tagged = take(tb);
+  P.arrive = reinterpret_cast<unsigned *>(tagged);
+  P.win = reinterpret_cast<ulonglong2 *>(tagged + 128);
+  P.rec = reinterpret_cast<ulonglong2 *>(tagged + 128 + 128 * (size_t)pl.G);
+  P.pcol = P.rec + 2 * (size_t)pl.G * kRecWords;
   P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));
   P.ctrl = ctrl;
   P.limit_ns = limit_ns ? limit_ns : kDefaultSpinNs;
@@ -637,11 +668,11 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   // the permutation stays valid even if the kernel stops early on an error
   e = iota(piv, n, st);
   if (e != cudaSuccess) return e;
-  // barrier counter and winner records of this launch
-  e = cudaMemsetAsync(sync, 0, sync_bytes, st);
+  // no tagged word of an earlier launch may match this launch's exchanges
+  e = cudaMemsetAsync(tagged, 0, tb, st);
   if (e != cudaSuccess) return e;
   if (pl.G == 1) {
-    // one CTA: its grid barrier never waits, no co-residency is needed
+    // one CTA: it is always the last arriver, no co-residency is needed
     if (pl.use_smem)
       k_cpqr_wide<true><<<1, kThreads, pl.smem, st>>>(P);
     else

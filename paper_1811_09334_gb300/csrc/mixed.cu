@@ -462,10 +462,8 @@ k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloa
       if (vec && j + 1 < n) {
         if (sizeof(T) == 8) {
           const double2 p = *reinterpret_cast<const double2 *>(A + i * lda + j);
-          // one conversion instruction (FP64 unit) and one integer-pipe
-          // rounding: the two pipes share the load
           f0 = (float)p.x;
-          f1 = d2f_rn(p.y);
+          f1 = (float)p.y;
         } else {
           const float2 p = *reinterpret_cast<const float2 *>(A + i * lda + j);
           f0 = p.x;
