@@ -74,8 +74,9 @@ typedef struct {
   int32_t pivot2;       /* 1: Algorithm 2.1, second QR column-pivoted; 0: Algorithm 2.2 */
   int32_t prec;         /* rqlp_prec */
   int32_t block_b;      /* 0: unblocked; b > 0: Algorithm 4.1 with blocks of b columns (b divides l) */
-  int32_t debug_flags;  /* 0 in normal use; bit 0: the first device-side grid barrier waits for one
-                           arrival too many, so that it runs out of time (tests of the timeout path) */
+  int32_t debug_flags;  /* 0 in normal use; bit 0: the first grid-wide exchange of the pivoted QR
+                           waits for an exchange number that never comes, so that it runs out of
+                           time (tests of the timeout path) */
   int64_t spin_limit_ns;/* bound on every device-side wait in ns; 0 selects 2 s */
 } rqlp_opts;
 

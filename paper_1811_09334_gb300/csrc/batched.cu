@@ -6,7 +6,7 @@
 // so that independent problems run side by side, and instantiates it once;
 // rqlp_batched_launch() replays it with a single cudaGraphLaunch.  While
 // recording, launch shapes are lowered so that one problem does not claim the
-// whole GPU: the CPQR of B runs as one CTA (no grid barrier, nothing waits on
+// whole GPU: the CPQR of B runs as one CTA (its exchanges never wait on
 // another CTA), and the split-K targets of the FP64 and tensor-core products
 // come from the tuning record (picked by the autotuner).  Problems of one
 // branch run one after another and share one workspace; each problem's status

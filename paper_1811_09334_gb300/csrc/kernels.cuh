@@ -17,7 +17,7 @@ int num_sms();
 // defaults, which are upper bounds of every tuned value.
 struct Tuning {
   int gemm_target_ctas;  // FP64 GEMM: split K until about this many CTAs (0: 3 x SMs)
-  int cpqr_max_ctas;     // CPQR of B: at most this many CTAs (0: one per SM; 1: no grid barrier)
+  int cpqr_max_ctas;     // CPQR of B: at most this many CTAs (0: one per SM; 1: one CTA, no waits on others)
   int mma_max_splits;    // tcgen05 products: at most this many K splits (0: fill the SMs)
   int chol_ctas;         // Cholesky of the Gram matrix: cluster of 16 or 8 CTAs, or 1 CTA
                          // (0: 16 where such a cluster fits, else 8)

@@ -168,8 +168,9 @@ def test_nonfinite_input_is_reported(R):
 
 
 def test_device_wait_timeout_is_reported_and_context_survives(R):
-    # The first grid barrier of the CPQR kernel waits for one arrival that
-    # never comes; the bounded wait gives up after 50 ms and reports a status.
+    # The first grid-wide exchange of the CPQR kernel waits for an exchange
+    # number that never comes; the bounded wait gives up after 50 ms and
+    # reports a status.
     pr = W.c1(m=400, n=300, k=10, p=5)
     Om = _t(W.omega(pr.n, pr.l, 0))
     A = _t(pr.A)
