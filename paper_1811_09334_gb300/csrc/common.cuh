@@ -169,6 +169,12 @@ __device__ __forceinline__ void stage_smem(int n, const double *any, Src src, Ds
   }
 }
 
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum over the whole CTA; `red` is shared scratch of >= 32 doubles.  All
 // threads receive the result.
 __device__ inline double block_sum(double v, double *red) {
