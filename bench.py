@@ -47,11 +47,11 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA-core and DMMA) nominal rate
 _TRAFFIC = {
     "cpqr_of_B": {
         "source": "paper_1811_09334_gb300/csrc/cpqr.cu",
-        "sha256": "b67f757d26f7352c403c54216966d233dc34b38d74a359e43a30f0ec67c17a82",
+        "sha256": "a1fffd55bad28cf00240e7f44fb614f1b70645eaad4cd22996092324d56738e2",
         "profile": "profiles/k_cpqr_wide_b110x4096.md",
         # dram__bytes_read.sum + dram__bytes_write.sum at n = 4096 columns
-        # (3.71 MB + 1.0 KB), scaled by the columns processed
-        "bytes_per_column": (3.712256e6 + 1.024e3) / 4096,
+        # (3.72 MB + 9.7 KB), scaled by the columns processed
+        "bytes_per_column": (3.717376e6 + 9.728e3) / 4096,
     },
 }
 

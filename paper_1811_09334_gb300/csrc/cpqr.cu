@@ -168,9 +168,13 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   // (cj != 0: the step's axpy, applied here) is subtracted.  The record is
   // (cn, index), sigma = ||col(r0 + 1:)||^2 exactly and x0 = col(r0); the
   // column goes out from row r0 on.
-  auto publish = [&](int buf, unsigned k, int jc, double cn, int r0, double cj) {
+  // One CTA (G = 1) exchanges nothing: it keeps sigma and x0 (lane 0) and
+  // takes the winner, its own candidate, straight from shared memory.
+  auto publish = [&](int buf, unsigned k, int jc, double cn, int r0, double cj, double &sg,
+                     double &x0) {
     const unsigned long long t = (unsigned long long)k << 32;
-    double sg = 0.0, x0 = 0.0;
+    sg = 0.0;
+    x0 = 0.0;
     if (jc >= 0) {
       double *col = cols + (int64_t)jc * l;
       ulonglong2 *dst = P.pcol + ((int64_t)buf * G + b) * l;
@@ -180,13 +184,13 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
           x = fma(-cj, s_v[r - r0 + 1], x);
           col[r] = x;
         }
-        st_word(dst + r, dbits(x), t);
+        if (G > 1) st_word(dst + r, dbits(x), t);
         if (r > r0) sg = fma(x, x, sg);
         else x0 = x;  // lane 0
       }
       sg = warp_sum(sg);
     }
-    if (lane == 0) {
+    if (lane == 0 && G > 1) {
       ulonglong2 *rc = P.rec + ((int64_t)buf * G + b) * kRecWords;
       st_word(rc + 1, dbits(sg), t);
       st_word(rc + 2, dbits(x0), t);
@@ -272,6 +276,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     won_x0 = bx;
     return true;
   };
+  // G = 1: lane 0 of warp 0 records its own candidate as exchange k's winner
+  auto keep_own = [&](unsigned k, int jc, double sg, double x0) {
+    won = k;
+    won_w0 = (unsigned long long)(unsigned)(jc >= 0 ? (int)(c0 + jc) : -1) |
+             ((unsigned long long)(k & 0xffffu) << 48);
+    won_sigma = sg;
+    won_x0 = x0;
+  };
   // thread 0: the winner of exchange k, from registers when this CTA
   // arrived last, else from the two words in its line; all threads return
   // whether it succeeded.  `extra` > 0 (the timeout test) asks for a tag
@@ -352,8 +364,11 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       int ci = s_bi[0];
       for (int w = 1; w < kWarps; ++w)
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
-      publish(0, 1u, ci >= 0 ? (int)(ci - c0) : -1, cn, 0, 0.0);
-      if (!arrive(0, 1u, 1)) s_err = 1;
+      const int jc0 = ci >= 0 ? (int)(ci - c0) : -1;
+      double sg, x0;
+      publish(0, 1u, jc0, cn, 0, 0.0, sg, x0);
+      if (G == 1) keep_own(1u, jc0, sg, x0);
+      else if (!arrive(0, 1u, 1)) s_err = 1;
     }
   }
   if (!wait_winner(1u, 1) || s_err) return;
@@ -402,7 +417,12 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     }
     // warps 1.. load the column (published for exchange s + 1) meanwhile
     const ulonglong2 *xc = P.pcol + ((int64_t)buf * G + wc) * l;
-    if (warp > 0)
+    if (G == 1) {
+      // the winner is this CTA's own column, updated in the slab
+      const double *own = cols + (int64_t)(wi - c0) * l;
+      if (warp > 0)
+        for (int r = s + tid - 32; r < l; r += kThreads - 32) s_v[r - s] = own[r];
+    } else if (warp > 0)
       for (int r = s + tid - 32; r < l; r += kThreads - 32) {
         ulonglong2 w = ld_word(xc + r);
         Deadline dl;
@@ -497,8 +517,10 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     // ---- 4. warp 0: update the candidate and publish it ----
     if (warp == 0 && s + 1 < l) {
       const unsigned k = (unsigned)(s + 2);
-      publish(buf ^ 1, k, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0);
-      if (!arrive(buf ^ 1, k, 5) && lane == 0) s_err = 1;
+      double sg, x0;
+      publish(buf ^ 1, k, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0, sg, x0);
+      if (G == 1) keep_own(k, jc, sg, x0);
+      else if (!arrive(buf ^ 1, k, 5) && lane == 0) s_err = 1;
     }
     // ---- 5. the remaining axpys, while warp 0 arrives (and, if last, picks
     // the winner) ----
