@@ -133,6 +133,20 @@ int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t
               double *P_host, double *Lvalues_host, int32_t *piv0_host, int32_t *piv1_host,
               void *ws, size_t ws_bytes, rqlp_stream_t stream);
 
+/*
+ * rqlp_host() without the final synchronization: enqueues the copies in,
+ * the factorization and the copies out on `stream` and returns at once
+ * (RQLP_OK, or an argument or CUDA error found while enqueueing).  The host
+ * buffers must stay valid and untouched until the stream has finished;
+ * rqlp_read_status(ws, stream) then gives the device status.  Calls with
+ * their own workspaces and streams overlap one problem's copies with
+ * another's factorization (double buffering across a sequence of problems).
+ */
+int rqlp_host_async(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k,
+                    int32_t p, const double *Omega_host, const rqlp_opts *opts, double *Q_host,
+                    double *L_host, double *P_host, double *Lvalues_host, int32_t *piv0_host,
+                    int32_t *piv1_host, void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Stage entry points (each one a step of Algorithm 2.1 / 2.2).  They use the
  * same workspace rules; rqlp_stage_workspace_size() covers all of them.

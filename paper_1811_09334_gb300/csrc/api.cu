@@ -503,10 +503,10 @@ size_t rqlp_host_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, cons
          up((size_t)l * 4);
 }
 
-int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k, int32_t p,
-              const double *Omega_host, const rqlp_opts *opts, double *Q_host, double *L_host,
-              double *P_host, double *Lvalues_host, int32_t *piv0_host, int32_t *piv1_host,
-              void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+int rqlp_host_async(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k,
+                    int32_t p, const double *Omega_host, const rqlp_opts *opts, double *Q_host,
+                    double *L_host, double *P_host, double *Lvalues_host, int32_t *piv0_host,
+                    int32_t *piv1_host, void *ws, size_t ws_bytes, rqlp_stream_t stream) {
   if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
   if (!A_host || !Omega_host || !Q_host || !L_host || !P_host || !ws) return RQLP_ERR_INVALID_ARG;
   if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
@@ -537,7 +537,17 @@ int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t
   if (Lvalues_host) CK(cudaMemcpyAsync(Lvalues_host, dLv, (size_t)l * 8, cudaMemcpyDeviceToHost, st));
   if (piv0_host) CK(cudaMemcpyAsync(piv0_host, dp0, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
   if (piv1_host) CK(cudaMemcpyAsync(piv1_host, dp1, (size_t)l * 4, cudaMemcpyDeviceToHost, st));
-  return rqlp_read_status(c, stream);
+  return RQLP_OK;
+}
+
+int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k, int32_t p,
+              const double *Omega_host, const rqlp_opts *opts, double *Q_host, double *L_host,
+              double *P_host, double *Lvalues_host, int32_t *piv0_host, int32_t *piv1_host,
+              void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  const int r = rqlp_host_async(A_host, a_dtype, m, n, k, p, Omega_host, opts, Q_host, L_host,
+                                P_host, Lvalues_host, piv0_host, piv1_host, ws, ws_bytes, stream);
+  if (r != RQLP_OK) return r;
+  return rqlp_read_status(ws, stream);
 }
 
 // ---------------------------------------------------------------- stages

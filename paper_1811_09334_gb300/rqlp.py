@@ -65,6 +65,9 @@ _SIGS = {
     "rqlp_host": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i32, _c_i32, _c_p,
                            ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz,
                            _c_p]),
+    "rqlp_host_async": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i32, _c_i32, _c_p,
+                                 ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                 _c_sz, _c_p]),
     "rqlp_stage_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32]),
     "rqlp_sketch": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_p, _c_i64, _c_i32, _c_i32,
                              _c_p, _c_i64, _c_p, _c_sz, _c_p]),
@@ -239,14 +242,8 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
     return res
 
 
-def rqlp_host(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1, pivot2: bool = True,
-              prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
-              device="cuda", stream=None) -> dict:
-    """rqlp() on host tensors: copies in, factors, copies out, synchronizes.
-
-    A_host / Omega_host are CPU tensors (pinned for full copy speed); the
-    results come back in CPU tensors (pinned when `out` is not given).
-    """
+def _host_call(entry: str, A_host, k, p, Omega_host, q, d, pivot2, prec, block_b, ws, out,
+               device, stream) -> dict:
     torch = _torch()
     m, n = A_host.shape
     l = k + p
@@ -268,15 +265,48 @@ def rqlp_host(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1, pivot2
                    Lvalues=torch.empty((l,), dtype=torch.float64, **pin),
                    piv0=torch.empty((n,), dtype=torch.int32, **pin),
                    piv1=torch.empty((l,), dtype=torch.int32, **pin))
-    code = L_.rqlp_host(_ptr(A_host), dt, m, n, k, p, _ptr(Omega_host), ctypes.byref(o),
-                        _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]), _ptr(out["Lvalues"]),
-                        _ptr(out["piv0"]), _ptr(out["piv1"]), _ptr(ws), ws.numel(),
-                        _stream(stream))
-    _check(code, "rqlp_host")
+    code = getattr(L_, entry)(_ptr(A_host), dt, m, n, k, p, _ptr(Omega_host), ctypes.byref(o),
+                              _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]),
+                              _ptr(out["Lvalues"]), _ptr(out["piv0"]), _ptr(out["piv1"]),
+                              _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, entry)
     res = dict(out)
     res["ws"] = ws
     res["status"] = code
+    res["stream"] = stream
     return res
+
+
+def rqlp_host(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1, pivot2: bool = True,
+              prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
+              device="cuda", stream=None) -> dict:
+    """rqlp() on host tensors: copies in, factors, copies out, synchronizes.
+
+    A_host / Omega_host are CPU tensors (pinned for full copy speed); the
+    results come back in CPU tensors (pinned when `out` is not given).
+    """
+    return _host_call("rqlp_host", A_host, k, p, Omega_host, q, d, pivot2, prec, block_b, ws,
+                      out, device, stream)
+
+
+def rqlp_host_async(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1,
+                    pivot2: bool = True, prec: str = "fp64", block_b: int = 0, ws=None,
+                    out: Optional[dict] = None, device="cuda", stream=None) -> dict:
+    """rqlp_host() without the final synchronization: everything is enqueued
+    on `stream`.  The host tensors must stay alive and untouched, and the
+    results are valid, only after host_wait() on the returned dict.  Calls
+    with their own workspaces and streams overlap one problem's copies with
+    another's factorization."""
+    return _host_call("rqlp_host_async", A_host, k, p, Omega_host, q, d, pivot2, prec, block_b,
+                      ws, out, device, stream)
+
+
+def host_wait(res: dict) -> int:
+    """Waits for an rqlp_host_async() call; raises on a device error."""
+    code = lib().rqlp_read_status(_ptr(res["ws"]), _stream(res.get("stream")))
+    _check(code, "rqlp_host_async (device status)")
+    res["status"] = code
+    return code
 
 
 # ------------------------------------------------------------------ stages

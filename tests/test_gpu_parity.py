@@ -191,6 +191,36 @@ def test_host_entry_point_matches_device_path(R):
         assert torch.equal(dev[key].cpu(), host[key]), key
 
 
+def test_host_async_two_streams_match_device_path(R):
+    """Two problems in flight on two streams (the double-buffered host path):
+    every result equals that problem's device-path result, including when a
+    slot's workspace and host buffers are reused for the next problem."""
+    probs = []
+    for seed, (m, n) in enumerate(((900, 400), (700, 500))):
+        pr = W.c1(m=m, n=n, k=12, p=4)
+        Om = W.omega(pr.n, pr.l, seed)
+        dev = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False, prec="bf16x3")
+        probs.append((torch.from_numpy(pr.A).pin_memory(), torch.from_numpy(Om).pin_memory(),
+                      pr, {k: dev[k].cpu() for k in ("Q", "L", "P", "Lvalues", "piv0", "piv1")}))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    slots = [None, None]
+    for i in range(4):
+        A_h, Om_h, pr, ref = probs[i % 2]
+        sl = slots[i % 2]
+        if sl is not None:
+            R.host_wait(sl)
+            for key, v in ref.items():
+                assert torch.equal(sl[key], v), (i, key)
+        slots[i % 2] = R.rqlp_host_async(
+            A_h, pr.k, pr.p, Om_h, q=1, d=2, pivot2=False, prec="bf16x3",
+            ws=None if sl is None else sl["ws"],
+            out=None if sl is None else {k: sl[k] for k in ref}, stream=streams[i % 2])
+    for i, sl in enumerate(slots):
+        R.host_wait(sl)
+        for key, v in probs[i][3].items():
+            assert torch.equal(sl[key], v), (i, key)
+
+
 @pytest.mark.slow
 def test_c2_full_size_fp64_parity(R):
     """The 8192 x 8192 ERQLP workload (q = 1, d = 2) in the launch configuration
