@@ -103,14 +103,26 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfApply, ev, st);
     return RQLP_OK;
   };
+  // X and Xq share no element: a pass may then write Xq while it reads X
+  const bool dis = X + (rows - 1) * ldx + l <= Xq || Xq + (rows - 1) * ldq + l <= X;
   int r;
   if (lowp_first && passes >= 2) {
     r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0, true);  // FP32 pass: X -> tmp
     if (r != RQLP_OK) return r;
     r = pass(o.tmp, l, Xq, ldq, false, nullptr, -1.0);      // FP64 pass: tmp -> Xq
+  } else if (lowp_first && dis) {
+    r = pass(X, ldx, Xq, ldq, true, nullptr, -1.0, true);  // one FP32 pass: X -> Xq
   } else if (lowp_first) {
-    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0, true);  // one FP32 pass
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0, true);  // one FP32 pass, in place
     if (r == RQLP_OK) CK(copy2d(o.tmp, rows, l, l, Xq, ldq, nullptr, st));
+  } else if (passes >= 2 && again_tol >= 0.0 && dis) {
+    // adaptive, usually one pass: X -> Xq; only when the first pass asks for
+    // it, Xq -> tmp -> Xq
+    r = pass(X, ldx, Xq, ldq, true, nullptr, again_tol);
+    if (r != RQLP_OK) return r;
+    r = pass(Xq, ldq, o.tmp, l, false, &ctrl->again_flag[site], -1.0);
+    if (r != RQLP_OK) return r;
+    CK(copy2d(o.tmp, rows, l, l, Xq, ldq, &ctrl->again_flag[site], st));
   } else if (passes >= 2 && again_tol >= 0.0) {
     // adaptive: the second pass runs only when the first one says it is needed
     r = pass(X, ldx, o.tmp, l, true, nullptr, again_tol);
@@ -122,8 +134,10 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0);   // pass 1: X -> tmp
     if (r != RQLP_OK) return r;
     r = pass(o.tmp, l, Xq, ldq, false, nullptr, -1.0); // pass 2: tmp -> Xq
+  } else if (dis) {
+    r = pass(X, ldx, Xq, ldq, true, nullptr, -1.0);    // one pass: X -> Xq
   } else {
-    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0);   // one pass: X -> tmp -> Xq
+    r = pass(X, ldx, o.tmp, l, true, nullptr, -1.0);   // one pass, in place: X -> tmp -> Xq
     if (r == RQLP_OK) CK(copy2d(o.tmp, rows, l, l, Xq, ldq, nullptr, st));
   }
   if (r != RQLP_OK) return r;

@@ -52,22 +52,20 @@ __global__ void k_transpose(const double *__restrict__ X, int64_t r, int64_t c, 
   }
 }
 
+// Row-major elementwise kernels run on (32, 8) blocks: lanes along a row
+// (coalesced), warps over rows, no index division per element.
 __global__ void k_copy2d(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
                          double *__restrict__ Y, int64_t ldy, const int *skip_unless) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / c, j = e - i * c;
-    Y[i * ldy + j] = X[i * ldx + j];
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < r;
+       i += (int64_t)gridDim.x * blockDim.y)
+    for (int64_t j = threadIdx.x; j < c; j += blockDim.x) Y[i * ldy + j] = X[i * ldx + j];
 }
 
 __global__ void k_set_identity(double *X, int64_t r, int64_t c, int64_t ld) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * c;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / c, j = e - i * c;
-    X[i * ld + j] = (i == j) ? 1.0 : 0.0;
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < r;
+       i += (int64_t)gridDim.x * blockDim.y)
+    for (int64_t j = threadIdx.x; j < c; j += blockDim.x) X[i * ld + j] = (i == j) ? 1.0 : 0.0;
 }
 
 __global__ void k_gather_cols(const double *__restrict__ X, int64_t r, int64_t c, int64_t ldx,
@@ -257,6 +255,13 @@ __global__ void k_mask_lower_trapezoid(double *X, int64_t r, int64_t c, int64_t 
   }
 }
 
+// blocks for a (32, 8)-block row kernel: 8 rows per block, at most 4 waves
+inline int rows_grid(int64_t rows) {
+  int64_t b = (rows + 7) / 8;
+  if (b > 4LL * num_sms()) b = 4LL * num_sms();
+  return (int)std::max<int64_t>(b, 1);
+}
+
 inline int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
   if (b > 4LL * num_sms()) b = 4LL * num_sms();
@@ -291,14 +296,14 @@ cudaError_t transpose(const double *X, int64_t r, int64_t c, int64_t ldx, double
 cudaError_t copy2d(const double *X, int64_t r, int64_t c, int64_t ldx, double *Y, int64_t ldy,
                    const int *skip_unless, cudaStream_t st) {
   if (r <= 0 || c <= 0) return cudaSuccess;
-  k_copy2d<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ldx, Y, ldy, skip_unless);
+  k_copy2d<<<rows_grid(r), dim3(32, 8), 0, st>>>(X, r, c, ldx, Y, ldy, skip_unless);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t set_identity(double *X, int64_t r, int64_t c, int64_t ld, cudaStream_t st) {
   if (r <= 0 || c <= 0) return cudaSuccess;
-  k_set_identity<<<grid_for(r * c, 256), 256, 0, st>>>(X, r, c, ld);
+  k_set_identity<<<rows_grid(r), dim3(32, 8), 0, st>>>(X, r, c, ld);
   count_launch();
   return cudaGetLastError();
 }

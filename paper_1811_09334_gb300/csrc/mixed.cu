@@ -312,20 +312,19 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
 
 // C (M x ncols, FP64, ldc) = sum of S FP32 partial slices, divided by the
 // row and column scales of a scaled (FP8) product when they are given.
+// (32, 8) blocks: lanes along a row of C, warps over rows.
 __global__ void k_sum_parts_f32(const float *__restrict__ part, int S, int64_t split_stride,
                                 int64_t M, int ncols, int ldp, double *__restrict__ C,
                                 int64_t ldc, const float *__restrict__ rscale,
                                 const float *__restrict__ cscale) {
-  const int64_t total = M * ncols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / ncols;
-    const int j = (int)(e - i * ncols);
-    double s = 0.0;
-    for (int z = 0; z < S; ++z) s += f2d(part[(int64_t)z * split_stride + i * ldp + j]);
-    if (rscale) s /= f2d(rscale[i]) * f2d(cscale[j]);
-    C[i * ldc + j] = s;
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < M;
+       i += (int64_t)gridDim.x * blockDim.y)
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+      double s = 0.0;
+      for (int z = 0; z < S; ++z) s += f2d(part[(int64_t)z * split_stride + i * ldp + j]);
+      if (rscale) s /= f2d(rscale[i]) * f2d(cscale[j]);
+      C[i * ldc + j] = s;
+    }
 }
 
 // Per-row maxima of |A| and per-column maxima (one atomic max per column and
@@ -521,19 +520,38 @@ k_split_a(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloa
   }
 }
 
-// S (K x l, FP64, lds) -> S^T halves (l x ldk, BF16)
+// S (K x l, FP64, lds) -> S^T halves (l x ldk, BF16).  32 x 32 tiles on
+// (32, 8) blocks through shared memory: rows of S are read and rows of S^T
+// written along the lanes (both coalesced); blockIdx.x over column tiles of
+// S, blockIdx.y over row tiles.
 __global__ void k_split_skinny_t(const double *__restrict__ S, int64_t K, int l, int64_t lds,
                                  __nv_bfloat16 *Sh, __nv_bfloat16 *Sl, int64_t ldk, int with_lo) {
-  const int64_t total = (int64_t)l * K;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / K);
-    const int64_t k = e - (int64_t)c * K;
-    // the pair split in FP32, as for A
-    const float f = d2f_rn(S[k * lds + c]);
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
-    Sh[(int64_t)c * ldk + k] = h;
-    if (with_lo) Sl[(int64_t)c * ldk + k] = __float2bfloat16_rn(f - __bfloat162float(h));
+  __shared__ __nv_bfloat16 th[32][34], tl[32][34];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c0 = blockIdx.x * 32;
+  for (int64_t k0 = (int64_t)blockIdx.y * 32; k0 < K; k0 += (int64_t)gridDim.y * 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kr = ty + 8 * q;
+      const int64_t k = k0 + kr;
+      const int c = c0 + tx;
+      // the pair split in FP32, as for A
+      const float f = (k < K && c < l) ? d2f_rn(S[k * lds + c]) : 0.0f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
+      th[kr][tx] = h;
+      tl[kr][tx] = __float2bfloat16_rn(f - __bfloat162float(h));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + ty + 8 * q;
+      const int64_t k = k0 + tx;
+      if (c < l && k < K) {
+        Sh[(int64_t)c * ldk + k] = th[tx][ty + 8 * q];
+        if (with_lo) Sl[(int64_t)c * ldk + k] = tl[tx][ty + 8 * q];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -636,21 +654,23 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   else k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return RQLP_ERR_CUDA;
-  const int64_t total = M * l;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4LL * num_sms());
-  k_sum_parts_f32<<<blocks, 256, 0, st>>>(mx.part, g.S, a.split_stride, M, l, a.ldp, C, l,
-                                          fp8 ? xscale : nullptr, fp8 ? yscale : nullptr);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((M + 7) / 8, 4LL * num_sms()));
+  k_sum_parts_f32<<<blocks, dim3(32, 8), 0, st>>>(mx.part, g.S, a.split_stride, M, l, a.ldp, C,
+                                                  l, fp8 ? xscale : nullptr,
+                                                  fp8 ? yscale : nullptr);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
 int split_skinny(const MixedBufs &mx, bool split, const double *S, int64_t K, int l, int64_t lds,
                  int64_t ldk, cudaStream_t st) {
-  const int64_t total = (int64_t)l * K;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4LL * num_sms());
-  k_split_skinny_t<<<blocks, 256, 0, st>>>(S, K, l, lds, static_cast<__nv_bfloat16 *>(mx.Whi),
-                                           static_cast<__nv_bfloat16 *>(mx.Wlo), ldk,
-                                           split ? 1 : 0);
+  const int64_t ktiles = (K + 31) / 32;
+  const dim3 grid((unsigned)((l + 31) / 32),
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>(ktiles, 8LL * num_sms())));
+  k_split_skinny_t<<<grid, dim3(32, 8), 0, st>>>(S, K, l, lds,
+                                                 static_cast<__nv_bfloat16 *>(mx.Whi),
+                                                 static_cast<__nv_bfloat16 *>(mx.Wlo), ldk,
+                                                 split ? 1 : 0);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
