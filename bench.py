@@ -9,7 +9,7 @@ factorization A ~= Q L P^T through the C ABI with A resident in HBM (A is
 steps).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--prec fp64|bf16x3|bf16|fp8] [--shape M N]
+                       [--prec fp64|bf16x3|bf16|fp8|tf32x3|tf32] [--shape M N]
 --shape runs the same recipe at another size (profiling captures use a
 smaller case); the default is the 8192 x 8192 workload.
 Prints ONE JSON line (rank 0).  With N > 1 (torchrun), each rank factors
@@ -153,7 +153,8 @@ def _class_work(m, n, l, q, d, prec):
     """Algorithmic work per factorization of each timed kernel class.
 
     Products with A: 2q + 2 passes of 2 m n l flops, reading A once per pass
-    (8 bytes per element in FP64, 4 for the BF16 pair, 2 for BF16).
+    (8 bytes per element in FP64 and for the TF32 pair, 4 for the BF16 pair and
+    TF32, 2 for BF16, 1 for E4M3).
     CholeskyQR on an N x l panel, per pass: Gram N l^2 flops (symmetric),
     X R^-1 N l^2 flops (triangular) plus the l^3 / 3 R update, Cholesky and
     triangular inverse l^3 / 3 each; two passes.  CPQR of B: step s updates the
@@ -162,7 +163,8 @@ def _class_work(m, n, l, q, d, prec):
     """
     rows = [m] * q + [n] * q + [m, n] + [l] * max(0, d - 1)
     passes = 2
-    a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0, "fp8": 1.0}[prec] * m * n
+    a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0, "fp8": 1.0, "tf32x3": 8.0,
+               "tf32": 4.0}[prec] * m * n
     prod = ("flops", (2 * q + 2) * 2.0 * m * n * l) if prec == "fp64" else \
         ("bytes", (2 * q + 2) * a_bytes)
     return {
@@ -173,7 +175,8 @@ def _class_work(m, n, l, q, d, prec):
         "cholqr_trinv": ("flops", passes * len(rows) * l ** 3 / 3.0),
         "cholqr_apply": ("flops", passes * sum(r * l * l + l ** 3 / 3.0 for r in rows)),
         "explicit_Q0": ("flops", 4.0 * l ** 3 / 3.0),
-        "prep_A": ("bytes", {"fp64": 0.0, "bf16x3": 16.0, "bf16": 12.0, "fp8": 18.0}[prec] * m * n),
+        "prep_A": ("bytes", {"fp64": 0.0, "bf16x3": 16.0, "bf16": 12.0, "fp8": 18.0,
+                              "tf32x3": 24.0, "tf32": 16.0}[prec] * m * n),
         "assembly": ("flops", 2.0 * (m + n) * l * l),
     }
 
@@ -317,7 +320,9 @@ def run_ours(args):
     A = pr.A
     Om_np = W.omega(pr.n, pr.l, 0)
     Om = torch.from_numpy(Om_np).to(dev)
-    forms = [args.prec] + (["fp64"] if args.prec != "fp64" else [])
+    # the timed form first, then the other reported forms: TF32x3 (the accuracy
+    # between BF16x3 and FP64) and FP64
+    forms = [args.prec] + [f for f in ("tf32x3", "fp64") if f != args.prec]
     stream = torch.cuda.current_stream()
     results = {}
     outs = {}
@@ -492,7 +497,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3", "bf16", "fp8"])
+    ap.add_argument("--prec", default="bf16x3",
+                    choices=["fp64", "bf16x3", "bf16", "fp8", "tf32x3", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--shape", type=int, nargs=2, default=[M, N_], metavar=("M", "N"))

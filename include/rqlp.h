@@ -60,9 +60,15 @@ typedef enum {
   RQLP_PREC_BF16X3 = 1, /* tcgen05 BF16 tensor cores, split A = Ah + Al and W = Wh + Wl,
                            three products Ah Wh + Ah Wl + Al Wh accumulated in FP32 */
   RQLP_PREC_BF16 = 2,   /* tcgen05 BF16 tensor cores, one product, FP32 accumulation */
-  RQLP_PREC_FP8 = 3     /* tcgen05 E4M3 tensor cores, one product, FP32 accumulation; A scaled
+  RQLP_PREC_FP8 = 3,    /* tcgen05 E4M3 tensor cores, one product, FP32 accumulation; A scaled
                            by a power of two per row (per column for the A^T products) and the
                            skinny operand per column, the scales divided out in FP64 */
+  RQLP_PREC_TF32X3 = 4, /* tcgen05 TF32 tensor cores (10-bit significands), split A = Ah + Al
+                           and W = Wh + Wl into TF32 values (round to nearest), three products
+                           Ah Wh + Ah Wl + Al Wh accumulated in FP32: the pairs hold about
+                           2^-22, the tensor cores' accumulation (about 2^-24 per 8 values of
+                           K) dominates at large K; twice the bytes of BF16X3 per pass over A */
+  RQLP_PREC_TF32 = 5    /* tcgen05 TF32 tensor cores, one product, FP32 accumulation */
 } rqlp_prec;
 
 /* Element type of A. */

@@ -215,7 +215,7 @@ bool valid_opts(const rqlp_opts *o) {
   if (o->q < 0 || o->q > 16) return false;
   if (o->pivot2 != 0 && o->pivot2 != 1) return false;
   if (!o->pivot2 && (o->d < 1 || o->d > 64)) return false;
-  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_FP8) return false;
+  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_TF32) return false;
   if (o->block_b < 0) return false;
   if (o->spin_limit_ns < 0) return false;
   return true;
@@ -582,7 +582,7 @@ int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t ld
   if (!A || !W || !Y || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldw < l ||
       ldy < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP8) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_TF32) return RQLP_ERR_INVALID_ARG;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;
@@ -608,7 +608,7 @@ int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   if (!A || !V || !Z || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldv < l ||
       ldz < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP8) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_TF32) return RQLP_ERR_INVALID_ARG;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;

@@ -123,11 +123,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor, both operands K-major, F32 accumulator:
-// kind::f16 with BF16 x BF16 (format 1), or kind::f8f6f4 with E4M3 x E4M3
-// (format 0).
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool fp8 = false) {
-  return (1u << 4) | (fp8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// kind::f16 with BF16 x BF16 (format 1), kind::tf32 with TF32 x TF32
+// (format 2), or kind::f8f6f4 with E4M3 x E4M3 (format 0).  A and B always
+// have the same format.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool fp8 = false,
+                                                  bool tf32 = false) {
+  return (1u << 4) | (fp8 ? 0u : tf32 ? ((2u << 7) | (2u << 10)) : ((1u << 7) | (1u << 10))) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
@@ -136,6 +138,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -183,9 +195,11 @@ struct MmaArgs {
   unsigned long long limit_ns;
 };
 
-// SPLIT: three BF16 products of the hi/lo pairs; FP8: one E4M3 product with
-// 128 values per 128-byte K row (K tile of 128 elements instead of 64).
-template <bool SPLIT, bool FP8 = false>
+// SPLIT: three products of the hi/lo pairs; FP8: one E4M3 product with 128
+// values per 128-byte K row (K tile of 128 elements instead of 64); TF32:
+// FP32 storage read as TF32, 32 values per 128-byte K row.  Every MMA
+// consumes 32 bytes of each K row (16 BF16, 8 TF32 or 32 E4M3 values).
+template <bool SPLIT, bool FP8 = false, bool TF32 = false>
 __global__ void __launch_bounds__(128, 1)
 k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
            const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
@@ -197,7 +211,7 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  constexpr int KT = FP8 ? 128 : kTileK;  // K elements per stage
+  constexpr int KT = FP8 ? 128 : TF32 ? 32 : kTileK;  // K elements per stage
   const uint32_t ybytes = (uint32_t)a.n_pad * 128;
   const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (kXBytes + ybytes);
   const int m_tile = blockIdx.x, split = blockIdx.y;
@@ -251,7 +265,7 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      const uint32_t idesc = instr_desc(kTileM, a.n_pad, FP8);
+      const uint32_t idesc = instr_desc(kTileM, a.n_pad, FP8, TF32);
       for (int i = 0; i < nkb; ++i) {
         const int s = i % a.stages;
         const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
@@ -270,6 +284,14 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
           const uint32_t off = k * 32;
           if (FP8) {
             mma_fp8(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            continue;
+          }
+          if (TF32) {
+            mma_tf32(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            if (SPLIT) {
+              mma_tf32(tmem, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
+              mma_tf32(tmem, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
+            }
             continue;
           }
           mma_bf16(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
@@ -555,6 +577,83 @@ __global__ void k_split_skinny_t(const double *__restrict__ S, int64_t K, int l,
   }
 }
 
+// FP32 -> TF32 (10-bit significand), round to nearest (ties away from zero);
+// the result is an FP32 value whose low 13 significand bits are zero
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// A (m x n, lda) -> TF32 pairs Ah, Al (m x ld1) and A^T pairs Ath, Atl
+// (n x ld2), FP32 storage.  32 x 32 tiles on (32, 8) blocks; the transposed
+// pairs go through shared memory.  h = tf32(f), l = tf32(f - h) with f the
+// FP32 rounding of A: f - h is exact in FP32, and the pair holds about 22
+// significand bits.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_split_a_tf32(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda, float *Ah, float *Al,
+               int64_t ld1, float *Ath, float *Atl, int64_t ld2, int with_lo) {
+  __shared__ float th[32][33], tl[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k;
+    const int64_t i = i0 + r, j = j0 + tx;
+    const float f = (i < m && j < n) ? as_f32(A[i * lda + j]) : 0.0f;
+    const float h = tf32_rn(f), lo = tf32_rn(f - h);
+    if (i < m && j < n) {
+      Ah[i * ld1 + j] = h;
+      if (with_lo) Al[i * ld1 + j] = lo;
+    }
+    th[tx][r] = h;
+    tl[tx][r] = lo;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jr = ty + 8 * k;
+    const int64_t j = j0 + jr, i = i0 + tx;
+    if (j < n && i < m) {
+      Ath[j * ld2 + i] = th[jr][tx];
+      if (with_lo) Atl[j * ld2 + i] = tl[jr][tx];
+    }
+  }
+}
+
+// S (K x l, FP64, lds) -> S^T TF32 pairs (l x ldk, FP32 storage), tiled as
+// k_split_skinny_t
+__global__ void k_split_skinny_tf32_t(const double *__restrict__ S, int64_t K, int l, int64_t lds,
+                                      float *Sh, float *Sl, int64_t ldk, int with_lo) {
+  __shared__ float th[32][33], tl[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c0 = blockIdx.x * 32;
+  for (int64_t k0 = (int64_t)blockIdx.y * 32; k0 < K; k0 += (int64_t)gridDim.y * 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kr = ty + 8 * q;
+      const int64_t k = k0 + kr;
+      const int c = c0 + tx;
+      const float f = (k < K && c < l) ? d2f_rn(S[k * lds + c]) : 0.0f;
+      const float h = tf32_rn(f);
+      th[kr][tx] = h;
+      tl[kr][tx] = tf32_rn(f - h);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + ty + 8 * q;
+      const int64_t k = k0 + tx;
+      if (c < l && k < K) {
+        Sh[(int64_t)c * ldk + k] = th[tx][ty + 8 * q];
+        if (with_lo) Sl[(int64_t)c * ldk + k] = tl[tx][ty + 8 * q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -570,18 +669,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D BF16 tensor map: `rows` x `cols` (cols contiguous, ld elements per
-// row), box of box_rows x 64 with the 128-byte swizzle.
+// 2-D tensor map of BF16, E4M3 (fp8) or FP32 (tf32) elements: `rows` x `cols`
+// (cols contiguous, ld elements per row), box of box_rows x (128 bytes) with
+// the 128-byte swizzle.
 bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld,
-              int box_rows, bool fp8 = false) {
+              int box_rows, bool fp8 = false, bool tf32 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const int es = fp8 ? 1 : 2;
+  const int es = fp8 ? 1 : tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * es};
   cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUtensorMapDataType dt = fp8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = fn(map, dt, 2,
                   const_cast<void *>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -596,14 +699,15 @@ struct GemmPlan {
   size_t smem;
 };
 
-GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false) {
+GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false,
+                   bool tf32 = false) {
   GemmPlan g;
   g.n_pad = (int)round_up(l, 16);
   const size_t ybytes = (size_t)g.n_pad * 128;
   const size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
   g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
   g.smem = g.stages * stage + 1024;
-  const int kt = fp8 ? 128 : kTileK;
+  const int kt = fp8 ? 128 : tf32 ? 32 : kTileK;
   g.nk = (int)((K + kt - 1) / kt);
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   int S = (int)std::max<int64_t>(1, num_sms() / tiles);
@@ -620,15 +724,17 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false) {
 int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const void *Xh,
              const void *Xl, int64_t ldx, const void *Yh, const void *Yl, int64_t ldy, double *C,
              Ctrl *ctrl, int64_t spin_ns, cudaStream_t st, bool fp8 = false,
-             const float *xscale = nullptr, const float *yscale = nullptr) {
-  GemmPlan g = plan_gemm(M, K, l, split, fp8);
+             const float *xscale = nullptr, const float *yscale = nullptr, bool tf32 = false) {
+  GemmPlan g = plan_gemm(M, K, l, split, fp8, tf32);
   if (g.stages < 2) return RQLP_ERR_UNSUPPORTED;
   if ((int64_t)g.S * M * g.n_pad > mx.part_floats) return RQLP_ERR_WORKSPACE;
   CUtensorMap mXh, mXl, mYh, mYl;
-  if (!make_map(&mXh, Xh, M, K, ldx, kTileM, fp8) || !make_map(&mYh, Yh, l, K, ldy, g.n_pad, fp8))
+  if (!make_map(&mXh, Xh, M, K, ldx, kTileM, fp8, tf32) ||
+      !make_map(&mYh, Yh, l, K, ldy, g.n_pad, fp8, tf32))
     return RQLP_ERR_CUDA;
   if (split) {
-    if (!make_map(&mXl, Xl, M, K, ldx, kTileM) || !make_map(&mYl, Yl, l, K, ldy, g.n_pad))
+    if (!make_map(&mXl, Xl, M, K, ldx, kTileM, false, tf32) ||
+        !make_map(&mYl, Yl, l, K, ldy, g.n_pad, false, tf32))
       return RQLP_ERR_CUDA;
   } else {
     mXl = mXh;
@@ -650,6 +756,8 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)g.S);
   if (mixed_init() != RQLP_OK) return RQLP_ERR_CUDA;
   if (fp8) k_mma_bf16<false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else if (tf32 && split) k_mma_bf16<true, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else if (tf32) k_mma_bf16<false, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else if (split) k_mma_bf16<true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   count_launch();
@@ -663,14 +771,19 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
 }
 
 int split_skinny(const MixedBufs &mx, bool split, const double *S, int64_t K, int l, int64_t lds,
-                 int64_t ldk, cudaStream_t st) {
+                 int64_t ldk, cudaStream_t st, bool tf32 = false) {
   const int64_t ktiles = (K + 31) / 32;
   const dim3 grid((unsigned)((l + 31) / 32),
                   (unsigned)std::max<int64_t>(1, std::min<int64_t>(ktiles, 8LL * num_sms())));
-  k_split_skinny_t<<<grid, dim3(32, 8), 0, st>>>(S, K, l, lds,
-                                                 static_cast<__nv_bfloat16 *>(mx.Whi),
-                                                 static_cast<__nv_bfloat16 *>(mx.Wlo), ldk,
-                                                 split ? 1 : 0);
+  if (tf32)
+    k_split_skinny_tf32_t<<<grid, dim3(32, 8), 0, st>>>(S, K, l, lds, static_cast<float *>(mx.Whi),
+                                                        static_cast<float *>(mx.Wlo), ldk,
+                                                        split ? 1 : 0);
+  else
+    k_split_skinny_t<<<grid, dim3(32, 8), 0, st>>>(S, K, l, lds,
+                                                   static_cast<__nv_bfloat16 *>(mx.Whi),
+                                                   static_cast<__nv_bfloat16 *>(mx.Wlo), ldk,
+                                                   split ? 1 : 0);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
@@ -686,11 +799,21 @@ int mixed_init() {
       cudaFuncSetAttribute(k_mma_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess ||
       cudaFuncSetAttribute(k_mma_bf16<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<true, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess)
     return RQLP_ERR_CUDA;
   done = 1;
   return RQLP_OK;
 }
+
+// the forms with a hi/lo pair (three products), and the TF32 forms
+static bool is_split(int prec) { return prec == RQLP_PREC_BF16X3 || prec == RQLP_PREC_TF32X3; }
+static bool is_tf32(int prec) { return prec == RQLP_PREC_TF32X3 || prec == RQLP_PREC_TF32; }
 
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx) {
   mx = MixedBufs{};
@@ -717,22 +840,25 @@ void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx)
     mx.part = a.take<float>((size_t)pf);
     return;
   }
-  const bool split = prec == RQLP_PREC_BF16X3;
+  const bool split = is_split(prec), tf32 = is_tf32(prec);
   mx.m = m;
   mx.n = n;
   mx.l = l;
+  // BF16 (2 bytes) or FP32-stored TF32 (4 bytes); rows of a multiple of 8
+  // elements keep every row 16-byte aligned for the tensor maps
+  const size_t es = tf32 ? 4 : 2;
   const int64_t ld1 = round_up(n, 8), ld2 = round_up(m, 8);
-  mx.Ahi = a.take<__nv_bfloat16>((size_t)m * ld1);
-  mx.Alo = split ? a.take<__nv_bfloat16>((size_t)m * ld1) : nullptr;
-  mx.Athi = a.take<__nv_bfloat16>((size_t)n * ld2);
-  mx.Atlo = split ? a.take<__nv_bfloat16>((size_t)n * ld2) : nullptr;
+  mx.Ahi = a.take<uint8_t>((size_t)m * ld1 * es);
+  mx.Alo = split ? a.take<uint8_t>((size_t)m * ld1 * es) : nullptr;
+  mx.Athi = a.take<uint8_t>((size_t)n * ld2 * es);
+  mx.Atlo = split ? a.take<uint8_t>((size_t)n * ld2 * es) : nullptr;
   const int64_t ldk = round_up(std::max(m, n), 8);
-  mx.Whi = a.take<__nv_bfloat16>((size_t)l * ldk);
-  mx.Wlo = split ? a.take<__nv_bfloat16>((size_t)l * ldk) : nullptr;
+  mx.Whi = a.take<uint8_t>((size_t)l * ldk * es);
+  mx.Wlo = split ? a.take<uint8_t>((size_t)l * ldk * es) : nullptr;
   int64_t pf = 0;
   for (int64_t M : {m, n}) {
     const int64_t K = (M == m) ? n : m;
-    GemmPlan g = plan_gemm(M, K, l, split);
+    GemmPlan g = plan_gemm(M, K, l, split, false, tf32);
     pf = std::max<int64_t>(pf, (int64_t)g.S * M * g.n_pad);
   }
   mx.part_floats = pf;
@@ -766,8 +892,24 @@ int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, i
     count_launch();
     return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
   }
-  const bool split = prec == RQLP_PREC_BF16X3;
+  const bool split = is_split(prec);
   const int64_t ld1 = round_up(n, 8), ld2 = round_up(m, 8);
+  if (is_tf32(prec)) {
+    dim3 g32((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+    auto *Ah = static_cast<float *>(mx.Ahi);
+    auto *Al = static_cast<float *>(mx.Alo);
+    auto *Ath = static_cast<float *>(mx.Athi);
+    auto *Atl = static_cast<float *>(mx.Atlo);
+    if (a_dtype == RQLP_F32)
+      k_split_a_tf32<float><<<g32, dim3(32, 8), 0, st>>>(static_cast<const float *>(A), m, n, lda,
+                                                          Ah, Al, ld1, Ath, Atl, ld2, split ? 1 : 0);
+    else
+      k_split_a_tf32<double><<<g32, dim3(32, 8), 0, st>>>(static_cast<const double *>(A), m, n,
+                                                           lda, Ah, Al, ld1, Ath, Atl, ld2,
+                                                           split ? 1 : 0);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+  }
   dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 31) / 32));
   auto *Ah = static_cast<__nv_bfloat16 *>(mx.Ahi);
   auto *Al = static_cast<__nv_bfloat16 *>(mx.Alo);
@@ -800,12 +942,12 @@ int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *
     return gemm_xyt(mx, false, m, n, l, mx.Ahi, nullptr, round_up(n, 16), mx.Whi, nullptr, ldk, Y,
                     ctrl, spin_ns, st, true, mx.sA, mx.sW);
   }
-  const bool split = prec == RQLP_PREC_BF16X3;
+  const bool split = is_split(prec), tf32 = is_tf32(prec);
   const int64_t ldk = round_up(n, 8);
-  int r = split_skinny(mx, split, W, n, l, ldw, ldk, st);
+  int r = split_skinny(mx, split, W, n, l, ldw, ldk, st, tf32);
   if (r != RQLP_OK) return r;
   return gemm_xyt(mx, split, m, n, l, mx.Ahi, mx.Alo, round_up(n, 8), mx.Whi, mx.Wlo, ldk, Y, ctrl,
-                  spin_ns, st);
+                  spin_ns, st, false, nullptr, nullptr, tf32);
 }
 
 int mixed_tn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *V, int64_t ldv,
@@ -817,12 +959,12 @@ int mixed_tn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *
     return gemm_xyt(mx, false, n, m, l, mx.Athi, nullptr, round_up(m, 16), mx.Whi, nullptr, ldk, Z,
                     ctrl, spin_ns, st, true, mx.sAt, mx.sW);
   }
-  const bool split = prec == RQLP_PREC_BF16X3;
+  const bool split = is_split(prec), tf32 = is_tf32(prec);
   const int64_t ldk = round_up(m, 8);
-  int r = split_skinny(mx, split, V, m, l, ldv, ldk, st);
+  int r = split_skinny(mx, split, V, m, l, ldv, ldk, st, tf32);
   if (r != RQLP_OK) return r;
   return gemm_xyt(mx, split, n, m, l, mx.Athi, mx.Atlo, round_up(m, 8), mx.Whi, mx.Wlo, ldk, Z,
-                  ctrl, spin_ns, st);
+                  ctrl, spin_ns, st, false, nullptr, nullptr, tf32);
 }
 
 }  // namespace rqk

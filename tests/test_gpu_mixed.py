@@ -1,12 +1,17 @@
-"""Mixed-precision (tcgen05 BF16 tensor-core) products and factorizations.
+"""Mixed-precision (tcgen05 tensor-core) products and factorizations.
 
 Tolerances, derived from the arithmetic: BF16 keeps 8 significant bits
 (unit roundoff u = 2^-8); the BF16x3 split represents A and W to about u^2
 and drops only the Al Wl term (about u^2 |A| |W|), and the FP32 accumulation
 over K <= 16384 adds about 1e-6; so the normwise relative error of a BF16x3
-product is held to 1e-4 and that of a plain BF16 product to 2e-2.  For whole
-factorizations the L-values are compared with the FP64 oracle on the same
-Omega at 1e-3 relative for sigma_j / sigma_1 >= 1e-3.
+product is held to 1e-4 and that of a plain BF16 product to 2e-2.  TF32
+keeps 11 (u = 2^-11): the TF32x3 pairs represent A and W to about u^2 =
+2^-22, but the tensor cores' FP32 accumulation then dominates: measured
+2.9e-5 normwise at K = 8192 (4096 per K split, 512 accumulation steps of
+8 values, consistent with a bias of about one 2^-24 per step), so a TF32x3
+product is held to 1e-4 like BF16x3 and a plain TF32 product to 4e-3.  For
+whole factorizations the L-values are compared with the FP64 oracle on the
+same Omega at 1e-3 relative for sigma_j / sigma_1 >= 1e-3.
 """
 import numpy as np
 import pytest
@@ -38,7 +43,8 @@ def _normrel(a, b):
 
 @pytest.mark.parametrize("m,n,l", [(256, 192, 16), (1000, 700, 30), (2048, 1536, 110),
                                    (333, 257, 17), (130, 4100, 200), (8192, 8192, 110)])
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("bf16", 2e-2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("bf16", 2e-2), ("tf32x3", 1e-4),
+                                      ("tf32", 4e-3)])
 def test_mixed_products(R, m, n, l, prec, tol):
     rng = np.random.default_rng(m * 3 + n + l)
     A = rng.standard_normal((m, n))
@@ -58,7 +64,7 @@ def test_mixed_product_fp32_input(R):
     assert _normrel(Y, O.sketch(A.astype(np.float64), Om)) <= 1e-4
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32x3", "tf32"])
 @pytest.mark.parametrize("q,d,pivot2", [(1, 2, False), (0, 1, True), (2, 1, False)])
 def test_mixed_factorization_lvalues(R, prec, q, d, pivot2):
     pr = W.c2(m=2048, n=1536, k=60, p=10, q=q, d=d)
@@ -67,18 +73,18 @@ def test_mixed_factorization_lvalues(R, prec, q, d, pivot2):
     ref = O.rqlp(pr.A, pr.k, pr.p, Om, q=q, d=d, pivot2=pivot2)
     lv = out["Lvalues"].cpu().numpy()
     keep = ref["Lvalues"] >= 1e-3 * ref["Lvalues"].max()
-    if prec == "bf16x3":
+    if prec in ("bf16x3", "tf32x3"):
         # pivots agree with the FP64 oracle, so L-values compare index by index
         assert np.array_equal(out["piv0"].cpu().numpy()[:pr.l], ref["piv0"][:pr.l])
         rel = np.abs(lv - ref["Lvalues"])[keep] / ref["Lvalues"][keep]
         assert rel.max() <= 1e-3, rel.max()
     else:
-        # a 2^-8 perturbation may reorder near-equal pivots; compare what does
-        # not depend on them: the singular values of L (= those of B)
+        # a 2^-8 (2^-11) perturbation may reorder near-equal pivots; compare
+        # what does not depend on them: the singular values of L (= those of B)
         sg = np.linalg.svd(out["L"].cpu().numpy(), compute_uv=False)
         so = np.linalg.svd(ref["L"], compute_uv=False)
         keep = so >= 1e-3 * so[0]
-        assert (np.abs(sg - so)[keep] / so[keep]).max() <= 2e-2
+        assert (np.abs(sg - so)[keep] / so[keep]).max() <= (2e-2 if prec == "bf16" else 5e-3)
     Q = out["Q"].cpu().numpy()
     assert np.abs(Q.T @ Q - np.eye(pr.l)).max() <= 1e-12
 
