@@ -43,3 +43,27 @@ def test_argument_errors_are_synchronous(lib):
     assert code == -1
     code = lib.rqlp_orth(None, 10, 4, 4, None, 4, None, None, 0, None)
     assert code == -1
+
+
+def test_precision_names_match_the_header(lib):
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "rqlp.h")) as f:
+        hdr = f.read()
+    enum = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"RQLP_PREC_([A-Z0-9]+)\s*=\s*(\d+)", hdr)}
+    assert enum == R.PREC
+    # every precision is accepted, the next value is not
+    sizes = {}
+    for name, code in R.PREC.items():
+        o = R.opts(q=1, d=2, pivot2=False, prec=name)
+        sizes[name] = lib.rqlp_workspace_size(4096, 2048, 100, 10, ctypes.byref(o))
+        assert sizes[name] > 0, name
+    o = R.opts(q=1, d=2, pivot2=False)
+    o.prec = max(R.PREC.values()) + 1
+    assert lib.rqlp_workspace_size(4096, 2048, 100, 10, ctypes.byref(o)) == 0
+    # the TF32 pairs take twice the bytes of the BF16 pairs, one TF32 copy
+    # those of the BF16 pair; FP64 keeps no copies of A
+    assert sizes["tf32x3"] > sizes["bf16x3"] > sizes["bf16"] > sizes["fp64"]
+    assert sizes["tf32"] > sizes["bf16"]
