@@ -65,9 +65,11 @@ typedef enum {
                            skinny operand per column, the scales divided out in FP64 */
   RQLP_PREC_TF32X3 = 4, /* tcgen05 TF32 tensor cores (10-bit significands), split A = Ah + Al
                            and W = Wh + Wl into TF32 values (round to nearest), three products
-                           Ah Wh + Ah Wl + Al Wh accumulated in FP32: the pairs hold about
-                           2^-22, the tensor cores' accumulation (about 2^-24 per 8 values of
-                           K) dominates at large K; twice the bytes of BF16X3 per pass over A */
+                           Ah Wh + Ah Wl + Al Wh accumulated in FP32 over four rotating
+                           accumulators: the pairs hold about 2^-22, the tensor cores'
+                           accumulation (about 2^-24 per 8 values of K per accumulator)
+                           dominates at large K (7e-6 normwise at K = 8192, BF16X3 1.5e-5);
+                           twice the bytes of BF16X3 per pass over A */
   RQLP_PREC_TF32 = 5    /* tcgen05 TF32 tensor cores, one product, FP32 accumulation */
 } rqlp_prec;
 

@@ -188,6 +188,8 @@ struct MmaArgs {
   int kb_per;      // K blocks per split
   int stages;
   uint32_t tmem_cols;
+  int nacc;        // accumulators in TMEM, k-block i into number i mod nacc
+  int acc_cols;    // TMEM columns between two accumulators
   float *part;     // [split][M][ldp]
   int64_t split_stride;
   int ldp;
@@ -278,26 +280,30 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
         const uint32_t yh = xh + kXBytes;
         const uint32_t xl = yh + ybytes;
         const uint32_t yl = xl + kXBytes;
+        // the accumulator of this k-block; its first k-block overwrites it
+        const uint32_t td = tmem + (uint32_t)((i % a.nacc) * a.acc_cols);
+        const uint32_t first = (i < a.nacc) ? 1u : 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          // 32 bytes along K inside the swizzled row: 16 BF16 or 32 FP8 values
+          // 32 bytes along K inside the swizzled row: 16 BF16, 8 TF32 or 32 FP8 values
           const uint32_t off = k * 32;
+          const uint32_t accum = (first && k == 0) ? 0u : 1u;
           if (FP8) {
-            mma_fp8(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            mma_fp8(td, smem_desc(xh + off), smem_desc(yh + off), idesc, accum);
             continue;
           }
           if (TF32) {
-            mma_tf32(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            mma_tf32(td, smem_desc(xh + off), smem_desc(yh + off), idesc, accum);
             if (SPLIT) {
-              mma_tf32(tmem, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
-              mma_tf32(tmem, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
+              mma_tf32(td, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
+              mma_tf32(td, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
             }
             continue;
           }
-          mma_bf16(tmem, smem_desc(xh + off), smem_desc(yh + off), idesc, (i > 0 || k > 0) ? 1u : 0u);
+          mma_bf16(td, smem_desc(xh + off), smem_desc(yh + off), idesc, accum);
           if (SPLIT) {
-            mma_bf16(tmem, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
-            mma_bf16(tmem, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
+            mma_bf16(td, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
+            mma_bf16(td, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
           }
         }
         mma_commit(&bar_empty[s]);
@@ -317,13 +323,22 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   } else {
     const int row = m_tile * kTileM + warp * 32 + lane;
     float *out = a.part + (int64_t)split * a.split_stride + (int64_t)row * a.ldp;
+    const int used = min(a.nacc, nkb);  // accumulators that received a k-block
     for (int c0 = 0; c0 < a.n_pad; c0 += 16) {
+      float v[16];
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+      for (int q = 1; q < used; ++q) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * a.acc_cols + c0), r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+      }
       if (row < a.M) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < a.ncols) out[c0 + j] = __uint_as_float(r[j]);
+          if (c0 + j < a.ncols) out[c0 + j] = v[j];
       }
     }
   }
@@ -747,7 +762,13 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   a.nk = g.nk;
   a.kb_per = g.kb_per;
   a.stages = g.stages;
-  a.tmem_cols = g.tmem_cols;
+  // TF32 forms: up to four accumulators (at most 512 TMEM columns), each
+  // taking every fourth k-block, so that every FP32 accumulation chain in
+  // the tensor cores is four times shorter (its error, about 2^-24 per MMA
+  // of 8 values, otherwise bounds the TF32x3 product)
+  a.nacc = tf32 ? (int)std::min<uint32_t>(4u, 512u / g.tmem_cols) : 1;
+  a.acc_cols = (int)g.tmem_cols;
+  a.tmem_cols = g.tmem_cols * (uint32_t)a.nacc;
   a.part = mx.part;
   a.ldp = g.n_pad;
   a.split_stride = M * g.n_pad;
