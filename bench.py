@@ -428,7 +428,7 @@ def run_ours(args):
         Om_h = torch.from_numpy(Om_np).pin_memory()
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=args.prec)
-        outs = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
+        out_keys = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
         slots = [R.rqlp_host(A_h, pr.k, pr.p, Om_h, stream=streams[i], **kw) for i in range(2)]
         hsteps = max(4, min(args.steps, 10))
         torch.cuda.synchronize()
@@ -438,7 +438,7 @@ def run_ours(args):
             if i >= 2:
                 R.host_wait(sl)
             slots[i % 2] = R.rqlp_host_async(A_h, pr.k, pr.p, Om_h, ws=sl["ws"],
-                                             out={k: sl[k] for k in outs},
+                                             out={k: sl[k] for k in out_keys},
                                              stream=streams[i % 2], **kw)
         for sl in slots:
             R.host_wait(sl)
