@@ -251,6 +251,8 @@ def _host_call(entry: str, A_host, k, p, Omega_host, q, d, pivot2, prec, block_b
         raise ValueError("host inputs must be contiguous")
     o = opts(q, d, pivot2, prec, block_b)
     L_ = lib()
+    if stream is None:
+        stream = torch.cuda.current_stream()  # the wait must use the same stream
     dt = _dtype_code(A_host)
     need = L_.rqlp_host_workspace_size(m, n, k, p, ctypes.byref(o), dt)
     if need == 0:
