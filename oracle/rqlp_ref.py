@@ -241,25 +241,20 @@ def rqlp(A: np.ndarray, k: int, p: int, Omega: np.ndarray, q: int = 0, d: int = 
 
 
 # ------------------------------------------------------------------ BRQLP
-def brqlp(A: np.ndarray, k: int, p: int, b: int, Omega: np.ndarray, pivot2: bool = True,
-          d: int = 1):
-    """Block randomized QLP, Algorithm 4.1, taken literally.
-
-    l = k + p = h b.  Per block j: Y_j = A Omega_j; V_j = qr(Y_j);
-    V_j = qr(V_j - sum_{i<j} V_i V_i^T V_j); B_j = V_j^T A(j-1);
-    A(j) = A(j-1) - V_j B_j; [Q_B(j), L_j, P_B(j)] = qlp(B_j);
-    Q_j = V_j Q_B(j), P_j = P_B(j).  Output Q = [Q_j], L = blkdiag(L_j),
-    P = [P_j]; also V = [V_j] and B = [B_j] (stacked).
-    """
+def _brqlp_blocks(A: np.ndarray, b: int, Omega: np.ndarray, nblocks: int, pivot2: bool, d: int,
+                  tol: float = None):
+    """The block loop of Algorithm 4.1: per block j, Y_j = A Omega_j;
+    V_j = qr(Y_j); V_j = qr(V_j - sum_{i<j} V_i V_i^T V_j); B_j = V_j^T A(j-1);
+    A(j) = A(j-1) - V_j B_j; [Q_B(j), L_j, P_B(j)] = qlp(B_j).  With tol, the
+    loop stops after the first block at which ||A||_F^2 - ||B||_F^2 <=
+    tol^2 ||A||_F^2, B the stacked B_j (the residual ||A - V V^T A||_F^2 of
+    eq. 2.1, V = [V_j] orthonormal)."""
     A = np.asarray(A, dtype=np.float64)
-    m, n = A.shape
-    l = k + p
-    if l % b != 0:
-        raise ValueError("block size must divide k + p")
-    h = l // b
     Aj = A.copy()
+    a2 = float(np.sum(A * A))
+    b2 = 0.0
     Vs, Bs, Qs, Ls, Ps = [], [], [], [], []
-    for j in range(h):
+    for j in range(nblocks):
         Om = np.asarray(Omega, dtype=np.float64)[:, j * b:(j + 1) * b]
         Yj = sketch(A, Om)
         Vj = orth(Yj)
@@ -274,15 +269,49 @@ def brqlp(A: np.ndarray, k: int, p: int, b: int, Omega: np.ndarray, pivot2: bool
         Qs.append(Vj @ f["QB"])
         Ls.append(f["T"])
         Ps.append(f["PB"])
+        b2 += float(np.sum(Bj * Bj))
+        if tol is not None and a2 - b2 <= tol * tol * a2:
+            break
+    h = len(Vs)
+    l = h * b
     L = np.zeros((l, l))
     for j in range(h):
         L[j * b:(j + 1) * b, j * b:(j + 1) * b] = Ls[j]
     return dict(Q=np.concatenate(Qs, axis=1), L=L, P=np.concatenate(Ps, axis=1),
                 Lvalues=np.diag(L).copy(), V=np.concatenate(Vs, axis=1),
-                B=np.concatenate(Bs, axis=0), Lblocks=Ls)
+                B=np.concatenate(Bs, axis=0), Lblocks=Ls, l=l)
 
 
-# ----------------------------------------------------------------- metrics
+def brqlp(A: np.ndarray, k: int, p: int, b: int, Omega: np.ndarray, pivot2: bool = True,
+          d: int = 1):
+    """Block randomized QLP, Algorithm 4.1, taken literally.
+
+    l = k + p = h b.  Per block j: Y_j = A Omega_j; V_j = qr(Y_j);
+    V_j = qr(V_j - sum_{i<j} V_i V_i^T V_j); B_j = V_j^T A(j-1);
+    A(j) = A(j-1) - V_j B_j; [Q_B(j), L_j, P_B(j)] = qlp(B_j);
+    Q_j = V_j Q_B(j), P_j = P_B(j).  Output Q = [Q_j], L = blkdiag(L_j),
+    P = [P_j]; also V = [V_j] and B = [B_j] (stacked).
+    """
+    l = k + p
+    if l % b != 0:
+        raise ValueError("block size must divide k + p")
+    return _brqlp_blocks(A, b, Omega, l // b, pivot2, d)
+
+
+def brqlp_tol(A: np.ndarray, b: int, l_max: int, tol: float, Omega: np.ndarray,
+              pivot2: bool = True, d: int = 1):
+    """Fixed-accuracy BRQLP: the blocks of Algorithm 4.1 are added until the
+    relative residual ||A - V V^T A||_F / ||A||_F is at most tol (evaluated
+    through eq. 2.1 as ||A||_F^2 - ||B||_F^2), or until l_max = h b columns
+    (the blocked scheme's use named at the end of the paper).  Omega is
+    n x l_max; returns brqlp's dict for the l = j b columns used, with "l"."""
+    if l_max % b != 0:
+        raise ValueError("block size must divide l_max")
+    if tol < 0:
+        raise ValueError("tol must be >= 0")
+    return _brqlp_blocks(A, b, Omega, l_max // b, pivot2, d, tol=tol)
+
+
 def lvalue_err(sigma: np.ndarray, Lvalues: np.ndarray, k: int) -> float:
     """err = max_{j<=k} |sigma_j(A) - |L_jj|| (Section 5 error measure)."""
     return float(np.max(np.abs(np.asarray(sigma)[:k] - np.abs(np.asarray(Lvalues)[:k]))))

@@ -244,6 +244,48 @@ def test_brqlp_matches_unblocked_projector():
     assert np.abs(blk["L"] * (1 - mask)).max() == 0.0
 
 
+def test_brqlp_tol_meets_the_tolerance_with_the_fewest_blocks():
+    # the stopping rule evaluated directly, without eq. 2.1: the returned
+    # basis meets ||A - V V^T A||_F <= tol ||A||_F and one block fewer does not
+    A, _ = _decaying(90, 60, 31, decay=0.85)
+    b, l_max = 4, 40
+    Om = _rand((60, l_max), 32)
+    na = np.linalg.norm(A)
+    for tol in (0.3, 0.1, 0.03, 1e-2):
+        out = R.brqlp_tol(A, b, l_max, tol, Om)
+        l = out["l"]
+        V = out["V"]
+        assert V.shape[1] == l and l % b == 0 and b <= l <= l_max
+        assert np.linalg.norm(A - V @ (V.T @ A)) <= tol * na * (1 + 1e-12)
+        if l > b:
+            Vs = V[:, :l - b]
+            assert np.linalg.norm(A - Vs @ (Vs.T @ A)) > tol * na
+        # eq. 2.1 itself: ||A - V V^T A||_F^2 = ||A||_F^2 - ||B||_F^2
+        assert np.isclose(np.linalg.norm(A - V @ (V.T @ A)) ** 2,
+                          na ** 2 - np.linalg.norm(out["B"]) ** 2, rtol=1e-9, atol=1e-12 * na ** 2)
+
+
+def test_brqlp_tol_zero_tolerance_is_the_full_brqlp():
+    A, _ = _decaying(70, 50, 33)
+    b, l_max = 5, 20
+    Om = _rand((50, l_max), 34)
+    full = R.brqlp(A, l_max, 0, b, Om)
+    out = R.brqlp_tol(A, b, l_max, 0.0, Om)
+    assert out["l"] == l_max
+    for key in ("Q", "L", "P", "V", "B"):
+        assert np.array_equal(out[key], full[key]), key
+
+
+def test_brqlp_tol_finds_an_exact_rank():
+    # rank 12 = 3 blocks of 4: three blocks capture A to rounding, two cannot
+    m, n, r, b = 60, 45, 12, 4
+    A = _rand((m, r), 35) @ _rand((r, n), 36)
+    Om = _rand((n, 24), 37)
+    out = R.brqlp_tol(A, b, 24, 1e-10, Om)
+    assert out["l"] == r
+    assert np.linalg.norm(A - out["Q"] @ out["L"] @ out["P"].T) <= 1e-12 * np.linalg.norm(A)
+
+
 @pytest.mark.slow
 def test_paper_tables_1_2_order_of_magnitude():
     """Section 5, Tables 1-2 (n = 2000): RQLP matches deterministic QLP and inner QRs help.
