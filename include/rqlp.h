@@ -122,6 +122,29 @@ int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int3
          double *Lvalues, int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
          rqlp_stream_t stream);
 
+/*
+ * Fixed-accuracy BRQLP: the blocks of Algorithm 4.1 (b columns each) are
+ * added until the relative residual ||A - V V^T A||_F / ||A||_F is at most
+ * `tol`, evaluated through eq. 2.1 as ||A||_F^2 - ||B||_F^2 with B = V^T A
+ * the stacked B_j, or until l_max columns (the blocked scheme's use for an
+ * unknown rank, which the paper's conclusion names).  Omega is n x l_max
+ * (ldo >= l_max); the workspace is rqlp_workspace_size(m, n, l_max, 0, opts)
+ * with opts->block_b = b; opts->q must be 0 (no power steps in Algorithm
+ * 4.1).  *l_used gets the number of columns used, a multiple of b; Q (m x
+ * l_max), P (n x l_max) and L (l_max x l_max, zero outside the used blocks)
+ * hold the factorization in their first *l_used columns (of L: its leading
+ * *l_used x *l_used block), Lvalues (may be NULL) its first *l_used
+ * L-values, piv0 (n) the first block's column pivots and piv1 (l_max) the
+ * per-block second-stage pivots.  The stopping test is taken on the host
+ * after every block, so this call synchronizes `stream` once per block and
+ * returns the final status (argument, CUDA or device status).
+ */
+int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t b,
+                   int32_t l_max, double tol, const double *Omega, int64_t ldo,
+                   const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+                   int32_t *piv0, int32_t *piv1, int32_t *l_used, void *ws, size_t ws_bytes,
+                   rqlp_stream_t stream);
+
 /* Synchronizes `stream` and returns the device status word of the last call
  * that used `ws` (RQLP_OK, a warning or an error). */
 int rqlp_read_status(const void *ws, rqlp_stream_t stream);

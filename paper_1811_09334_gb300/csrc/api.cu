@@ -381,33 +381,86 @@ __global__ void k_zero(double *p, int64_t n) {
 // L = blkdiag(L_j).  The deflation A(j) = A(j-1) - V_j B_j is not formed:
 // B_j = V_j^T A(j-1) = V_j^T A because V_j is orthogonal to V_<j (Section 4),
 // which saves one pass over A per block.
+// Block j of Algorithm 4.1 (l columns in all, blocks of o.block_b): Y_j =
+// A Omega_j, V_j = qr(Y_j), re-orthonormalized against V_<j, Z = A^T V_j =
+// B_j^T (B_j = V_j^T A: V_j is orthogonal to V_<j, so the deflation of
+// A(j - 1) changes nothing), and the QLP of B_j into the j-th block columns of
+// Q and P and the j-th diagonal block of L.  Leaves B_j^T in P.Z (n x b).
+int brqlp_block(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64_t m,
+                int64_t n, int64_t lda, int l, const double *Omega, int64_t ldo, double *Q,
+                double *L, double *Pout, int32_t *piv0, int32_t *piv1, int j, int &site,
+                cudaStream_t st) {
+  const int b = o.block_b;
+  double *Vj = P.V + (size_t)j * b;  // column block of V (m x l, ld l)
+  RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega + (size_t)j * b, ldo, b, P.Y, st));
+  RET(orth(P.Y, m, b, b, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
+  if (j > 0) {
+    const int jb = j * b;
+    // C = V_<j^T V_j (jb x b), then V_j -= V_<j C
+    CK(gemm_f64(true, RQLP_F64, P.V, l, Vj, l, P.sm1, b, jb, b, m, 1.0, 0.0, P.ob.part, nullptr,
+                nullptr, st));
+    CK(gemm_f64(false, RQLP_F64, P.V, l, P.sm1, b, Vj, l, m, b, jb, -1.0, 1.0, P.ob.part,
+                nullptr, nullptr, st));
+    RET(orth(Vj, m, b, l, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
+  }
+  RET(prod_tn(P, o, A, a_dtype, m, n, lda, Vj, l, b, P.Z, st));
+  int32_t *p0 = (j == 0) ? piv0 : P.piv0;
+  RET(qlp_stage(P, o, m, n, b, Vj, l, P.Z, Q + (size_t)j * b, L + (size_t)j * b * l + j * b,
+                Pout + (size_t)j * b, l, p0, piv1 + (size_t)j * b, site, st));
+  site += o.d + 1;
+  return RQLP_OK;
+}
+
 int run_brqlp(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, int64_t m, int64_t n,
               int64_t lda, int l, const double *Omega, int64_t ldo, double *Q, double *L,
               double *Pout, int32_t *piv0, int32_t *piv1, cudaStream_t st) {
-  const int b = o.block_b, h = l / b;
+  const int h = l / o.block_b;
   k_zero<<<(int)std::min<int64_t>(((int64_t)l * l + 255) / 256, 1024), 256, 0, st>>>(L, (int64_t)l * l);
   count_launch();
   CK(cudaGetLastError());
   int site = 0;
-  for (int j = 0; j < h; ++j) {
-    double *Vj = P.V + (size_t)j * b;  // column block of V (m x l, ld l)
-    RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega + (size_t)j * b, ldo, b, P.Y, st));
-    RET(orth(P.Y, m, b, b, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
-    if (j > 0) {
-      const int jb = j * b;
-      // C = V_<j^T V_j (jb x b), then V_j -= V_<j C
-      CK(gemm_f64(true, RQLP_F64, P.V, l, Vj, l, P.sm1, b, jb, b, m, 1.0, 0.0, P.ob.part, nullptr,
-                  nullptr, st));
-      CK(gemm_f64(false, RQLP_F64, P.V, l, P.sm1, b, Vj, l, m, b, jb, -1.0, 1.0, P.ob.part,
-                  nullptr, nullptr, st));
-      RET(orth(Vj, m, b, l, Vj, l, nullptr, P.ob, P.ctrl, site++, st));
+  for (int j = 0; j < h; ++j)
+    RET(brqlp_block(P, o, A, a_dtype, m, n, lda, l, Omega, ldo, Q, L, Pout, piv0, piv1, j, site,
+                    st));
+  return RQLP_OK;
+}
+
+// Per-CTA partial sums of squares of an r x c row-major matrix (ld), in
+// FP64 and in a fixed order (1-D blocks of 256: eight rows at a time, lanes
+// along a row, then the CTA sum), so that the total is reproducible.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sumsq(const T *__restrict__ X, int64_t r, int64_t c,
+                                               int64_t ld, double *__restrict__ part) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + rg; i < r; i += (int64_t)gridDim.x * 8)
+    for (int64_t j = lane; j < c; j += 32) {
+      const double v = (double)X[i * ld + j];
+      s = fma(v, v, s);
     }
-    RET(prod_tn(P, o, A, a_dtype, m, n, lda, Vj, l, b, P.Z, st));
-    int32_t *p0 = (j == 0) ? piv0 : P.piv0;
-    RET(qlp_stage(P, o, m, n, b, Vj, l, P.Z, Q + (size_t)j * b, L + (size_t)j * b * l + j * b,
-                  Pout + (size_t)j * b, l, p0, piv1 + (size_t)j * b, site, st));
-    site += o.d + 1;
-  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// ||X||_F^2 of an r x c matrix (FP64 or FP32), summed on the host from the
+// CTA partials in index order; synchronizes the stream.  `part` holds at
+// least 4 x SMs doubles.
+int sum_squares(const void *X, int dtype, int64_t r, int64_t c, int64_t ld, double *part,
+                cudaStream_t st, double *out) {
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>((r + 7) / 8, 4LL * num_sms()));
+  if (dtype == RQLP_F32)
+    k_sumsq<float><<<G, 256, 0, st>>>(static_cast<const float *>(X), r, c, ld, part);
+  else
+    k_sumsq<double><<<G, 256, 0, st>>>(static_cast<const double *>(X), r, c, ld, part);
+  count_launch();
+  CK(cudaGetLastError());
+  std::vector<double> h((size_t)G);
+  CK(cudaMemcpyAsync(h.data(), part, (size_t)G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double s = 0.0;
+  for (int i = 0; i < G; ++i) s += h[(size_t)i];
+  *out = s;
   return RQLP_OK;
 }
 
@@ -494,6 +547,53 @@ int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int3
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
   return run_rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, *opts, Q, L, P, Lvalues, piv0, piv1, ws,
                   ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t b,
+                   int32_t l_max, double tol, const double *Omega, int64_t ldo,
+                   const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+                   int32_t *piv0, int32_t *piv1, int32_t *l_used, void *ws, size_t ws_bytes,
+                   rqlp_stream_t stream) {
+  if (!valid_dims(m, n, l_max, 0) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
+  if (!A || !Omega || !Q || !L || !P || !l_used || !ws) return RQLP_ERR_INVALID_ARG;
+  if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
+  if (b < 1 || l_max % b != 0 || !(tol >= 0.0) || lda < n || ldo < l_max)
+    return RQLP_ERR_INVALID_ARG;
+  if (opts->q > 0) return RQLP_ERR_UNSUPPORTED;  // Algorithm 4.1 has no power steps
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  *l_used = 0;
+  rqlp_opts o = *opts;
+  o.block_b = b;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan W = carve(ws, m, n, l_max, o);
+  if (W.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
+  CK(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), st));
+  int32_t *pv0 = piv0 ? piv0 : W.piv0;
+  int32_t *pv1 = piv1 ? piv1 : W.piv1;
+  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(W.mx, o.prec, A, a_dtype, m, n, lda, st));
+  const int64_t ll = (int64_t)l_max * l_max;
+  k_zero<<<(int)std::min<int64_t>((ll + 255) / 256, 1024), 256, 0, st>>>(L, ll);
+  count_launch();
+  CK(cudaGetLastError());
+  // the stopping rule of eq. 2.1: ||A - V V^T A||_F^2 = ||A||_F^2 - ||B||_F^2
+  double a2 = 0.0, b2 = 0.0;
+  RET(sum_squares(A, a_dtype, m, n, lda, W.ob.part, st, &a2));
+  int used = 0, site = 0;
+  for (int j = 0; j < l_max / b; ++j) {
+    RET(brqlp_block(W, o, A, a_dtype, m, n, lda, l_max, Omega, ldo, Q, L, P, pv0, pv1, j, site,
+                    st));
+    double z2 = 0.0;
+    RET(sum_squares(W.Z, RQLP_F64, n, b, b, W.ob.part, st, &z2));  // ||B_j||_F^2 (synchronizes)
+    int status = 0;
+    CK(cudaMemcpy(&status, W.ctrl, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status < 0) return status;
+    b2 += z2;
+    used = j + 1;
+    if (a2 - b2 <= tol * tol * a2) break;
+  }
+  *l_used = used * b;
+  if (Lvalues) CK(diag_of(L, used * b, l_max, Lvalues, st));
+  return rqlp_read_status(ws, stream);
 }
 
 int rqlp_read_status(const void *ws, rqlp_stream_t stream) {

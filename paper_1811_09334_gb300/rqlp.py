@@ -60,6 +60,10 @@ _SIGS = {
     "rqlp": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
                       ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_read_status": (_c_i32, [_c_p, _c_p]),
+    "rqlp_brqlp_tol": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32,
+                                ctypes.c_double, _c_p, _c_i64, ctypes.POINTER(Opts), _c_p, _c_p,
+                                _c_p, _c_p, _c_p, _c_p, ctypes.POINTER(ctypes.c_int32), _c_p,
+                                _c_sz, _c_p]),
     "rqlp_host_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts),
                                          _c_i32]),
     "rqlp_host": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i32, _c_i32, _c_p,
@@ -240,6 +244,44 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
         _check(status, "rqlp (device status)")
         res["status"] = status
     return res
+
+
+def brqlp_tol(A, b: int, l_max: int, tol: float, Omega, d: int = 1, pivot2: bool = True,
+              prec: str = "fp64", ws=None, stream=None) -> dict:
+    """Fixed-accuracy BRQLP: blocks of b columns (Algorithm 4.1) until
+    ||A - V V^T A||_F <= tol ||A||_F (eq. 2.1) or l_max columns.  Omega is
+    (n, l_max) float64.  Returns Q, L, P, Lvalues, piv1 cut to the l columns
+    used, piv0, l and status.  Synchronizes the stream once per block."""
+    torch = _torch()
+    m, n = A.shape
+    lda = _row_major(A, "A")
+    ldo = _row_major(Omega, "Omega")
+    if Omega.dtype != torch.float64 or tuple(Omega.shape) != (n, l_max):
+        raise ValueError("Omega must be float64 of shape (n, l_max)")
+    o = opts(0, d, pivot2, prec, b)
+    L_ = lib()
+    need = L_.rqlp_workspace_size(m, n, l_max, 0, ctypes.byref(o))
+    if need == 0:
+        raise RqlpError(-1, "rqlp_workspace_size")
+    dev = A.device
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    out = dict(Q=torch.empty((m, l_max), dtype=torch.float64, device=dev),
+               L=torch.empty((l_max, l_max), dtype=torch.float64, device=dev),
+               P=torch.empty((n, l_max), dtype=torch.float64, device=dev),
+               Lvalues=torch.zeros((l_max,), dtype=torch.float64, device=dev),
+               piv0=torch.empty((n,), dtype=torch.int32, device=dev),
+               piv1=torch.empty((l_max,), dtype=torch.int32, device=dev))
+    used = ctypes.c_int32(0)
+    code = L_.rqlp_brqlp_tol(_ptr(A), _dtype_code(A), m, n, lda, b, l_max, float(tol), _ptr(Omega),
+                             ldo, ctypes.byref(o), _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]),
+                             _ptr(out["Lvalues"]), _ptr(out["piv0"]), _ptr(out["piv1"]),
+                             ctypes.byref(used), _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "rqlp_brqlp_tol")
+    l = int(used.value)
+    return dict(Q=out["Q"][:, :l], L=out["L"][:l, :l], P=out["P"][:, :l],
+                Lvalues=out["Lvalues"][:l], piv0=out["piv0"], piv1=out["piv1"][:l], l=l,
+                status=code, ws=ws)
 
 
 def _host_call(entry: str, A_host, k, p, Omega_host, q, d, pivot2, prec, block_b, ws, out,

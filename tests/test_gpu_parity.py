@@ -264,6 +264,67 @@ def test_brqlp_large_blocks_bf16x3(R):
     assert np.max(np.abs(lv - ref["Lvalues"]) / ref["Lvalues"]) <= 1e-3
 
 
+def _block_residuals(A, B, b):
+    """||A - V V^T A||_F / ||A||_F after each block, from eq. 2.1 (oracle B)."""
+    a2 = float(np.sum(A * A))
+    return [np.sqrt(max(a2 - float(np.sum(B[:(j + 1) * b] ** 2)), 0.0) / a2)
+            for j in range(B.shape[0] // b)]
+
+
+@pytest.mark.parametrize("tol,l_expect", [(0.03, 16), (5e-3, 40), (1e-3, 64)])
+def test_brqlp_tol_parity(R, tol, l_expect):
+    """Fixed-accuracy BRQLP (blocks of 8, at most 64 columns) on the
+    900 x 600 sigma_j = j^-2 matrix: the same number of blocks as the oracle
+    and the same factorization; every tolerance is at least 10 % away from
+    the residual after any block, so the stopping block is unambiguous."""
+    pr = W.c1(m=900, n=600, k=20, p=10)
+    b, l_max = 8, 64
+    Om = W.omega(pr.n, l_max, 5)
+    full = O.brqlp_tol(pr.A, b, l_max, 0.0, Om)
+    assert all(abs(r - tol) > 0.1 * tol for r in _block_residuals(pr.A, full["B"], b))
+    ref = O.brqlp_tol(pr.A, b, l_max, tol, Om)
+    assert ref["l"] == l_expect
+    out = R.brqlp_tol(_t(pr.A), b, l_max, tol, _t(Om))
+    assert out["l"] == ref["l"]
+    Lg = out["L"].cpu().numpy()
+    assert _relmax(Lg, ref["L"]) <= 1e-10
+    lv = out["Lvalues"].cpu().numpy()
+    assert np.max(np.abs(lv - ref["Lvalues"]) / np.abs(ref["Lvalues"])) <= 1e-10
+    assert _relmax(out["Q"], ref["Q"]) <= 1e-9
+    assert _relmax(out["P"], ref["P"]) <= 1e-9
+    # below l_max the tolerance holds for the returned factors, computed directly
+    if out["l"] < l_max:
+        Q, P = out["Q"].cpu().numpy(), out["P"].cpu().numpy()
+        assert np.linalg.norm(pr.A - Q @ Lg @ P.T) <= tol * np.linalg.norm(pr.A)
+
+
+def test_brqlp_tol_zero_is_the_fixed_block_count(R):
+    pr = W.c1(m=900, n=600, k=20, p=10)
+    b, l_max = 8, 32
+    Om = _t(W.omega(pr.n, l_max, 5))
+    A = _t(pr.A)
+    out = R.brqlp_tol(A, b, l_max, 0.0, Om)
+    fix = R.rqlp(A, l_max, 0, Om, block_b=b)
+    assert out["l"] == l_max
+    for key in ("Q", "L", "P", "Lvalues", "piv0", "piv1"):
+        assert torch.equal(out[key], fix[key]), key
+
+
+def test_brqlp_tol_bf16x3(R):
+    # the mixed form's products carry ~1e-5 relative errors, so ||A||^2 -
+    # ||B||^2 is known to about 1e-5 ||A||^2: tolerances well above
+    # sqrt(1e-5) ~ 3e-3 keep the stopping block unambiguous
+    pr = W.c1(m=900, n=600, k=20, p=10)
+    b, l_max = 8, 64
+    Om = W.omega(pr.n, l_max, 5)
+    ref = O.brqlp_tol(pr.A, b, l_max, 0.03, Om)
+    out = R.brqlp_tol(_t(pr.A), b, l_max, 0.03, _t(Om), prec="bf16x3")
+    assert out["l"] == ref["l"] == 16
+    lv = out["Lvalues"].cpu().numpy()
+    keep = ref["Lvalues"] >= 1e-3 * ref["Lvalues"].max()
+    assert np.max(np.abs(lv - ref["Lvalues"])[keep] / ref["Lvalues"][keep]) <= 1e-3
+
+
 # ------------------------------------------------------------------ device helpers
 def test_device_arithmetic_helpers_match_cuda(R):
     # integer-pipe FP64/FP32 roundings bit-exact, FP32-seeded reciprocal and
