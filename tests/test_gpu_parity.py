@@ -288,8 +288,12 @@ def test_brqlp_tol_parity(R, tol, l_expect):
     assert out["l"] == ref["l"]
     Lg = out["L"].cpu().numpy()
     assert _relmax(Lg, ref["L"]) <= 1e-10
+    # L-values normwise (relative to the largest): the GPU forms B_j = V_j^T A
+    # where the oracle deflates A(j-1) literally (reading A8), so the
+    # smallest L-values of the deeper blocks (3.5e-4 of the largest at
+    # l = 64) differ by rounding of order 1e-14 absolute
     lv = out["Lvalues"].cpu().numpy()
-    assert np.max(np.abs(lv - ref["Lvalues"]) / np.abs(ref["Lvalues"])) <= 1e-10
+    assert np.max(np.abs(lv - ref["Lvalues"])) <= 1e-10 * np.max(np.abs(ref["Lvalues"]))
     assert _relmax(out["Q"], ref["Q"]) <= 1e-9
     assert _relmax(out["P"], ref["P"]) <= 1e-9
     # below l_max the tolerance holds for the returned factors, computed directly
