@@ -12,12 +12,14 @@
  * - Matrices are dense, row-major, with an explicit leading dimension
  *   (ld >= number of columns), FP64 unless stated.
  * - l = k + p is the sketch width; 1 <= l <= min(m, n) and l <= 256.
- * - All pointers are DEVICE pointers except in rqlp_host().  The caller
- *   owns every buffer, including the workspace; the library never
- *   allocates device memory.  Buffers must not overlap unless stated.
+ * - All pointers are DEVICE pointers except in rqlp_host() and
+ *   rqlp_host_async().  The caller owns every buffer, including the
+ *   workspace; the library never allocates device memory.  Buffers must not
+ *   overlap unless stated.
  * - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
- *   the legacy default stream).  Argument errors are returned at once and
- *   enqueue nothing.  Errors found on the device (non-finite data, a
+ *   the legacy default stream); rqlp_host(), rqlp_read_status() and
+ *   rqlp_brqlp_tol() synchronize it.  Argument errors are returned at once
+ *   and enqueue nothing.  Errors found on the device (non-finite data, a
  *   device-side wait that ran out of time) are written to a status word in
  *   the workspace; read it with rqlp_read_status() after the work is done.
  * - Every QR inside returns R with a non-negative diagonal, so Q, L and P
