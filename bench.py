@@ -181,6 +181,41 @@ def _class_work(m, n, l, q, d, prec):
     }
 
 
+# tensor-core rate of each mixed form relative to the measured BF16 rate
+# (NVIDIA's nominal dense ratios: TF32 1.1 and FP8 4.5 against BF16 2.25 PFLOP/s)
+_TC_RATIO = {"bf16x3": 1.0, "bf16": 1.0, "tf32x3": 0.5, "tf32": 0.5, "fp8": 2.0}
+_TC_PRODUCTS = {"bf16x3": 3, "bf16": 1, "tf32x3": 3, "tf32": 1, "fp8": 1}
+
+
+def _stage_roofline(form, m, n, l, q, d, prof, steps, peaks):
+    """Per kernel class of one form: achieved rate from its event time and the
+    algorithmic work of _class_work, against the measured HBM copy rate
+    (bytes) or the nominal FP64 rate (flops).  The products with A of a
+    mixed form also get their tensor-core rate (the products the tensor
+    cores execute: three per pass for the split forms) against the measured
+    sustained BF16 rate scaled to the form's dtype."""
+    work = _class_work(m, n, l, q, d, form)
+    out = {}
+    for cls, (ms, _cnt) in prof.items():
+        if ms <= 0 or cls not in work:
+            continue
+        kind, amount = work[cls]
+        per_s = amount * steps / (ms / 1e3)
+        if kind == "bytes":
+            e = {"bound": "hbm", "achieved_gbs": per_s / 1e9,
+                 "frac": per_s / 1e9 / peaks["hbm_gbs"]}
+        else:
+            e = {"bound": "alu", "achieved_tflops": per_s / 1e12,
+                 "frac": per_s / 1e12 / FP64_NOMINAL_TFLOPS}
+        if cls == "products_with_A" and form in _TC_RATIO:
+            tc = _TC_PRODUCTS[form] * (2 * q + 2) * 2.0 * m * n * l * steps / (ms / 1e3) / 1e12
+            peak = peaks["bf16_tflops_sustained"] * _TC_RATIO[form]
+            e["tensor_tflops"] = tc
+            e["tensor_frac"] = tc / peak
+        out[cls] = e
+    return out
+
+
 def _oracle_run(A_np, Om_np, prec_forms_out, budget_s=25.0):
     """Times the FP64 CPU oracle on the same factorization (bounded sample)."""
     from oracle import rqlp_ref as O
@@ -378,6 +413,7 @@ def run_ours(args):
     main = results[args.prec]
     value = world * main["steps"] / (main["ms_total"] / 1e3)
     flops = _sketch_flops(pr.m, pr.n, pr.l, Q_POW)
+    peaks, peak_src = _peaks()
     forms_out = {}
     for form, r in results.items():
         prod_ms, prod_cnt = r["prof"]["products_with_A"]
@@ -387,11 +423,12 @@ def run_ours(args):
             "sketch_tflops": flops * r["steps"] / (prod_ms / 1e3) / 1e12 if prod_ms > 0 else None,
             "stage_ms_per_step": {k: v[0] / r["steps"] for k, v in r["prof"].items()},
             "stage_launches_per_step": {k: v[1] / r["steps"] for k, v in r["prof"].items()},
+            "stage_roofline": _stage_roofline(form, pr.m, pr.n, pr.l, Q_POW, D_INNER, r["prof"],
+                                              r["steps"], peaks),
             "status": r["status"],
         }
 
     # dominant kernel class of the headline form and its roofline
-    peaks, peak_src = _peaks()
     prof = main["prof"]
     dom = max(prof, key=lambda c: prof[c][0])
     dom_ms, dom_cnt = prof[dom]

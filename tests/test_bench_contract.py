@@ -24,3 +24,34 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["m"] == 300 and d["config"]["n"] == 240
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_stage_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1600.0}
+    m = n = 8192
+    l, q, d = 110, 1, 2
+    work = bench._class_work(m, n, l, q, d, "bf16x3")
+    # one step, each class taking 1 ms
+    prof = {k: (1.0, 1) for k in work}
+    sr = bench._stage_roofline("bf16x3", m, n, l, q, d, prof, 1, peaks)
+    pa = sr["products_with_A"]
+    # 4 passes over the BF16 pair (4 bytes per element) in 1 ms
+    assert pa["bound"] == "hbm"
+    assert abs(pa["achieved_gbs"] - 4 * 4.0 * m * n / 1e-3 / 1e9) < 1e-6
+    assert abs(pa["frac"] - pa["achieved_gbs"] / 6000.0) < 1e-12
+    # three tensor-core products per pass, 2 m n l flops each
+    assert abs(pa["tensor_tflops"] - 3 * 4 * 2.0 * m * n * l / 1e-3 / 1e12) < 1e-6
+    assert abs(pa["tensor_frac"] - pa["tensor_tflops"] / 1600.0) < 1e-12
+    cp = sr["cpqr_of_B"]
+    assert cp["bound"] == "alu"
+    assert abs(cp["achieved_tflops"] - 2.0 * n * l * (l + 1) / 1e-3 / 1e12) < 1e-9
+    # TF32x3: twice the bytes, half the tensor rate
+    sr32 = bench._stage_roofline("tf32x3", m, n, l, q, d, prof, 1, peaks)
+    assert abs(sr32["products_with_A"]["achieved_gbs"] - 2 * pa["achieved_gbs"]) < 1e-6
+    assert abs(sr32["products_with_A"]["tensor_frac"] - 2 * pa["tensor_frac"]) < 1e-12
+    # the FP64 form's products are FP64 flops, without a tensor-core entry
+    sr64 = bench._stage_roofline("fp64", m, n, l, q, d, prof, 1, peaks)
+    assert sr64["products_with_A"]["bound"] == "alu"
+    assert "tensor_frac" not in sr64["products_with_A"]
