@@ -52,7 +52,7 @@ typedef enum {
   RQLP_ERR_TIMEOUT = -4,         /* a device-side wait gave up (see spin_limit_ns) */
   RQLP_ERR_CUDA = -5,            /* a CUDA runtime call failed */
   RQLP_ERR_WORKSPACE = -6,       /* workspace too small or misaligned (needs 256-byte alignment) */
-  RQLP_ERR_UNSUPPORTED = -7      /* option not available in this build */
+  RQLP_ERR_UNSUPPORTED = -7      /* option combination not supported */
 } rqlp_status;
 
 /* Precision of the products with A (sketch, power steps, projection).
