@@ -333,6 +333,66 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _run_extra(R, W, torch, A, steps):
+    """Rows of the method beside the headline, timed with CUDA events on the
+    current stream after two untimed runs: BRQLP (Algorithm 4.1) on the same
+    8192 x 8192 matrix with blocks of l / 5 = 22 columns, in BF16x3 and FP64,
+    and the adjoint on the 4096 x 2048 FP32 differentiable workload (q = 1,
+    cotangent on sum_{j<k} L_jj; each call recomputes the forward factorization
+    and reads the device status).  A failure is reported in the line instead
+    of ending the run."""
+    out = {}
+    dev = A.device
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, min(steps, 5))
+    l = K_RANK + P_OVER
+    b = l // 5
+    Om = torch.from_numpy(W.omega(A.shape[1], l, 0)).to(dev)
+    for form in ("bf16x3", "fp64"):
+        key = "brqlp_b%d_%s" % (b, form)
+        try:
+            held = {}
+
+            def run():
+                r = R.rqlp(A, K_RANK, P_OVER, Om, q=0, pivot2=True, block_b=b, prec=form,
+                           ws=held.get("ws"), check=False)
+                held["ws"] = r["ws"]
+
+            ms = timed(run, reps)
+            status = R.lib().rqlp_read_status(R._ptr(held["ws"]), R._stream(None))
+            out[key] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "status": int(status),
+                        "workload": "%dx%d, k = %d, p = %d, blocks of %d" % (
+                            A.shape[0], A.shape[1], K_RANK, P_OVER, b)}
+        except Exception as e:  # reported, not raised
+            out[key] = {"error": repr(e)[:300]}
+    try:
+        pr4 = W.c4(device=str(dev))
+        l4 = pr4.k + pr4.p
+        Om4 = torch.from_numpy(W.omega(pr4.n, l4, 0)).to(dev)
+        dL = torch.diag(torch.tensor([1.0] * pr4.k + [0.0] * pr4.p, dtype=torch.float64,
+                                     device=dev))
+        ms = timed(lambda: R.vjp(pr4.A, pr4.k, pr4.p, Om4, dL=dL, q=1), reps)
+        out["adjoint_c4"] = {"vjp_per_s": 1e3 / ms, "ms": ms,
+                             "workload": "%dx%d FP32, k = %d, p = %d, q = 1" % (
+                                 pr4.m, pr4.n, pr4.k, pr4.p)}
+    except Exception as e:  # reported, not raised
+        out["adjoint_c4"] = {"error": repr(e)[:300]}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -503,6 +563,11 @@ def run_ours(args):
         for form in forms_out:
             forms_out[form]["lvalue_err_vs_oracle"] = _lvalue_err(outs[form], ref)
 
+    # last, once every number of the line is in host memory
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = _run_extra(R, W, torch, A, args.steps)
+
     if rank == 0:
         line = {
             "metric": "erqlp_factorizations_per_s", "value": value, "unit": "factorizations/s",
@@ -519,6 +584,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "batched": batched,
+            "extra": extra,
             "e2e": e2e,
             "gpu_launches": int(main["launches"]),
             "clocks": main["clocks"],
@@ -538,6 +604,8 @@ def main():
                     choices=["fp64", "bf16x3", "bf16", "fp8", "tf32x3", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the BRQLP and adjoint lines")
     ap.add_argument("--shape", type=int, nargs=2, default=[M, N_], metavar=("M", "N"))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
