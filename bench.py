@@ -47,7 +47,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA-core and DMMA) nominal rate
 _TRAFFIC = {
     "cpqr_of_B": {
         "source": "paper_1811_09334_gb300/csrc/cpqr.cu",
-        "sha256": "a1fffd55bad28cf00240e7f44fb614f1b70645eaad4cd22996092324d56738e2",
+        "sha256": "9d6d630acbe26d8a0f3073f677ac83f1c426423082ba3becc4fef1e4f5bf3fb8",
         "profile": "profiles/k_cpqr_wide_b110x4096.md",
         # dram__bytes_read.sum + dram__bytes_write.sum at n = 4096 columns
         # (3.72 MB + 9.7 KB), scaled by the columns processed

@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   // warp 0: publish candidate jc (local index, key cn) for exchange k into
   // buffer buf; its column is final through row r0 - 1 once cj x(r0:)
   // (cj != 0: the step's axpy, applied here) is subtracted.  The record is
-  // (cn, index), sigma = ||col(r0 + 1:)||^2 exactly and x0 = col(r0); the
-  // column goes out from row r0 on.
+  // (cn, index), sigma = ||col(r0 + 1:)||^2 exactly and x0 = col(r0) (also
+  // returned, sigma to every lane, x0 to lane 0); the column goes out from
+  // row r0 on.
   // One CTA (G = 1) exchanges nothing: it keeps sigma and x0 (lane 0) and
   // takes the winner, its own candidate, straight from shared memory.
   auto publish = [&](int buf, unsigned k, int jc, double cn, int r0, double cj, double &sg,
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     // ---- 5. the remaining axpys, while warp 0 arrives (and, if last, picks
     // the winner) ----
     if (b == 0 && warp == kWarps - 1) {
-      // this step's reflector, off the path to the barrier
+      // this step's reflector, off the path to the exchange
       for (int r = lane; r < l; r += 32)
         P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : (r == s ? 1.0 : s_v[r - s] * rv0);
       if (lane == 0) { P.tau[s] = tau; P.piv[s] = wi; }
@@ -694,7 +695,7 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   e = cudaMemsetAsync(tagged, 0, tb, st);
   if (e != cudaSuccess) return e;
   if (pl.G == 1) {
-    // one CTA: it is always the last arriver, no co-residency is needed
+    // one CTA: it exchanges nothing, no co-residency is needed
     if (pl.use_smem)
       k_cpqr_wide<true><<<1, kThreads, pl.smem, st>>>(P);
     else
