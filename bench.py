@@ -38,7 +38,7 @@ K_RANK, P_OVER, Q_POW, D_INNER = 100, 10, 1, 2
 def workload_name(m: int, n: int) -> str:
     return "erqlp_%dx%d_k%d_p%d_q%d_d%d_expdecay" % (m, n, K_RANK, P_OVER, Q_POW, D_INNER)
 
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA-core and DMMA) nominal rate
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 nominal rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz), context only
 
 
 # DRAM traffic per launch of a kernel class's dominant kernel, from one ncu
@@ -177,7 +177,9 @@ def _class_work(m, n, l, q, d, prec):
         "explicit_Q0": ("flops", 4.0 * l ** 3 / 3.0),
         "prep_A": ("bytes", {"fp64": 0.0, "bf16x3": 16.0, "bf16": 12.0, "fp8": 18.0,
                               "tf32x3": 24.0, "tf32": 16.0}[prec] * m * n),
-        "assembly": ("flops", 2.0 * (m + n) * l * l),
+        # Q = V Q_B (2 m l^2); P = Pi0 Q(1) Q(3) ... is a product only for d > 2
+        # (for d <= 2 it is a row scatter of Q(1), no flops)
+        "assembly": ("flops", 2.0 * (m + (n if d > 2 else 0)) * l * l),
     }
 
 
@@ -190,7 +192,7 @@ _TC_PRODUCTS = {"bf16x3": 3, "bf16": 1, "tf32x3": 3, "tf32": 1, "fp8": 1}
 def _stage_roofline(form, m, n, l, q, d, prof, steps, peaks):
     """Per kernel class of one form: achieved rate from its event time and the
     algorithmic work of _class_work, against the measured HBM copy rate
-    (bytes) or the nominal FP64 rate (flops).  The products with A of a
+    (bytes) or the measured FP64 rate (flops; peaks["fp64_tflops"]).  The products with A of a
     mixed form also get their tensor-core rate (the products the tensor
     cores execute: three per pass for the split forms) against the measured
     sustained BF16 rate scaled to the form's dtype."""
@@ -206,7 +208,7 @@ def _stage_roofline(form, m, n, l, q, d, prof, steps, peaks):
                  "frac": per_s / 1e9 / peaks["hbm_gbs"]}
         else:
             e = {"bound": "alu", "achieved_tflops": per_s / 1e12,
-                 "frac": per_s / 1e12 / FP64_NOMINAL_TFLOPS}
+                 "frac": per_s / 1e12 / peaks["fp64_tflops"]}
         if cls == "products_with_A" and form in _TC_RATIO:
             tc = _TC_PRODUCTS[form] * (2 * q + 2) * 2.0 * m * n * l * steps / (ms / 1e3) / 1e12
             peak = peaks["bf16_tflops_sustained"] * _TC_RATIO[form]
@@ -474,6 +476,9 @@ def run_ours(args):
     value = world * main["steps"] / (main["ms_total"] / 1e3)
     flops = _sketch_flops(pr.m, pr.n, pr.l, Q_POW)
     peaks, peak_src = _peaks()
+    # the FP64 rate is measured here (the peaks file has no FP64 entry)
+    fp64 = R.fp64_peak()
+    peaks["fp64_tflops"] = fp64["tflops"]
     forms_out = {}
     for form, r in results.items():
         prod_ms, prod_cnt = r["prof"]["products_with_A"]
@@ -500,10 +505,10 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": per_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": per_s / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src}
     else:
-        roof = {"bound": "alu", "achieved": per_s / 1e12, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": per_s / 1e12 / FP64_NOMINAL_TFLOPS,
-                "peak_source": "GB300 FP64 rate from its unit counts and 2.07 GHz clock "
-                               "(2 FMA/clk/SM x 152 SMs); no measured FP64 peak"}
+        roof = {"bound": "alu", "achieved": per_s / 1e12, "peak": fp64["tflops"],
+                "unit": "TFLOP/s", "frac": per_s / 1e12 / fp64["tflops"],
+                "peak_source": "measured in this run: " + fp64["how"],
+                "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS}
     roof["kernel_class"] = dom
     roof["launches_timed"] = int(dom_cnt)
     roof["algorithmic_per_step"] = amount
@@ -562,6 +567,13 @@ def run_ours(args):
                          % len(times)}
         for form in forms_out:
             forms_out[form]["lvalue_err_vs_oracle"] = _lvalue_err(outs[form], ref)
+        # the forms not timed above: one untimed factorization each, for its error
+        for form in ("bf16", "tf32", "fp8"):
+            if form in forms_out:
+                continue
+            o = R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form,
+                       rvalues=False)
+            forms_out[form] = {"lvalue_err_vs_oracle": _lvalue_err(o, ref), "timed": False}
 
     # last, once every number of the line is in host memory
     extra = None

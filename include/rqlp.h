@@ -88,12 +88,23 @@ typedef struct {
                            waits for an exchange number that never comes, so that it runs out of
                            time (tests of the timeout path) */
   int64_t spin_limit_ns;/* bound on every device-side wait in ns; 0 selects 2 s */
+  int32_t fixed_pivots; /* 0: the column pivots are chosen (and written to piv0 / piv1);
+                           1: piv0 (its first l entries) and, for Algorithm 2.1 (pivot2 = 1),
+                           piv1 are INPUTS, and the two QRs take these columns in this order
+                           (the unpivoted QR of B Pi0 and of R0^T Pi1): the factorization
+                           at fixed pivots, on which the adjoint and finite differences at a
+                           pivot change rely.  An index out of range or repeated gives the
+                           device status RQLP_ERR_INVALID_ARG.  Not with block_b > 0. */
+  int32_t truncate_k;   /* 0: outputs l wide; 1: the rank-k truncation (the abstract's rank-k
+                           L): Q m x k, L k x k, P n x k and k L-values, each with ld k
+                           (Q[:, :k], L[:k, :k], P[:, :k] of the l-wide factorization) */
 } rqlp_opts;
 
 /* Human-readable name of a status code. */
 const char *rqlp_status_string(int status);
 
-/* Library ABI version (major * 100 + minor). */
+/* Library ABI version (major * 100 + minor); 200 added fixed_pivots, truncate_k,
+ * rqlp_rvalues() and the pivot arguments of rqlp_backward(). */
 int rqlp_version(void);
 
 /* Bytes of device workspace rqlp() needs for these sizes and options
@@ -115,8 +126,11 @@ size_t rqlp_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rql
  *  Lvalues [out] l values diag(L) (>= 0); may be NULL.
  *  piv0    [out] n int32 column pivots of the CPQR of B (position i holds the
  *                original column index); may be NULL.  BRQLP: first block.
+ *                [in] with opts->fixed_pivots: l entries, required.
  *  piv1    [out] l int32 pivots of the second CPQR (identity for ERQLP); may be NULL.
+ *                [in] with opts->fixed_pivots and pivot2 = 1: l entries, required.
  *  ws      [in]  device workspace of ws_bytes >= rqlp_workspace_size(), 256-byte aligned.
+ * With opts->truncate_k, Q, L, P and Lvalues are k wide (ld k).
  * Returns RQLP_OK once the work is enqueued, or an argument error.
  */
 int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t p,
@@ -147,6 +161,15 @@ int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t
                    int32_t *piv0, int32_t *piv1, int32_t *l_used, void *ws, size_t ws_bytes,
                    rqlp_stream_t stream);
 
+/* The R-values of the last rqlp() call that used `ws` with these sizes and
+ * options: diag R0 (>= 0) of the column-pivoted QR of B (Algorithm 2.1 step 5),
+ * which Section 5 (Figures 1-2) sets beside the L-values as the cruder
+ * estimate of the singular values; for BRQLP the R-values of each block's
+ * B_j in block order.  Copies l values (k with truncate_k) to the device
+ * array Rvalues, enqueued on `stream` after that call. */
+int rqlp_rvalues(const void *ws, int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts,
+                 double *Rvalues, rqlp_stream_t stream);
+
 /* Synchronizes `stream` and returns the device status word of the last call
  * that used `ws` (RQLP_OK, a warning or an error). */
 int rqlp_read_status(const void *ws, rqlp_stream_t stream);
@@ -159,7 +182,9 @@ size_t rqlp_host_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, cons
  * rqlp() on HOST buffers: copies A (m x n, dense, lda = n) and Omega (n x l)
  * to the device workspace, factors, copies Q, L, P, Lvalues, piv0, piv1 back
  * and synchronizes the stream.  Host buffers should be page-locked for full
- * copy speed.  Returns the final status (argument, CUDA or device status).
+ * copy speed.  With opts->fixed_pivots piv0 / piv1 are host inputs (copied in,
+ * not back); with opts->truncate_k the outputs are k wide.  Returns the final
+ * status (argument, CUDA or device status).
  */
 int rqlp_host(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, int32_t k, int32_t p,
               const double *Omega_host, const rqlp_opts *opts, double *Q_host, double *L_host,
@@ -217,19 +242,25 @@ int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, 
  * this differentiates Algorithm 2.1 (pivot2 = 1) with the column pivots held
  * fixed (they are piecewise constant in A).
  * ---------------------------------------------------------------------- */
-/* Workspace of rqlp_backward() (0 if invalid; needs pivot2 = 1, block_b = 0). */
+/* Workspace of rqlp_backward() (0 if invalid; needs pivot2 = 1, block_b = 0,
+ * truncate_k = 0). */
 size_t rqlp_backward_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p,
                                     const rqlp_opts *opts);
 
 /* dA = J^T (dQ, dL, dP): the vector-Jacobian product of A -> (Q, L, P) of
  * rqlp() at A with the same Omega and options.  dQ (m x l), dL (l x l), dP
  * (n x l) are FP64 device cotangents with ld l (NULL = zero); dA (m x n, FP64,
- * ld ldda) is written.  The forward is recomputed inside (no state is kept
- * between rqlp() and this call); the sweep runs in FP64. */
+ * ld ldda) is written.  piv0 / piv1 (device, l int32 each, both or neither):
+ * the pivots of the forward call, held fixed in the recomputed forward (the
+ * derivative of the factorization at those pivots even where another column
+ * order is as good); NULL recomputes them from A.  The forward is recomputed
+ * inside (no other state is kept between rqlp() and this call); the sweep
+ * runs in FP64. */
 int rqlp_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
                   int32_t p, const double *Omega, int64_t ldo, const rqlp_opts *opts,
-                  const double *dQ, const double *dL, const double *dP, double *dA, int64_t ldda,
-                  void *ws, size_t ws_bytes, rqlp_stream_t stream);
+                  const int32_t *piv0, const int32_t *piv1, const double *dQ, const double *dL,
+                  const double *dP, double *dA, int64_t ldda, void *ws, size_t ws_bytes,
+                  rqlp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched factorizations: many independent problems in one graph launch.
@@ -291,7 +322,7 @@ void rqlp_batched_destroy(rqlp_batch_t plan);
 
 /*
  * rqlp_cpqr() for callers that cannot allocate device memory.  The paper has
- * no counterpart: this is a deployment variant of Algorithm 2.1 step 5.
+ * no counterpart.
  *
  * Who needs it: code that runs under another runtime's memory manager which
  * owns all of the device memory, or a latency-critical loop that must not call
@@ -304,7 +335,9 @@ void rqlp_batched_destroy(rqlp_batch_t plan);
  * Arguments as for rqlp_cpqr() (Bt n x l device input, R0t n x l, piv0 n and,
  * if not NULL, Q0 l x l device outputs).  With sync != 0 the call synchronizes
  * `stream` and returns the device status; with sync == 0 it returns after
- * enqueueing (the status then stays in the library's array until the next call).
+ * enqueueing, and a device-side error (a timeout, non-finite data) is NOT
+ * reported to the caller: the status word stays in the library's array and
+ * the next call clears it.  Callers that need the status pass sync != 0.
  * Limits: the pivot tables plus l x l reflectors must fit the 2 MiB array and
  * each CTA's slab of columns must fit in shared memory (about
  * n * l * 8 bytes <= 152 * 190 KiB on GB300); larger sizes return
@@ -354,6 +387,17 @@ int rqlp_profile_end(double *ms, long long *count, int nclass);
  * race; serialize them.
  */
 int rqlp_selftest(int32_t count, int32_t *fails, rqlp_stream_t stream);
+
+/*
+ * FP64 throughput probe (a diagnostic; the paper has no counterpart): enqueues
+ * one kernel on `stream` whose threads (four 256-thread CTAs per SM) run eight
+ * independent FP64 FMA chains of `iters` steps each, so that it is bound by
+ * the FP64 units alone.  *flops (host) gets the flop count of the launch
+ * (2 per FMA); time the launch with CUDA events on `stream` to measure the
+ * GPU's FP64 rate, the denominator of the FP64 kernels' rooflines.  sink: one
+ * device double, written only in a case that never arises.  Returns at once.
+ */
+int rqlp_fp64_probe(int32_t iters, double *sink, double *flops, rqlp_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -170,21 +170,46 @@ def range_finder(A: np.ndarray, Omega: np.ndarray, q: int = 0):
 
 
 # ---------------------------------------------------------- QLP of small B
-def qlp_of_B(B: np.ndarray, d: int = 1, pivot2: bool = True):
+def complete_perm(first, n: int) -> np.ndarray:
+    """A permutation of range(n) that starts with the given distinct indices,
+    the others following in their original order (the convention for the
+    columns a column-pivoted QR never chooses)."""
+    first = [int(i) for i in first]
+    if len(set(first)) != len(first) or any(i < 0 or i >= n for i in first):
+        raise ValueError("given pivots must be distinct indices in range")
+    chosen = set(first)
+    return np.array(first + [j for j in range(n) if j not in chosen], dtype=np.int64)
+
+
+def qlp_of_B(B: np.ndarray, d: int = 1, pivot2: bool = True, piv0=None, piv1=None):
     """Pivoted QLP of the small l x n matrix B: B = Q_B T P_B^T.
 
     pivot2 = True: Algorithm 2.1 steps 5-7 (two CPQRs); T = L = R1^T.
     pivot2 = False: Algorithm 2.2 steps 5-9 with d >= 1 unpivoted inner QRs
     [R(i-1)]^T = Q(i) R(i); assembled as described in the module header.
+    With piv0 (its first l entries) and, for pivot2, piv1 given, the two
+    pivoted QRs become unpivoted QRs of the permuted matrices B Pi0 and
+    R0^T Pi1 (the factorization at fixed pivots).
 
     Returns a dict with QB (l x l), T (l x l), PB (n x l), piv0 (n,),
     piv1 (l,) (identity when pivot2 is False), lower (bool), R0 (l x n).
     """
     B = np.asarray(B, dtype=np.float64)
     l, n = B.shape
-    Q0, R0, piv0 = cpqr(B)
+    if piv0 is None:
+        Q0, R0, piv0 = cpqr(B)
+    else:
+        piv0 = complete_perm(np.asarray(piv0)[:l], n)
+        Q0, R0 = wide_qr(B[:, piv0])
     X = R0.T  # n x l, rows in pivoted order
-    if pivot2:
+    if pivot2 and piv1 is not None:
+        piv1 = complete_perm(np.asarray(piv1)[:l], l)
+        Q1, R1 = householder_qr(X[:, piv1])
+        T = R1.T
+        QB = Q0[:, piv1]
+        M = Q1
+        lower = True
+    elif pivot2:
         Q1, R1, piv1 = cpqr(X)
         T = R1.T
         QB = Q0[:, piv1]
@@ -215,13 +240,15 @@ def qlp_of_B(B: np.ndarray, d: int = 1, pivot2: bool = True):
 
 # ------------------------------------------------------------ RQLP / ERQLP
 def rqlp(A: np.ndarray, k: int, p: int, Omega: np.ndarray, q: int = 0, d: int = 1,
-         pivot2: bool = True):
+         pivot2: bool = True, piv0=None, piv1=None):
     """Randomized QLP (Algorithm 2.1) / enhanced RQLP (Algorithm 2.2).
 
     A (m x n), target rank k, oversampling p, l = k + p, Omega (n x l) given
-    by the caller, q power steps, d inner QRs (used when pivot2 is False).
-    Returns a dict with Q (m x l), L (l x l; lower unless even-d ERQLP),
-    P (n x l), Lvalues (l,), piv0, piv1, V, B, lower.  A ~= Q L P^T.
+    by the caller, q power steps, d inner QRs (used when pivot2 is False);
+    optional given pivots as in qlp_of_B.  Returns a dict with Q (m x l),
+    L (l x l; lower unless even-d ERQLP), P (n x l), Lvalues (l,), Rvalues
+    (l,), piv0, piv1, V, B, lower.  A ~= Q L P^T.  The R-values diag R0 are
+    the diagonal of the CPQR of B that Section 5 compares with the L-values.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -233,11 +260,19 @@ def rqlp(A: np.ndarray, k: int, p: int, Omega: np.ndarray, q: int = 0, d: int = 
         raise ValueError("need 1 <= k + p <= min(m, n)")
     V, Y = range_finder(A, Omega, q)
     B = project(V, A)
-    f = qlp_of_B(B, d=d, pivot2=pivot2)
+    f = qlp_of_B(B, d=d, pivot2=pivot2, piv0=piv0, piv1=piv1)
     Q = V @ f["QB"]
     L = f["T"]
     return dict(Q=Q, L=L, P=f["PB"], Lvalues=np.diag(L).copy(), piv0=f["piv0"],
-                piv1=f["piv1"], V=V, B=B, lower=f["lower"], R0=f["R0"], Y=Y)
+                piv1=f["piv1"], V=V, B=B, lower=f["lower"], R0=f["R0"], Y=Y,
+                Rvalues=np.diag(f["R0"][:, :l]).copy())
+
+
+def truncate(res: dict, k: int) -> dict:
+    """The rank-k truncation of a factorization (the abstract's rank-k L):
+    Q[:, :k], L[:k, :k], P[:, :k] and the first k L-values."""
+    return dict(Q=res["Q"][:, :k], L=res["L"][:k, :k], P=res["P"][:, :k],
+                Lvalues=res["Lvalues"][:k])
 
 
 # ------------------------------------------------------------------ BRQLP
@@ -395,15 +430,19 @@ def rqlp_trace(A, k, p, Omega, q=0, piv0=None, piv1=None):
     return t
 
 
-def rqlp_vjp(A, k, p, Omega, dQ, dL, dP, q=0):
+def rqlp_vjp(A, k, p, Omega, dQ, dL, dP, q=0, piv0=None, piv1=None):
     """dA = J^T (dQ, dL, dP) for RQLP (Algorithm 2.1) with fixed pivots.
 
     The sweep runs the forward of rqlp_trace backwards, product by product
-    and QR by QR (qr_vjp, wide_qr_vjp), recomputing the forward first.
+    and QR by QR (qr_vjp, wide_qr_vjp), recomputing the forward first (at the
+    given pivots, when piv0 and piv1 are given; piv0 may hold only its first
+    l entries, completed as in complete_perm).
     """
     A = np.asarray(A, dtype=np.float64)
     Om = np.asarray(Omega, dtype=np.float64)
-    t = rqlp_trace(A, k, p, Om, q)
+    if piv0 is not None:
+        piv0 = complete_perm(np.asarray(piv0)[:k + p], A.shape[1])
+    t = rqlp_trace(A, k, p, Om, q, piv0, piv1)
     l = t["V"].shape[1]
     n = A.shape[1]
     dQ = np.zeros_like(t["Q"]) if dQ is None else dQ

@@ -170,6 +170,8 @@ struct Plan {
   double *Y, *V, *Z, *W, *X, *R0t;
   double *Q0, *QB, *Macc, *Racc, *Rt, *Tl, *Vh, *tau, *Qi, *Rprev, *Xs, *sm1;
   double *utw;  // 2 l^2: scratch of the explicit Q from reflectors
+  double *rvals;  // l: R-values, diag R0 of the CPQR of B (per block for BRQLP)
+  double *Qf, *Lf, *Pf;  // full-width factors before a rank-k truncation (else null)
   int32_t *piv0, *piv1;
   void *cpqr_scratch;
   MixedBufs mx;
@@ -202,6 +204,13 @@ Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
   p.Xs = a.take<double>(ll);
   p.sm1 = a.take<double>(ll);
   p.utw = a.take<double>(2 * ll);
+  p.rvals = a.take<double>((size_t)l);
+  p.Qf = p.Lf = p.Pf = nullptr;
+  if (o.truncate_k) {
+    p.Qf = a.take<double>((size_t)m * l);
+    p.Lf = a.take<double>(ll);
+    p.Pf = a.take<double>((size_t)n * l);
+  }
   p.piv0 = a.take<int32_t>((size_t)n);
   p.piv1 = a.take<int32_t>((size_t)l);
   p.cpqr_scratch = a.take<char>(cpqr_ws_bytes(std::max<int64_t>(n, l), l));
@@ -218,6 +227,8 @@ bool valid_opts(const rqlp_opts *o) {
   if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_TF32) return false;
   if (o->block_b < 0) return false;
   if (o->spin_limit_ns < 0) return false;
+  if (o->fixed_pivots != 0 && o->fixed_pivots != 1) return false;
+  if (o->truncate_k != 0 && o->truncate_k != 1) return false;
   return true;
 }
 
@@ -291,17 +302,22 @@ SideStream *side_for(cudaStream_t st) {
 // ld w), followed by the assembly of Q and P (Algorithm 2.1 steps 5-7,
 // Algorithm 2.2 steps 5-9).  Vb is the m x w range basis (ld ldv); Q (m x w),
 // L (w x w) and P (n x w) are written with leading dimension ldo; piv1 gets w
-// entries.
+// entries; rv gets the w R-values diag R0.  fp0 / fp1 (device, may be null):
+// given pivots of the two column-pivoted QRs (w entries each), which are then
+// taken instead of chosen.
 int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, const double *Vb,
               int64_t ldv, const double *Bt, double *Q, double *L, double *Pout, int64_t ldo,
-              int32_t *piv0, int32_t *piv1, int site0, cudaStream_t st) {
+              int32_t *piv0, int32_t *piv1, int site0, cudaStream_t st, const int32_t *fp0,
+              const int32_t *fp1, double *rv) {
   Ctrl *ctrl = P.ctrl;
   const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
   const unsigned extra = (o.debug_flags & 1) ? 1u : 0u;
   const int l = w;
   int ev = prof_start(kProfCpqr, st);
-  CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st));
+  CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st,
+               fp0));
   prof_stop(kProfCpqr, ev, st);
+  CK(diag_of(P.R0t, l, l, rv, st));  // the R-values of Section 5
   // Q0 from the reflectors, beside the QR of R0^T (joined before Vh is
   // overwritten or Q0 is used)
   SideStream *sd = side_for(st);
@@ -324,7 +340,8 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     RET(orth(P.R0t, n, l, l, P.X, l, P.Racc, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
     CK(transpose(P.Racc, l, l, l, P.Rt, l, st));
     RET(join());
-    CK(cpqr_wide(P.Rt, l, l, l, P.Tl, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st));
+    CK(cpqr_wide(P.Rt, l, l, l, P.Tl, l, piv1, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, 0, st,
+                 fp1));
     CK(copy2d(P.Tl, l, l, l, L, ldo, nullptr, st));
     CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st, P.utw));
     CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
@@ -406,7 +423,8 @@ int brqlp_block(const Plan &P, const rqlp_opts &o, const void *A, int a_dtype, i
   RET(prod_tn(P, o, A, a_dtype, m, n, lda, Vj, l, b, P.Z, st));
   int32_t *p0 = (j == 0) ? piv0 : P.piv0;
   RET(qlp_stage(P, o, m, n, b, Vj, l, P.Z, Q + (size_t)j * b, L + (size_t)j * b * l + j * b,
-                Pout + (size_t)j * b, l, p0, piv1 + (size_t)j * b, site, st));
+                Pout + (size_t)j * b, l, p0, piv1 + (size_t)j * b, site, st, nullptr, nullptr,
+                P.rvals + (size_t)j * b));
   site += o.d + 1;
   return RQLP_OK;
 }
@@ -472,8 +490,29 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   Plan P = carve(ws, m, n, l, o);
   if (P.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
   CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
-  int32_t *pv0 = piv0 ? piv0 : P.piv0;
-  int32_t *pv1 = piv1 ? piv1 : P.piv1;
+  // given pivots are read from the caller's arrays; the pivots the kernels
+  // write then go to the workspace
+  const int32_t *fp0 = o.fixed_pivots ? piv0 : nullptr;
+  const int32_t *fp1 = (o.fixed_pivots && o.pivot2) ? piv1 : nullptr;
+  int32_t *pv0 = (piv0 && !o.fixed_pivots) ? piv0 : P.piv0;
+  int32_t *pv1 = (piv1 && !o.fixed_pivots) ? piv1 : P.piv1;
+  // a rank-k truncation (the rank-k output of the abstract) factors at full
+  // width l into the workspace and copies the leading k columns out
+  double *Qo = Q, *Lo = L, *Po = Pout, *LVo = Lvalues;
+  if (o.truncate_k) {
+    Q = P.Qf;
+    L = P.Lf;
+    Pout = P.Pf;
+    Lvalues = nullptr;
+  }
+  auto finish = [&]() -> int {
+    if (!o.truncate_k) return RQLP_OK;
+    CK(copy2d(Q, m, k, l, Qo, k, nullptr, st));
+    CK(copy2d(L, k, k, l, Lo, k, nullptr, st));
+    CK(copy2d(Pout, n, k, l, Po, k, nullptr, st));
+    if (LVo) CK(diag_of(L, k, l, LVo, st));
+    return RQLP_OK;
+  };
   if (o.prec != RQLP_PREC_FP64) {
     const int ev = prof_start(kProfPrep, st);
     RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
@@ -483,7 +522,7 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   if (o.block_b > 0) {
     RET(run_brqlp(P, o, A, a_dtype, m, n, lda, l, Omega, ldo, Q, L, Pout, pv0, pv1, st));
     if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
-    return RQLP_OK;
+    return finish();
   }
   // range finder (Section 2) with q power steps
   RET(prod_nn(P, o, A, a_dtype, m, n, lda, Omega, ldo, l, P.Y, st));
@@ -501,9 +540,10 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 2, again_tol_of(o)));
   // B^T = A^T V  (Algorithm 2.1 step 4)
   RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
-  RET(qlp_stage(P, o, m, n, l, P.V, l, P.Z, Q, L, Pout, l, pv0, pv1, site, st));
+  RET(qlp_stage(P, o, m, n, l, P.V, l, P.Z, Q, L, Pout, l, pv0, pv1, site, st, fp0, fp1,
+                P.rvals));
   if (Lvalues) CK(diag_of(L, l, l, Lvalues, st));
-  return RQLP_OK;
+  return finish();
 }
 
 }  // namespace
@@ -525,7 +565,7 @@ const char *rqlp_status_string(int s) {
   }
 }
 
-int rqlp_version(void) { return 100; }
+int rqlp_version(void) { return 200; }
 
 size_t rqlp_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts) {
   if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return 0;
@@ -544,6 +584,8 @@ int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int3
   if (lda < n || ldo < l) return RQLP_ERR_INVALID_ARG;
   if (opts->block_b > 0 && (l % opts->block_b != 0)) return RQLP_ERR_INVALID_ARG;
   if (opts->block_b > 0 && opts->q > 0) return RQLP_ERR_UNSUPPORTED;  // Algorithm 4.1 has no power steps
+  if (opts->fixed_pivots && opts->block_b > 0) return RQLP_ERR_UNSUPPORTED;
+  if (opts->fixed_pivots && (!piv0 || (opts->pivot2 && !piv1))) return RQLP_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
   return run_rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, *opts, Q, L, P, Lvalues, piv0, piv1, ws,
                   ws_bytes, reinterpret_cast<cudaStream_t>(stream));
@@ -560,6 +602,7 @@ int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t
   if (b < 1 || l_max % b != 0 || !(tol >= 0.0) || lda < n || ldo < l_max)
     return RQLP_ERR_INVALID_ARG;
   if (opts->q > 0) return RQLP_ERR_UNSUPPORTED;  // Algorithm 4.1 has no power steps
+  if (opts->fixed_pivots || opts->truncate_k) return RQLP_ERR_UNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
   *l_used = 0;
   rqlp_opts o = *opts;
@@ -596,6 +639,17 @@ int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t
   return rqlp_read_status(ws, stream);
 }
 
+int rqlp_rvalues(const void *ws, int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts,
+                 double *Rvalues, rqlp_stream_t stream) {
+  if (!ws || !Rvalues || !valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  Plan P = carve(const_cast<void *>(ws), m, n, k + p, *opts);
+  const int cnt = opts->truncate_k ? k : k + p;
+  CK(cudaMemcpyAsync(Rvalues, P.rvals, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToDevice,
+                     reinterpret_cast<cudaStream_t>(stream)));
+  return RQLP_OK;
+}
+
 int rqlp_read_status(const void *ws, rqlp_stream_t stream) {
   if (!ws) return RQLP_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -626,7 +680,10 @@ int rqlp_host_async(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, i
   if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
   const size_t need = rqlp_host_workspace_size(m, n, k, p, opts, a_dtype);
   if (ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  if (opts->fixed_pivots && (!piv0_host || (opts->pivot2 && !piv1_host)))
+    return RQLP_ERR_INVALID_ARG;
   const int64_t l = k + p;
+  const int64_t w = opts->truncate_k ? k : l;  // width of the outputs
   const size_t esz = a_dtype == RQLP_F32 ? 4 : 8;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   char *c = reinterpret_cast<char *>(ws);
@@ -642,15 +699,22 @@ int rqlp_host_async(const void *A_host, int32_t a_dtype, int64_t m, int64_t n, i
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemcpyAsync(dA, A_host, (size_t)m * n * esz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dO, Omega_host, (size_t)n * l * 8, cudaMemcpyHostToDevice, st));
+  if (opts->fixed_pivots) {
+    // given pivots are inputs: the first l of piv0 (and l of piv1 for RQLP)
+    CK(cudaMemcpyAsync(dp0, piv0_host, (size_t)l * 4, cudaMemcpyHostToDevice, st));
+    if (opts->pivot2) CK(cudaMemcpyAsync(dp1, piv1_host, (size_t)l * 4, cudaMemcpyHostToDevice, st));
+  }
   int r = rqlp(dA, a_dtype, m, n, n, k, p, dO, l, opts, dQ, dL, dP, dLv, dp0, dp1, c, base,
                stream);
   if (r != RQLP_OK) return r;
-  CK(cudaMemcpyAsync(Q_host, dQ, (size_t)m * l * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(L_host, dL, (size_t)l * l * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(P_host, dP, (size_t)n * l * 8, cudaMemcpyDeviceToHost, st));
-  if (Lvalues_host) CK(cudaMemcpyAsync(Lvalues_host, dLv, (size_t)l * 8, cudaMemcpyDeviceToHost, st));
-  if (piv0_host) CK(cudaMemcpyAsync(piv0_host, dp0, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
-  if (piv1_host) CK(cudaMemcpyAsync(piv1_host, dp1, (size_t)l * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(Q_host, dQ, (size_t)m * w * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(L_host, dL, (size_t)w * w * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(P_host, dP, (size_t)n * w * 8, cudaMemcpyDeviceToHost, st));
+  if (Lvalues_host) CK(cudaMemcpyAsync(Lvalues_host, dLv, (size_t)w * 8, cudaMemcpyDeviceToHost, st));
+  if (!opts->fixed_pivots) {
+    if (piv0_host) CK(cudaMemcpyAsync(piv0_host, dp0, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    if (piv1_host) CK(cudaMemcpyAsync(piv1_host, dp1, (size_t)l * 4, cudaMemcpyDeviceToHost, st));
+  }
   return RQLP_OK;
 }
 
@@ -841,9 +905,9 @@ cudaError_t zero(double *p, int64_t n, cudaStream_t st) {
 }
 
 int run_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int l,
-                 const double *Omega, int64_t ldo, const rqlp_opts &o, const double *dQ,
-                 const double *dL, const double *dP, double *dA, int64_t ldda, void *ws,
-                 size_t ws_bytes, cudaStream_t st) {
+                 const double *Omega, int64_t ldo, const rqlp_opts &o, const int32_t *fp0,
+                 const int32_t *fp1, const double *dQ, const double *dL, const double *dP,
+                 double *dA, int64_t ldda, void *ws, size_t ws_bytes, cudaStream_t st) {
   BwdPlan B = carve_bwd(ws, m, n, l, o);
   if (B.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
   const Plan &F = B.F;
@@ -865,11 +929,13 @@ int run_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   }
   RET(orth(F.Y, m, l, l, F.V, l, B.RY, F.ob, ctrl, site++, st));
   RET(prod_tn(F, o, A, a_dtype, m, n, lda, F.V, l, l, F.Z, st));  // B^T
-  CK(cpqr_wide(F.Z, n, l, l, F.R0t, l, F.piv0, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st));
+  CK(cpqr_wide(F.Z, n, l, l, F.R0t, l, F.piv0, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st,
+               fp0));
   CK(form_q(F.Vh, l, F.tau, l, l, F.Q0, l, st));
   RET(orth(F.R0t, n, l, l, F.X, l, F.Racc, F.ob, ctrl, site++, st));
   CK(transpose(F.Racc, l, l, l, F.Rt, l, st));
-  CK(cpqr_wide(F.Rt, l, l, l, F.Tl, l, F.piv1, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st));
+  CK(cpqr_wide(F.Rt, l, l, l, F.Tl, l, F.piv1, F.Vh, F.tau, F.cpqr_scratch, ctrl, lim, 0, st,
+               fp1));
   CK(form_q(F.Vh, l, F.tau, l, l, F.Qi, l, st));
   CK(gemm_f64(false, RQLP_F64, F.X, l, F.Qi, l, B.Q1, l, n, l, l, 1.0, 0.0, part, nullptr, nullptr,
               st));                                               // Q1 = Qa Qc
@@ -960,21 +1026,27 @@ extern "C" {
 size_t rqlp_backward_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p,
                                     const rqlp_opts *opts) {
   if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return 0;
-  if (!opts->pivot2 || opts->block_b != 0) return 0;
-  return carve_bwd(nullptr, m, n, k + p, *opts).bytes + 256;
+  if (!opts->pivot2 || opts->block_b != 0 || opts->truncate_k) return 0;
+  rqlp_opts o = *opts;
+  o.fixed_pivots = 0;
+  return carve_bwd(nullptr, m, n, k + p, o).bytes + 256;
 }
 
 int rqlp_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
                   int32_t p, const double *Omega, int64_t ldo, const rqlp_opts *opts,
-                  const double *dQ, const double *dL, const double *dP, double *dA, int64_t ldda,
-                  void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+                  const int32_t *piv0, const int32_t *piv1, const double *dQ, const double *dL,
+                  const double *dP, double *dA, int64_t ldda, void *ws, size_t ws_bytes,
+                  rqlp_stream_t stream) {
   if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return RQLP_ERR_INVALID_ARG;
   if (!A || !Omega || !dA || !ws || lda < n || ldo < k + p || ldda < n) return RQLP_ERR_INVALID_ARG;
   if (a_dtype != RQLP_F64 && a_dtype != RQLP_F32) return RQLP_ERR_INVALID_ARG;
-  if (!opts->pivot2 || opts->block_b != 0) return RQLP_ERR_UNSUPPORTED;
+  if (!opts->pivot2 || opts->block_b != 0 || opts->truncate_k) return RQLP_ERR_UNSUPPORTED;
+  if ((piv0 == nullptr) != (piv1 == nullptr)) return RQLP_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
-  return run_backward(A, a_dtype, m, n, lda, k + p, Omega, ldo, *opts, dQ, dL, dP, dA, ldda, ws,
-                      ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+  rqlp_opts o = *opts;
+  o.fixed_pivots = 0;  // the pivot arrays themselves say whether they are given
+  return run_backward(A, a_dtype, m, n, lda, k + p, Omega, ldo, o, piv0, piv1, dQ, dL, dP, dA,
+                      ldda, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

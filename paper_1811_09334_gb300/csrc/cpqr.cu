@@ -71,6 +71,7 @@ struct CpqrParams {
   unsigned extra;
   int cpb;
   int use_smem;
+  const int32_t *fpiv;  // given pivots (original column indices of steps 0..l-1), or null
 };
 
 __device__ __forceinline__ bool better(double na, int ia, double nb, int ib) {
@@ -82,6 +83,15 @@ __device__ __forceinline__ bool better(double na, int ia, double nb, int ib) {
   const long long ka = __double_as_longlong(na), kb = __double_as_longlong(nb);
   if (ka != kb) return ka > kb;
   return ia < ib;
+}
+
+// Selection key of column `idx` for step s: its trailing norm^2, or with
+// given pivots 1 for the step's given column and 0 for every other one (the
+// exchange then elects the given column; ties among the others go to the
+// lowest index as usual and never win).
+__device__ __forceinline__ double pick_key(const int32_t *fpiv, int s, int idx, double nrm2) {
+  if (!fpiv) return nrm2;
+  return (idx == __ldg(fpiv + s)) ? 1.0 : 0.0;
 }
 
 // (norm, index) of the better of this lane's pair and its xor partners'
@@ -355,8 +365,10 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   {
     double bn = -1.0;
     int bi = -1;
-    for (int jj = tid; jj < nc; jj += kThreads)
-      if (better(nrm[jj], (int)(c0 + jj), bn, bi)) { bn = nrm[jj]; bi = (int)(c0 + jj); }
+    for (int jj = tid; jj < nc; jj += kThreads) {
+      const double key = pick_key(P.fpiv, 0, (int)(c0 + jj), nrm[jj]);
+      if (better(key, (int)(c0 + jj), bn, bi)) { bn = key; bi = (int)(c0 + jj); }
+    }
     warp_best(bn, bi);
     if (lane == 0) { s_bn[warp] = bn; s_bi[warp] = bi; }
     __syncthreads();
@@ -379,7 +391,9 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     const int buf = s & 1;
     // ---- 1. winner (every CTA picked the same one) and its sigma ----
     const int wc = s_win_cta, wi = s_win_idx;
-    if (wi < 0 || wc < 0 || wc >= G) {
+    // with given pivots the elected column must be the given one: a given
+    // index out of range or repeated leaves no column with key 1
+    if (wi < 0 || wc < 0 || wc >= G || (P.fpiv && wi != __ldg(P.fpiv + s))) {
       if (tid == 0) set_status(P.ctrl, RQLP_ERR_INVALID_ARG);
       return;
     }
@@ -500,7 +514,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
           thr[jj] = 0.01 * nd;
           axdone[jj] = 1;
         }
-        if (better(nd, (int)(c0 + jj), bn, bi)) { bn = nd; bi = (int)(c0 + jj); }
+        const double key = s + 1 < l ? pick_key(P.fpiv, s + 1, (int)(c0 + jj), nd) : nd;
+        if (better(key, (int)(c0 + jj), bn, bi)) { bn = key; bi = (int)(c0 + jj); }
       }
     }
     warp_best(bn, bi);
@@ -658,7 +673,8 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
 
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
-                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st) {
+                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
+                      const int32_t *fixed_piv) {
   if (n <= 0 || l <= 0 || l > kMaxL || l > n) return cudaErrorInvalidValue;
   Plan pl = plan_for(n, l);
   if (pl.G > kMaxGrid) return cudaErrorInvalidValue;
@@ -688,6 +704,7 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   P.extra = debug_extra;
   P.cpb = pl.cpb;
   P.use_smem = pl.use_smem;
+  P.fpiv = fixed_piv;
   // the permutation stays valid even if the kernel stops early on an error
   e = iota(piv, n, st);
   if (e != cudaSuccess) return e;

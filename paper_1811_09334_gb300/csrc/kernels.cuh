@@ -154,9 +154,13 @@ size_t cpqr_ws_bytes(int64_t n, int l);
 size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits);
 // Column-pivoted Householder QR of the l x n matrix whose columns are the
 // rows of Bt (n x l, ld ldb).  Writes R0t (n x l, ld ldr), piv (n), the
-// reflectors Vh (l x l, ld l) and tau (l).  Cooperative launch.
+// reflectors Vh (l x l, ld l) and tau (l).  Cooperative launch.  With
+// fixed_piv (device, l entries) step s takes column fixed_piv[s] instead of
+// the largest trailing norm: the unpivoted Householder QR of the permuted
+// matrix; an index out of range or repeated sets RQLP_ERR_INVALID_ARG.
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
-                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st);
+                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
+                      const int32_t *fixed_piv = nullptr);
 
 }  // namespace rqk

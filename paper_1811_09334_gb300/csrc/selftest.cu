@@ -64,3 +64,44 @@ extern "C" int rqlp_selftest(int32_t count, int32_t *fails, rqlp_stream_t stream
   for (int k = 0; k < 4; ++k) fails[k] = out[k];
   return RQLP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 throughput probe: the denominator of the FP64 rooflines.  Every thread
+// runs eight independent FMA chains (enough in flight to keep the FP64 units
+// busy), so the kernel is bound by FP64 issue alone; the chains' sums are
+// written only when they match an impossible value, which keeps the compiler
+// from dropping the work without costing any traffic.
+namespace rqk {
+namespace {
+
+constexpr int kProbeChains = 8;
+constexpr int kProbeThreads = 256;
+
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_probe(int iters, double *sink) {
+  double a[kProbeChains];
+  const double x = 1.0 + 1e-9 * (double)threadIdx.x, y = 0.999999999;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) a[c] = (double)(c + 1);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) a[c] = fma(a[c], y, x);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) s += a[c];
+  if (s == -1.0) sink[0] = s;
+}
+
+}  // namespace
+}  // namespace rqk
+
+extern "C" int rqlp_fp64_probe(int32_t iters, double *sink, double *flops, rqlp_stream_t stream) {
+  if (iters <= 0 || !sink || !flops) return RQLP_ERR_INVALID_ARG;
+  const int blocks = 4 * rqk::num_sms();
+  rqk::k_fp64_probe<<<blocks, rqk::kProbeThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      iters, sink);
+  rqk::count_launch();
+  if (cudaGetLastError() != cudaSuccess) return RQLP_ERR_CUDA;
+  *flops = 2.0 * rqk::kProbeChains * (double)iters * blocks * rqk::kProbeThreads;
+  return RQLP_OK;
+}

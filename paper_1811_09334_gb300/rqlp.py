@@ -29,7 +29,8 @@ _c_i32, _c_i64, _c_sz, _c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, c
 
 class Opts(ctypes.Structure):
     _fields_ = [("q", _c_i32), ("d", _c_i32), ("pivot2", _c_i32), ("prec", _c_i32),
-                ("block_b", _c_i32), ("debug_flags", _c_i32), ("spin_limit_ns", _c_i64)]
+                ("block_b", _c_i32), ("debug_flags", _c_i32), ("spin_limit_ns", _c_i64),
+                ("fixed_pivots", _c_i32), ("truncate_k", _c_i32)]
 
 
 class Problem(ctypes.Structure):
@@ -60,6 +61,8 @@ _SIGS = {
     "rqlp": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
                       ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_read_status": (_c_i32, [_c_p, _c_p]),
+    "rqlp_rvalues": (_c_i32, [_c_p, _c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts), _c_p,
+                              _c_p]),
     "rqlp_brqlp_tol": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32,
                                 ctypes.c_double, _c_p, _c_i64, ctypes.POINTER(Opts), _c_p, _c_p,
                                 _c_p, _c_p, _c_p, _c_p, ctypes.POINTER(ctypes.c_int32), _c_p,
@@ -81,6 +84,7 @@ _SIGS = {
     "rqlp_cpqr": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_cpqr_static": (_c_i32, [_c_p, _c_i64, _c_i32, _c_i64, _c_p, _c_p, _c_p, _c_i32, _c_p]),
     "rqlp_selftest": (_c_i32, [_c_i32, _c_p, _c_p]),
+    "rqlp_fp64_probe": (_c_i32, [_c_i32, _c_p, _c_p, _c_p]),
     "rqlp_batched_workspace_size": (_c_sz, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
                                             ctypes.POINTER(BatchTuning)]),
     "rqlp_batched_create": (_c_i32, [ctypes.POINTER(Problem), _c_i32, ctypes.POINTER(Opts),
@@ -91,8 +95,8 @@ _SIGS = {
     "rqlp_batched_destroy": (None, [_c_p]),
     "rqlp_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
     "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
-                               ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_sz,
-                               _c_p]),
+                               ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i64,
+                               _c_p, _c_sz, _c_p]),
     "rqlp_launch_count": (ctypes.c_longlong, []),
     "rqlp_profile_begin": (_c_i32, []),
     "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
@@ -113,6 +117,31 @@ def selftest(count: int = 1 << 20, stream=None):
     fails = (ctypes.c_int32 * 4)()
     _check(lib().rqlp_selftest(count, ctypes.cast(fails, _c_p), _stream(stream)), "rqlp_selftest")
     return list(fails)
+
+
+def fp64_peak(iters: int = 1 << 14, reps: int = 5, stream=None) -> dict:
+    """Measured FP64 FMA rate of this GPU in TFLOP/s (rqlp_fp64_probe timed
+    with CUDA events on the launch stream; the best of `reps` launches after
+    one warm-up)."""
+    torch = _torch()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flops = ctypes.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    best = None
+    for r in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib().rqlp_fp64_probe(int(iters), _ptr(sink), ctypes.byref(flops), _stream(st)),
+               "rqlp_fp64_probe")
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if r > 0 and (best is None or ms < best):
+            best = ms
+    return {"tflops": flops.value / (best / 1e3) / 1e12, "ms": best, "flops": flops.value,
+            "how": "rqlp_fp64_probe: 8 independent FP64 FMA chains per thread, 4 x SMs CTAs "
+                   "of 256 threads, %d steps; best of %d event-timed launches" % (iters, reps)}
 
 
 def profile_begin():
@@ -150,9 +179,11 @@ def lib():
     return _lib
 
 
-def opts(q=0, d=1, pivot2=True, prec="fp64", block_b=0, debug_flags=0, spin_limit_ns=0) -> Opts:
+def opts(q=0, d=1, pivot2=True, prec="fp64", block_b=0, debug_flags=0, spin_limit_ns=0,
+         fixed_pivots=False, truncate_k=False) -> Opts:
     return Opts(int(q), int(d), 1 if pivot2 else 0, PREC[prec] if isinstance(prec, str) else int(prec),
-                int(block_b), int(debug_flags), int(spin_limit_ns))
+                int(block_b), int(debug_flags), int(spin_limit_ns), 1 if fixed_pivots else 0,
+                1 if truncate_k else 0)
 
 
 def _torch():
@@ -202,13 +233,18 @@ def read_status(ws, stream=None) -> int:
 
 def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
          prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
-         stream=None, check: bool = True, debug_flags: int = 0, spin_limit_ns: int = 0) -> dict:
+         stream=None, check: bool = True, debug_flags: int = 0, spin_limit_ns: int = 0,
+         piv0=None, piv1=None, truncate_k: bool = False, rvalues: bool = True) -> dict:
     """Randomized QLP A ~= Q L P^T on the GPU (Algorithms 2.1, 2.2 and 4.1).
 
     A: (m, n) float64/float32 CUDA tensor, row-major.  Omega: (n, k + p)
-    float64 CUDA tensor.  Returns a dict with Q, L, P, Lvalues, piv0, piv1,
-    status (and ws, for reuse).  With check=True the stream is synchronized
-    and a device-side error raises RqlpError.
+    float64 CUDA tensor.  Returns a dict with Q, L, P, Lvalues, Rvalues (diag
+    R0 of the CPQR of B), piv0, piv1, status (and ws, for reuse).  With
+    check=True the stream is synchronized and a device-side error raises
+    RqlpError.  Given piv0 (and piv1 for Algorithm 2.1), int32 CUDA tensors
+    of at least k + p entries, the factorization is taken at those pivots
+    (rqlp_opts.fixed_pivots).  truncate_k returns the rank-k truncation
+    (Q m x k, L k x k, P n x k).
     """
     torch = _torch()
     m, n = A.shape
@@ -217,7 +253,16 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
     ldo = _row_major(Omega, "Omega")
     if Omega.dtype != torch.float64 or tuple(Omega.shape) != (n, l):
         raise ValueError("Omega must be float64 of shape (n, k + p)")
-    o = opts(q, d, pivot2, prec, block_b, debug_flags, spin_limit_ns)
+    fixed = piv0 is not None
+    if fixed:
+        for t, need_n in ((piv0, l), (piv1, l)):
+            if t is None:
+                if pivot2:
+                    raise ValueError("fixed pivots of Algorithm 2.1 need piv0 and piv1")
+                continue
+            if t.dtype != torch.int32 or not t.is_contiguous() or t.numel() < need_n:
+                raise ValueError("given pivots must be contiguous int32 with >= k + p entries")
+    o = opts(q, d, pivot2, prec, block_b, debug_flags, spin_limit_ns, fixed, truncate_k)
     L_ = lib()
     need = L_.rqlp_workspace_size(m, n, k, p, ctypes.byref(o))
     if need == 0:
@@ -225,18 +270,26 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
     dev = A.device
     if ws is None or ws.numel() < need:
         ws = workspace(need, dev)
+    w = k if truncate_k else l
     if out is None:
-        out = dict(Q=torch.empty((m, l), dtype=torch.float64, device=dev),
-                   L=torch.empty((l, l), dtype=torch.float64, device=dev),
-                   P=torch.empty((n, l), dtype=torch.float64, device=dev),
-                   Lvalues=torch.empty((l,), dtype=torch.float64, device=dev),
+        out = dict(Q=torch.empty((m, w), dtype=torch.float64, device=dev),
+                   L=torch.empty((w, w), dtype=torch.float64, device=dev),
+                   P=torch.empty((n, w), dtype=torch.float64, device=dev),
+                   Lvalues=torch.empty((w,), dtype=torch.float64, device=dev),
                    piv0=torch.empty((n,), dtype=torch.int32, device=dev),
                    piv1=torch.empty((l,), dtype=torch.int32, device=dev))
+        if rvalues:
+            out["Rvalues"] = torch.empty((w,), dtype=torch.float64, device=dev)
+    if fixed:
+        out["piv0"], out["piv1"] = piv0, piv1
     st = _stream(stream)
     code = L_.rqlp(_ptr(A), _dtype_code(A), m, n, lda, k, p, _ptr(Omega), ldo, ctypes.byref(o),
                    _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]), _ptr(out["Lvalues"]),
-                   _ptr(out["piv0"]), _ptr(out["piv1"]), _ptr(ws), ws.numel(), st)
+                   _ptr(out["piv0"]), _ptr(out.get("piv1")), _ptr(ws), ws.numel(), st)
     _check(code, "rqlp")
+    if out.get("Rvalues") is not None:
+        _check(L_.rqlp_rvalues(_ptr(ws), m, n, k, p, ctypes.byref(o), _ptr(out["Rvalues"]), st),
+               "rqlp_rvalues")
     res = dict(out)
     res["ws"] = ws
     if check:
@@ -498,9 +551,12 @@ class Batch:
 
 
 # ----------------------------------------------------------------- adjoint
-def vjp(A, k, p, Omega, dQ=None, dL=None, dP=None, q=0, prec="fp64", ws=None, stream=None):
+def vjp(A, k, p, Omega, dQ=None, dL=None, dP=None, q=0, prec="fp64", ws=None, stream=None,
+        piv0=None, piv1=None):
     """dA = J^T (dQ, dL, dP) of A -> (Q, L, P) for RQLP (Algorithm 2.1) with
-    fixed pivots, computed on the GPU (FP64 sweep, forward recomputed)."""
+    fixed pivots, computed on the GPU (FP64 sweep, forward recomputed).  piv0
+    / piv1 (int32 CUDA tensors, >= k + p entries each): the forward call's
+    pivots, held fixed; None recomputes them from A."""
     torch = _torch()
     m, n = A.shape
     o = opts(q, 1, True, prec)
@@ -513,10 +569,18 @@ def vjp(A, k, p, Omega, dQ=None, dL=None, dP=None, q=0, prec="fp64", ws=None, st
     dA = torch.empty((m, n), dtype=torch.float64, device=A.device)
     cont = lambda t: None if t is None else t.detach().to(torch.float64).contiguous()
     dQ, dL, dP = cont(dQ), cont(dL), cont(dP)
+    if (piv0 is None) != (piv1 is None):
+        raise ValueError("give both pivot arrays or neither")
+    if piv0 is not None:
+        piv0 = piv0.to(torch.int32).contiguous()
+        piv1 = piv1.to(torch.int32).contiguous()
+        if piv0.numel() < k + p or piv1.numel() < k + p:
+            raise ValueError("pivot arrays need >= k + p entries")
     st = _stream(stream)
     _check(L_.rqlp_backward(_ptr(A), _dtype_code(A), m, n, _row_major(A, "A"), k, p, _ptr(Omega),
-                            _row_major(Omega, "Omega"), ctypes.byref(o), _ptr(dQ), _ptr(dL),
-                            _ptr(dP), _ptr(dA), n, _ptr(ws), ws.numel(), st), "rqlp_backward")
+                            _row_major(Omega, "Omega"), ctypes.byref(o), _ptr(piv0), _ptr(piv1),
+                            _ptr(dQ), _ptr(dL), _ptr(dP), _ptr(dA), n, _ptr(ws), ws.numel(), st),
+           "rqlp_backward")
     _check(L_.rqlp_read_status(_ptr(ws), st), "rqlp_backward (device status)")
     return dA
 
@@ -529,16 +593,18 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, A, Omega, k, p, q, prec):
-            out = rqlp(A.detach(), k, p, Omega, q=q, pivot2=True, prec=prec)
-            ctx.save_for_backward(A, Omega)
+            out = rqlp(A.detach(), k, p, Omega, q=q, pivot2=True, prec=prec, rvalues=False)
+            # the backward sweep recomputes the forward at these pivots, so the
+            # derivative belongs to the factorization returned here
+            ctx.save_for_backward(A, Omega, out["piv0"], out["piv1"])
             ctx.cfg = (k, p, q, prec)
             return out["Q"], out["L"], out["P"]
 
         @staticmethod
         def backward(ctx, dQ, dL, dP):
-            A, Omega = ctx.saved_tensors
+            A, Omega, piv0, piv1 = ctx.saved_tensors
             k, p, q, prec = ctx.cfg
-            dA = vjp(A.detach(), k, p, Omega, dQ, dL, dP, q=q, prec=prec)
+            dA = vjp(A.detach(), k, p, Omega, dQ, dL, dP, q=q, prec=prec, piv0=piv0, piv1=piv1)
             return dA.to(A.dtype), None, None, None, None, None
 
     return RQLPFunction

@@ -67,3 +67,24 @@ def test_precision_names_match_the_header(lib):
     # those of the BF16 pair; FP64 keeps no copies of A
     assert sizes["tf32x3"] > sizes["bf16x3"] > sizes["bf16"] > sizes["fp64"]
     assert sizes["tf32"] > sizes["bf16"]
+
+
+def test_new_options_are_checked(lib):
+    # fixed pivots and truncation are 0/1 switches; fixed pivots need the
+    # pivot arrays and are not offered for the blocked form
+    o = R.opts(fixed_pivots=True, truncate_k=True)
+    assert lib.rqlp_workspace_size(100, 50, 5, 5, ctypes.byref(o)) > \
+        lib.rqlp_workspace_size(100, 50, 5, 5, ctypes.byref(R.opts()))
+    o.truncate_k = 2
+    assert lib.rqlp_workspace_size(100, 50, 5, 5, ctypes.byref(o)) == 0
+    o = R.opts(fixed_pivots=True)
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the call fails on its arguments
+    code = lib.rqlp(dummy, 0, 100, 50, 50, 5, 5, dummy, 10, ctypes.byref(o), dummy, dummy, dummy,
+                    None, None, None, dummy, 1 << 20, None)
+    assert code == -1
+    o = R.opts(fixed_pivots=True, block_b=5)
+    code = lib.rqlp(dummy, 0, 100, 50, 50, 5, 5, dummy, 10, ctypes.byref(o), dummy, dummy, dummy,
+                    None, dummy, dummy, dummy, 1 << 20, None)
+    assert code == -7
+    assert lib.rqlp_backward_workspace_size(100, 50, 5, 5, ctypes.byref(R.opts(truncate_k=True))) == 0
+    assert lib.rqlp_version() >= 200

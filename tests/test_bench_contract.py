@@ -29,7 +29,8 @@ def test_reference_arm_prints_one_contract_line():
 def test_stage_roofline_arithmetic():
     sys.path.insert(0, ROOT)
     import bench
-    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1600.0}
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1600.0,
+             "fp64_tflops": 1.0}
     m = n = 8192
     l, q, d = 110, 1, 2
     work = bench._class_work(m, n, l, q, d, "bf16x3")
@@ -47,6 +48,11 @@ def test_stage_roofline_arithmetic():
     cp = sr["cpqr_of_B"]
     assert cp["bound"] == "alu"
     assert abs(cp["achieved_tflops"] - 2.0 * n * l * (l + 1) / 1e-3 / 1e12) < 1e-9
+    assert abs(cp["frac"] - cp["achieved_tflops"] / 1.0) < 1e-12  # the measured FP64 rate
+    # the assembly at d <= 2 is the product Q = V Q_B only (P is a row scatter)
+    assert abs(sr["assembly"]["achieved_tflops"] - 2.0 * m * l * l / 1e-3 / 1e12) < 1e-9
+    sr3 = bench._stage_roofline("bf16x3", m, n, l, q, 3, prof, 1, peaks)
+    assert abs(sr3["assembly"]["achieved_tflops"] - 2.0 * (m + n) * l * l / 1e-3 / 1e12) < 1e-9
     # TF32x3: twice the bytes, half the tensor rate
     sr32 = bench._stage_roofline("tf32x3", m, n, l, q, d, prof, 1, peaks)
     assert abs(sr32["products_with_A"]["achieved_gbs"] - 2 * pa["achieved_gbs"]) < 1e-6

@@ -329,3 +329,56 @@ def test_paper_tables_1_2_order_of_magnitude():
         for key in ("RQLP", "QLP"):
             ratio = err[key] / row[key]
             assert 0.2 <= ratio <= 5.0, (row["kind"], key, err[key], row[key])
+
+
+# ---------------------------------------------------------- fixed pivots, R-values
+def test_complete_perm_closed_form():
+    assert list(R.complete_perm([4, 1], 6)) == [4, 1, 0, 2, 3, 5]
+    assert list(R.complete_perm([], 3)) == [0, 1, 2]
+    for bad in ([1, 1], [6], [-1]):
+        with pytest.raises(ValueError):
+            R.complete_perm(bad, 6)
+
+
+@pytest.mark.parametrize("pivot2,d", [(True, 1), (False, 2), (False, 3)])
+def test_fixed_pivots_equal_the_chosen_ones(pivot2, d):
+    # given the pivots the CPQRs chose, the unpivoted QRs of the permuted
+    # matrices are the same factorization (the QR with non-negative diagonal
+    # is unique)
+    A, _ = _decaying(120, 90, 41, decay=0.85)
+    Om = _rand((90, 20), 42)
+    ref = R.rqlp(A, 15, 5, Om, q=1, d=d, pivot2=pivot2)
+    fix = R.rqlp(A, 15, 5, Om, q=1, d=d, pivot2=pivot2, piv0=ref["piv0"][:20],
+                 piv1=ref["piv1"] if pivot2 else None)
+    for key in ("Q", "L", "P", "Lvalues"):
+        assert np.allclose(fix[key], ref[key], rtol=0, atol=1e-13), key
+    assert np.array_equal(fix["piv0"], ref["piv0"])
+
+
+def test_fixed_pivots_in_another_order_match_lapack_qr():
+    # any given column order: R0[:, :l] is LAPACK's QR (sign-fixed) of the
+    # chosen columns, and B = Q_B T P_B^T still holds with orthonormal factors
+    B = _rand((12, 40), 43) * (0.9 ** np.arange(40))[None, :]
+    piv0 = [7, 3, 30, 0, 11, 25, 2, 39, 14, 5, 21, 33]
+    piv1 = [3, 0, 11, 1, 2, 10, 4, 9, 5, 8, 6, 7]
+    f = R.qlp_of_B(B, pivot2=True, piv0=piv0, piv1=piv1)
+    assert list(f["piv0"][:12]) == piv0 and list(f["piv1"]) == piv1
+    Ql, Rl = np.linalg.qr(B[:, piv0])
+    s = np.where(np.diag(Rl) < 0, -1.0, 1.0)
+    assert np.allclose(f["R0"][:, :12], Rl * s[:, None], atol=1e-13)
+    assert np.allclose(f["QB"] @ f["T"] @ f["PB"].T, B, atol=1e-13)
+    assert np.allclose(f["PB"].T @ f["PB"], np.eye(12), atol=1e-13)
+    assert np.allclose(np.triu(f["T"], 1), 0.0)
+
+
+def test_rvalues_are_lapack_pivoted_qr_diagonal():
+    A, _ = _decaying(150, 100, 44, decay=0.8)
+    Om = _rand((100, 25), 45)
+    out = R.rqlp(A, 20, 5, Om, q=0, d=2, pivot2=False)
+    _, Rl, pl = sla.qr(out["B"], pivoting=True, mode="economic")  # LAPACK dgeqp3
+    assert np.array_equal(pl[:25], out["piv0"][:25])
+    assert np.allclose(out["Rvalues"], np.abs(np.diag(Rl)), rtol=1e-12)
+    # truncation to k keeps the leading k columns
+    t = R.truncate(out, 20)
+    assert t["Q"].shape == (150, 20) and t["L"].shape == (20, 20) and t["P"].shape == (100, 20)
+    assert np.array_equal(t["Lvalues"], out["Lvalues"][:20])

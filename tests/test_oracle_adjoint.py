@@ -86,3 +86,29 @@ def test_sum_of_lvalues_gradient_entrywise():
         fp = np.trace(O.rqlp_trace(Ap, k, p, Om, 1, base["piv0"], base["piv1"])["L"][:k, :k])
         fm = np.trace(O.rqlp_trace(Am, k, p, Om, 1, base["piv0"], base["piv1"])["L"][:k, :k])
         assert abs((fp - fm) / (2 * h) - dA[i, j]) <= 1e-6 * max(1.0, abs(dA[i, j]))
+
+
+def test_rqlp_vjp_at_given_pivots_matches_finite_differences():
+    # pivots that the CPQRs would not choose (two pivots swapped in each QR):
+    # the sweep is the derivative of the factorization at those pivots
+    m, n, k, p = 50, 30, 5, 3
+    A = W.gaussian(m, n, 12) * (2.0 ** (-np.arange(n) / 6.0))[None, :]
+    Om = W.omega(n, k + p, 2)
+    base = O.rqlp_trace(A, k, p, Om, 1)
+    piv0 = base["piv0"].copy()
+    piv0[[1, 4]] = piv0[[4, 1]]
+    piv1 = base["piv1"].copy()
+    piv1[[0, 2]] = piv1[[2, 0]]
+    rng = np.random.default_rng(21)
+    l = k + p
+    cQ, cL, cP = rng.standard_normal((m, l)), rng.standard_normal((l, l)), rng.standard_normal((n, l))
+    E = rng.standard_normal((m, n))
+    h = 1e-6
+    fp = _f(O.rqlp_trace(A + h * E, k, p, Om, 1, piv0, piv1), cQ, cL, cP)
+    fm = _f(O.rqlp_trace(A - h * E, k, p, Om, 1, piv0, piv1), cQ, cL, cP)
+    fd = (fp - fm) / (2 * h)
+    dA = O.rqlp_vjp(A, k, p, Om, cQ, np.tril(cL), cP, q=1, piv0=piv0[:l], piv1=piv1)
+    assert abs(fd - np.sum(dA * E)) <= 1e-6 * max(1.0, abs(fd)), (fd, np.sum(dA * E))
+    # and it differs from the derivative at the chosen pivots
+    dA0 = O.rqlp_vjp(A, k, p, Om, cQ, np.tril(cL), cP, q=1)
+    assert np.linalg.norm(dA - dA0) > 1e-3 * np.linalg.norm(dA0)
