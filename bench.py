@@ -155,14 +155,24 @@ def _class_work(m, n, l, q, d, prec):
     Products with A: 2q + 2 passes of 2 m n l flops, reading A once per pass
     (8 bytes per element in FP64 and for the TF32 pair, 4 for the BF16 pair and
     TF32, 2 for BF16, 1 for E4M3).
-    CholeskyQR on an N x l panel, per pass: Gram N l^2 flops (symmetric),
-    X R^-1 N l^2 flops (triangular) plus the l^3 / 3 R update, Cholesky and
-    triangular inverse l^3 / 3 each; two passes.  CPQR of B: step s updates the
-    n - s trailing columns over l - s rows with a dot product and an axpy
-    (4 flops per entry), 4 n l (l + 1) / 2 = 2 n l (l + 1) in all.
+    CholeskyQR on an N x l panel, per FP64 pass: Gram N l^2 flops
+    (symmetric), X R^-1 N l^2 flops (triangular) plus the l^3 / 3 R update,
+    Cholesky and triangular inverse l^3 / 3 each.  The passes that run: one per
+    power-step basis (m and n rows, q times), two (CholeskyQR2) for the final
+    basis V (m rows), for R0^T (n rows) and for each of the d - 1 inner l x l
+    QRs.  In the mixed forms the power steps' passes run in FP32 (about 1e8
+    flops each, microseconds at the FP32 rate, not counted) and the second
+    pass of a CholeskyQR2 runs only when eps cond(R)^2 > 1e-10, which these
+    well-conditioned bases never reach, so one FP64 pass is counted there.
+    CPQR of B: step s updates the n - s trailing columns over l - s rows with a
+    dot product and an axpy (4 flops per entry), 4 n l (l + 1) / 2 =
+    2 n l (l + 1) in all.
     """
-    rows = [m] * q + [n] * q + [m, n] + [l] * max(0, d - 1)
-    passes = 2
+    if prec == "fp64":
+        rows = [m] * q + [n] * q + 2 * ([m, n] + [l] * max(0, d - 1))
+    else:
+        rows = [m, n] + [l] * max(0, d - 1)
+    passes = 1
     a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0, "fp8": 1.0, "tf32x3": 8.0,
                "tf32": 4.0}[prec] * m * n
     prod = ("flops", (2 * q + 2) * 2.0 * m * n * l) if prec == "fp64" else \

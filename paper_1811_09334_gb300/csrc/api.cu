@@ -918,6 +918,9 @@ int run_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   double *part = F.ob.part;
   const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
   CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  // the recomputed forward's products with A run in the forward's precision,
+  // so the mixed forms need their copies of A
+  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(F.mx, o.prec, A, a_dtype, m, n, lda, st));
   // ---- forward with intermediates (Algorithm 2.1) ----
   int site = 0;
   RET(prod_nn(F, o, A, a_dtype, m, n, lda, Omega, ldo, l, F.Y, st));

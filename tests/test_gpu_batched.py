@@ -91,3 +91,60 @@ def test_autotuner_picks_and_caches(R, tmp_path, monkeypatch):
     assert (tmp_path / "tune.json").exists()
     t2 = autotune.tune(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec="bf16x3", sample=12)
     assert t1 == t2
+
+
+def _check_against_oracle(prec, out, ref, l, where):
+    lv = out["Lvalues"].cpu().numpy()
+    keep = ref["Lvalues"] >= 1e-3 * ref["Lvalues"].max()
+    if prec == "fp64":
+        rel = np.abs(lv - ref["Lvalues"]) / np.abs(ref["Lvalues"])
+        assert rel.max() <= 1e-10, (where, rel.max())
+        assert np.array_equal(out["piv0"].cpu().numpy()[:l], ref["piv0"][:l]), where
+        Q = out["Q"].cpu().numpy()
+        assert np.abs(Q - ref["Q"]).max() <= 1e-9, where
+        return
+    # index-wise while the pivots agree, then the pivot-free singular values of L
+    pg = out["piv0"].cpu().numpy()[:l]
+    diff = np.nonzero(pg != ref["piv0"][:l])[0]
+    t = int(diff[0]) if diff.size else l
+    kt = keep[:t]
+    if kt.any():
+        rel = np.abs(lv[:t] - ref["Lvalues"][:t])[kt] / ref["Lvalues"][:t][kt]
+        assert rel.max() <= 1e-3, (where, t, rel.max())
+    sg = np.linalg.svd(out["L"].cpu().numpy(), compute_uv=False)
+    so = np.linalg.svd(ref["L"], compute_uv=False)
+    k2 = so >= 1e-3 * so[0]
+    assert (np.abs(sg - so)[k2] / so[k2]).max() <= 1e-3, where
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+def test_full_512_problem_batch_sampled_against_the_oracle(R, prec, tmp_path, monkeypatch):
+    """The whole 512-problem workload (m ~ U[256, 4096], n ~ U[128, m],
+    k ~ U[8, 64], p = 8, ERQLP q = 1, d = 2) in the launch configuration the
+    benchmark times (autotuned shapes, one graph launch), with a seeded
+    sample of 20 problems and the 4 largest compared with the FP64 oracle."""
+    from paper_1811_09334_gb300 import autotune
+    monkeypatch.setenv("RQLP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    shapes = W.c5_shapes()
+    As, ks, Oms = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, _ = W.c5_matrix(i, m, n, device="cuda", fast=True)
+        As.append(A)
+        ks.append(k)
+        Oms.append(torch.from_numpy(W.omega(n, k + 8, i)).cuda())
+    torch.cuda.synchronize()
+    tune = autotune.tune(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, sample=128)
+    b = R.Batch(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, **tune)
+    b.launch()
+    worst, st = b.status()
+    assert worst >= 0 and all(s >= 0 for s in st)
+    cost = [m * n * (k + 8) for (m, n, k) in shapes]
+    largest = sorted(range(len(shapes)), key=lambda i: -cost[i])[:4]
+    rng = np.random.default_rng(512)
+    sample = sorted(set(largest) | set(int(i) for i in rng.choice(len(shapes), 20, replace=False)))
+    for i in sample:
+        m, n, k = shapes[i]
+        ref = O.rqlp(As[i].cpu().numpy(), k, 8, Oms[i].cpu().numpy(), q=1, d=2, pivot2=False)
+        _check_against_oracle(prec, b.out[i], ref, k + 8, (i, m, n, k))
+    b.close()

@@ -221,15 +221,28 @@ def test_host_async_two_streams_match_device_path(R):
             assert torch.equal(sl[key], v), (i, key)
 
 
-@pytest.mark.slow
-def test_c2_full_size_fp64_parity(R):
-    """The 8192 x 8192 ERQLP workload (q = 1, d = 2) in the launch configuration
-    the benchmark times, against the oracle run on the same matrix."""
+@pytest.fixture(scope="module")
+def c2_full():
     pr = W.c2(device=DEV)
-    Om = W.omega(pr.n, pr.l, 0)
-    out = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=1, d=2, pivot2=False)
-    ref = O.rqlp(pr.A.cpu().numpy(), pr.k, pr.p, Om, q=1, d=2, pivot2=False)
+    return pr, pr.A.cpu().numpy(), W.omega(pr.n, pr.l, 0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("q", [1, 2])
+def test_c2_full_size_fp64_parity(R, c2_full, q):
+    """The 8192 x 8192 ERQLP workload (q = 1 and 2, d = 2) in the launch
+    configuration the benchmark times, against the oracle run on the same matrix."""
+    pr, A_np, Om = c2_full
+    out = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=q, d=2, pivot2=False)
+    ref = O.rqlp(A_np, pr.k, pr.p, Om, q=q, d=2, pivot2=False)
     _compare(out, ref, pr.l)
+    if q == 2:
+        # the same matrix in BF16x3 at q = 2: pivots identical, L-values to 1e-3
+        mx = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=q, d=2, pivot2=False, prec="bf16x3")
+        assert np.array_equal(mx["piv0"].cpu().numpy()[:pr.l], ref["piv0"][:pr.l])
+        lv = mx["Lvalues"].cpu().numpy()
+        keep = ref["Lvalues"] >= 1e-3 * ref["Lvalues"][0]
+        assert (np.abs(lv - ref["Lvalues"])[keep] / ref["Lvalues"][keep]).max() <= 1e-3
 
 
 # ------------------------------------------------------------------ BRQLP

@@ -1,10 +1,11 @@
 """The remaining workloads at full size, against the FP64 oracle.
 
 * 32768 x 16384 low rank plus noise, FP32 storage, k = 200, p = 10, q = 2,
-  d = 2, BF16x3 and BF16 products: L-values compared index-wise up to the
-  first pivot divergence (the plateau of noise-level singular values makes
-  later pivots precision-dependent) and through sigma(L) for
-  sigma_j / sigma_1 >= 1e-3, at the tolerances of the mixed forms.
+  d = 2, BF16x3, BF16 and E4M3 products: L-values compared index-wise up to
+  the first pivot divergence (the plateau of noise-level singular values
+  makes later pivots precision-dependent) and through sigma(L) for
+  sigma_j / sigma_1 >= 1e-3, at the tolerances of the mixed forms (E4M3:
+  0.15, its 2^-4 unit roundoff per operand).
 * The paper's pds / eds matrices of Example 5.1 (n = 2000, k = 120, p = 5):
   FP64 RQLP and ERQLP (d = 2, 4) at the FP64 parity tolerance, and the
   Section 5 error err = max_j |sigma_j - L_jj| equal to the oracle's.
@@ -38,7 +39,7 @@ def c3():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-3), ("bf16", 2e-2), ("fp8", 0.15)])
 def test_large_low_rank_plus_noise(R, c3, prec, tol):
     pr, Om, ref = c3
     out = R.rqlp(pr.A, pr.k, pr.p, torch.from_numpy(Om).cuda(), q=2, d=2, pivot2=False, prec=prec)
@@ -54,7 +55,10 @@ def test_large_low_rank_plus_noise(R, c3, prec, tol):
     sg = np.linalg.svd(out["L"].cpu().numpy(), compute_uv=False)
     so = np.linalg.svd(ref["L"], compute_uv=False)
     k2 = so >= 1e-3 * so[0]
-    assert (np.abs(sg - so)[k2] / so[k2]).max() <= tol
+    err = (np.abs(sg - so)[k2] / so[k2]).max()
+    # the measured figure, for the record (the E4M3 form's is a statement, not a claim)
+    print("\n%s sigma(L) max rel err %.3e, pivots identical through step %d" % (prec, err, t))
+    assert err <= tol
     if prec == "bf16x3":
         assert t >= 30  # the signal part (sigma_j ~ 1/j above the noise) pivots identically
     Q = out["Q"].cpu().numpy()
