@@ -254,6 +254,28 @@ def _lvalue_err(gpu_out, ref):
             "pivots_match": piv_ok}
 
 
+def _lvalue_err_np(host, ref, sigma_floor=1e-3):
+    """L-value error of a factorization kept on the host (L, Lvalues, piv0)
+    against the oracle's: index-wise relative error for L-values at or above
+    sigma_floor times the largest, up to the first pivot that differs, the
+    step of that first difference, and the relative error of sigma(L)."""
+    import numpy as np
+    lg, lr = host["Lvalues"], ref["Lvalues"]
+    l = len(lr)
+    pg = host["piv0"][:l]
+    diff = np.nonzero(pg != ref["piv0"][:l])[0]
+    t = int(diff[0]) if diff.size else l
+    keep = np.abs(lr) >= sigma_floor * np.abs(lr).max()
+    idx = np.arange(l) < t
+    rel = np.abs(lg - lr) / np.abs(lr)
+    sg = np.linalg.svd(host["L"], compute_uv=False)
+    so = np.linalg.svd(ref["L"], compute_uv=False)
+    k2 = so >= sigma_floor * so[0]
+    return {"max_rel_while_pivots_agree": float(rel[keep & idx].max()) if (keep & idx).any() else None,
+            "pivots_identical_through": t,
+            "sigma_L_max_rel": float((np.abs(sg - so)[k2] / so[k2]).max())}
+
+
 def _run_batched(R, dev, count=512):
     """The 512-problem batch (ERQLP q = 1, d = 2): one graph launch per step.
 
@@ -345,64 +367,264 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _run_extra(R, W, torch, A, steps):
-    """Rows of the method beside the headline, timed with CUDA events on the
-    current stream after two untimed runs: BRQLP (Algorithm 4.1) on the same
-    8192 x 8192 matrix with blocks of l / 5 = 22 columns, in BF16x3 and FP64,
-    and the adjoint on the 4096 x 2048 FP32 differentiable workload (q = 1,
-    cotangent on sum_{j<k} L_jj; each call recomputes the forward factorization
-    and reads the device status).  A failure is reported in the line instead
-    of ending the run."""
-    out = {}
+def _worse(a, b):
+    """The worse of two statuses: an error over a warning over RQLP_OK."""
+    if a < 0 or b == 0:
+        return a
+    if b < 0 or a == 0:
+        return b
+    return a
+
+
+def _timed(torch, fn, reps, warm=2):
+    """Mean ms per call of fn over `reps` calls, CUDA events on the current
+    stream, after `warm` untimed calls."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _host_result(out):
+    return {k: out[k].detach().cpu().numpy() for k in ("L", "Lvalues", "piv0") if k in out}
+
+
+def _run_extra(R, W, torch, A, steps, peaks):
+    """Rows of the method beside the headline, each timed with CUDA events on
+    the current stream after two untimed runs whose device status is read (the
+    worst status seen is reported); a failure is reported in the line instead
+    of ending the run:
+    * BRQLP (Algorithm 4.1) on the same 8192 x 8192 matrix with blocks of l/5
+      = 22 and l/2 = 55 columns, BF16x3 and FP64;
+    * the adjoint on the 4096 x 2048 FP32 differentiable workload (q = 1,
+      cotangent on sum_{j<k} L_jj; each call recomputes the forward);
+    * the 8192 x 8192 workload at q = 2 (BF16x3, FP64);
+    * the 32768 x 16384 FP32 low-rank-plus-noise workload (k = 200, p = 10,
+      q = 2, d = 2) in BF16, E4M3 and BF16x3, with the products' executed
+      tensor-core rate against the sustained BF16 peak scaled to the dtype and
+      the attainable fraction min(1, l BW / peak) of a pass that streams A
+      once (the skinny products are HBM-bound);
+    * the paper-shaped pds / eds matrices of Example 5.1 (m = n in {2000,
+      4000, 6000}, k = 120, p = 5, q = 0), RQLP and ERQLP d = 2, 4 in FP64, with
+      the Section 5 error of the L-values and of the R-values beside the
+      paper's Tables 1-2 (an i5-7500 in MATLAB: context only).
+    Returns (extra, held): `held` keeps host copies of the factorizations
+    whose error against the oracle the CPU-baseline leg computes."""
+    import numpy as np
+    out, held = {}, {}
     dev = A.device
-
-    def timed(fn, reps):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
     reps = max(1, min(steps, 5))
+
+    def run_status(fn):
+        worst = 0
+        for _ in range(2):
+            r = fn()
+            worst = _worse(worst, R.read_status(r["ws"]))
+        return worst
+
     l = K_RANK + P_OVER
-    b = l // 5
     Om = torch.from_numpy(W.omega(A.shape[1], l, 0)).to(dev)
-    for form in ("bf16x3", "fp64"):
-        key = "brqlp_b%d_%s" % (b, form)
-        try:
-            held = {}
+    for b in (l // 5, l // 2):
+        for form in ("bf16x3", "fp64"):
+            key = "brqlp_b%d_%s" % (b, form)
+            try:
+                keep = {}
 
-            def run():
-                r = R.rqlp(A, K_RANK, P_OVER, Om, q=0, pivot2=True, block_b=b, prec=form,
-                           ws=held.get("ws"), check=False)
-                held["ws"] = r["ws"]
+                def run():
+                    r = R.rqlp(A, K_RANK, P_OVER, Om, q=0, pivot2=True, block_b=b, prec=form,
+                               ws=keep.get("ws"), check=False, rvalues=False)
+                    keep["ws"] = r["ws"]
+                    return r
 
-            ms = timed(run, reps)
-            status = R.lib().rqlp_read_status(R._ptr(held["ws"]), R._stream(None))
-            out[key] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "status": int(status),
-                        "workload": "%dx%d, k = %d, p = %d, blocks of %d" % (
-                            A.shape[0], A.shape[1], K_RANK, P_OVER, b)}
-        except Exception as e:  # reported, not raised
-            out[key] = {"error": repr(e)[:300]}
+                worst = run_status(run)
+                ms = _timed(torch, run, reps, warm=0)
+                worst = _worse(worst, R.read_status(keep["ws"]))
+                out[key] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "worst_status": int(worst),
+                            "workload": "%dx%d, k = %d, p = %d, blocks of %d" % (
+                                A.shape[0], A.shape[1], K_RANK, P_OVER, b)}
+            except Exception as e:  # reported, not raised
+                out[key] = {"error": repr(e)[:300]}
     try:
         pr4 = W.c4(device=str(dev))
         l4 = pr4.k + pr4.p
         Om4 = torch.from_numpy(W.omega(pr4.n, l4, 0)).to(dev)
         dL = torch.diag(torch.tensor([1.0] * pr4.k + [0.0] * pr4.p, dtype=torch.float64,
                                      device=dev))
-        ms = timed(lambda: R.vjp(pr4.A, pr4.k, pr4.p, Om4, dL=dL, q=1), reps)
+        ms = _timed(torch, lambda: R.vjp(pr4.A, pr4.k, pr4.p, Om4, dL=dL, q=1), reps)
         out["adjoint_c4"] = {"vjp_per_s": 1e3 / ms, "ms": ms,
                              "workload": "%dx%d FP32, k = %d, p = %d, q = 1" % (
                                  pr4.m, pr4.n, pr4.k, pr4.p)}
     except Exception as e:  # reported, not raised
         out["adjoint_c4"] = {"error": repr(e)[:300]}
-    return out
+    # the 8192 x 8192 workload at q = 2
+    for form in ("bf16x3", "fp64"):
+        key = "c2_q2_%s" % form
+        try:
+            keep = {}
+
+            def run2():
+                r = R.rqlp(A, K_RANK, P_OVER, Om, q=2, d=D_INNER, pivot2=False, prec=form,
+                           ws=keep.get("ws"), check=False, rvalues=False)
+                keep["ws"] = r["ws"]
+                keep["out"] = r
+                return r
+
+            worst = run_status(run2)
+            ms = _timed(torch, run2, 3 if form == "fp64" else reps, warm=0)
+            out[key] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "worst_status": int(worst),
+                        "workload": "%dx%d, k = %d, p = %d, q = 2, d = %d" % (
+                            A.shape[0], A.shape[1], K_RANK, P_OVER, D_INNER)}
+            held[key] = _host_result(keep["out"])
+        except Exception as e:  # reported, not raised
+            out[key] = {"error": repr(e)[:300]}
+    # the 32768 x 16384 workload
+    try:
+        pr3 = W.c3(device=str(dev))
+        l3 = pr3.l
+        Om3 = torch.from_numpy(W.omega(pr3.n, l3, 0)).to(dev)
+        torch.cuda.synchronize()
+        c3 = {"workload": "%dx%d FP32 low rank + noise, k = %d, p = %d, q = 2, d = 2" % (
+            pr3.m, pr3.n, pr3.k, pr3.p)}
+        elem = float(pr3.m) * pr3.n
+        for form, ebytes, ratio, nprod in (("bf16", 2.0, 1.0, 1), ("fp8", 1.0, 2.0, 1),
+                                           ("bf16x3", 4.0, 1.0, 3)):
+            try:
+                keep = {}
+
+                def run3():
+                    r = R.rqlp(pr3.A, pr3.k, pr3.p, Om3, q=2, d=2, pivot2=False, prec=form,
+                               ws=keep.get("ws"), check=False, rvalues=False)
+                    keep["ws"] = r["ws"]
+                    keep["out"] = r
+                    return r
+
+                worst = run_status(run3)
+                ms = _timed(torch, run3, 3, warm=0)
+                R.profile_begin()
+                for _ in range(2):
+                    run3()
+                prof = R.profile_end()
+                pms = prof["products_with_A"][0] / 2
+                passes = 6  # 2q + 2
+                tc = nprod * passes * 2.0 * elem * l3 / (pms / 1e3) / 1e12
+                tpeak = peaks["bf16_tflops_sustained"] * ratio
+                gbs = passes * ebytes * elem / (pms / 1e3) / 1e9
+                # one pass streams A once: l flops per element per byte-of-A-size,
+                # so the tensor rate is capped at (l / bytes per element) x BW
+                cap = min(1.0, (l3 * 2.0 / ebytes) * peaks["hbm_gbs"] / 1e3 / tpeak)
+                c3[form] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "worst_status": int(worst),
+                            "products_ms": pms, "products_tensor_tflops": tc,
+                            "products_tensor_frac": tc / tpeak,
+                            "tensor_frac_cap_hbm": cap, "products_hbm_gbs": gbs,
+                            "products_hbm_frac": gbs / peaks["hbm_gbs"],
+                            "stage_ms": {k: v[0] / 2 for k, v in prof.items()}}
+                held["c3_" + form] = _host_result(keep["out"])
+                del keep
+            except Exception as e:  # reported, not raised
+                c3[form] = {"error": repr(e)[:300]}
+        out["c3"] = c3
+        held["c3_problem"] = (pr3, Om3.cpu().numpy())
+    except Exception as e:  # reported, not raised
+        out["c3"] = {"error": repr(e)[:300]}
+    torch.cuda.empty_cache()
+    # Example 5.1 / Tables 1-2 shaped lines
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as f:
+            tab = json.load(f)
+        rows = []
+        for row in tab["rows"]:
+            pr6 = W.w6(row["kind"], row["n"], t=tab["t"], s=row["s"], device=str(dev))
+            Om6 = torch.from_numpy(W.omega(pr6.n, pr6.l, 0)).to(dev)
+            ent = {"kind": row["kind"], "n": row["n"], "paper_table": row["table"]}
+            for name, piv2, d in (("RQLP", True, 1), ("ERQLP_d2", False, 2), ("ERQLP_d4", False, 4)):
+                keep = {}
+
+                def run6():
+                    r = R.rqlp(pr6.A, pr6.k, pr6.p, Om6, q=0, d=d, pivot2=piv2, ws=keep.get("ws"),
+                               check=False)
+                    keep["ws"] = r["ws"]
+                    keep["out"] = r
+                    return r
+
+                ms = _timed(torch, run6, 3)
+                st = R.read_status(keep["ws"])
+                lv = keep["out"]["Lvalues"].cpu().numpy()
+                rv = keep["out"]["Rvalues"].cpu().numpy()
+                k6 = pr6.k
+                sig = pr6.sigma[:k6]
+                ent[name] = {"ms": ms, "status": int(st),
+                             "err_L": float(np.max(np.abs(sig - np.abs(lv[:k6])))),
+                             "err_R": float(np.max(np.abs(sig - np.abs(rv[:k6])))),
+                             "mean_rel_L": float(np.mean(np.abs(sig - lv[:k6]) / sig)),
+                             "mean_rel_R": float(np.mean(np.abs(sig - rv[:k6]) / sig)),
+                             "paper_err": row[name],
+                             "paper_T_s": row.get("T_%s_s" % name)}
+            rows.append(ent)
+            del pr6
+        out["w6_paper_shaped"] = {
+            "workload": "Example 5.1 pds (t = 30, s = 2) / eds (t = 30, s = 1/20), m = n, k = 120, "
+                        "p = 5, q = 0, FP64; err = max_{j<=k} |sigma_j - value_j| for the L-values "
+                        "and the R-values (diag R0); paper_* from Tables 1-2 (i5-7500, MATLAB, "
+                        "unseeded Omega: context only)",
+            "rows": rows}
+    except Exception as e:  # reported, not raised
+        out["w6_paper_shaped"] = {"error": repr(e)[:300]}
+    return out, held
+
+
+def _lapack_erqlp(A, k, p, Om, q, d):
+    """The same ERQLP pipeline on numpy / scipy's LAPACK (FP64, all host
+    cores): the tuned-CPU context line (the analogue of the paper's MATLAB
+    built-ins), not the oracle."""
+    import numpy as np
+    import scipy.linalg as sla
+    Y = A @ Om
+    for _ in range(q):
+        V = np.linalg.qr(Y)[0]
+        Wq = np.linalg.qr(A.T @ V)[0]
+        Y = A @ Wq
+    V = np.linalg.qr(Y)[0]
+    B = V.T @ A
+    Q0, R0, piv = sla.qr(B, pivoting=True, mode="economic")
+    X = R0.T
+    for _ in range(d):
+        Qi, X = np.linalg.qr(X)
+        X = X.T
+    return np.abs(np.diag(X))
+
+
+def _oracle_one_core(A_np, Om_np, budget_s=120.0):
+    """Seconds of one oracle factorization of the workload on ONE host core
+    (a child process with single-threaded BLAS), or None past the budget."""
+    import numpy as np
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    fo, opath = tempfile.mkstemp(suffix=".npy")
+    os.close(fo)
+    try:
+        np.save(path, A_np)
+        np.save(opath, Om_np)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1")
+        code = ("import sys, time, numpy as np; sys.path.insert(0, %r); "
+                "from oracle import rqlp_ref as O; A = np.load(%r); Om = np.load(%r); "
+                "t = time.time(); O.rqlp(A, %d, %d, Om, q=%d, d=%d, pivot2=False); "
+                "print(time.time() - t)" % (ROOT, path, opath, K_RANK, P_OVER, Q_POW, D_INNER))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=budget_s)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+    finally:
+        os.unlink(path)
+        os.unlink(opath)
 
 
 def run_ours(args):
@@ -566,7 +788,23 @@ def run_ours(args):
     if not args.no_batched:
         batched = _run_batched(R, dev)
 
-    # CPU baseline (oracle) on rank 0 at N = 1; L-value error of each form against it
+    # the other rows of the method (GPU work only; host copies of the results
+    # whose error the CPU-baseline leg computes are kept in `held`)
+    extra, held = None, {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra, held = _run_extra(R, W, torch, A, args.steps, peaks)
+
+    # the forms not timed above: one untimed factorization each, for its error
+    for form in ("bf16", "tf32", "fp8"):
+        if form not in outs and rank == 0 and world == 1 and not args.no_cpu_baseline:
+            o = R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form,
+                       rvalues=False)
+            outs[form] = {k: v.clone() for k, v in o.items() if hasattr(v, "clone")}
+            forms_out[form] = {"timed": False}
+
+    # CPU-baseline leg (oracle) on rank 0 at N = 1: the oracle timed on all host
+    # cores and on one, the LAPACK context line, and every L-value error
+    # against the oracle
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         A_np = A.cpu().numpy()
@@ -575,20 +813,42 @@ def run_ours(args):
                "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d whole factorization(s) of the workload (numpy FP64, all host cores)"
                          % len(times)}
+        t1 = _oracle_one_core(A_np, Om_np)
+        cpu["one_core"] = {"value": (1.0 / t1) if t1 else None, "cores": 1,
+                           "sample": "1 whole factorization, single-threaded BLAS"}
+        t0 = time.time()
+        lv_lapack = _lapack_erqlp(A_np, pr.k, pr.p, Om_np, Q_POW, D_INNER)
+        tl = time.time() - t0
+        cpu["lapack_context"] = {
+            "value": 1.0 / tl, "unit": "factorizations/s", "cores": os.cpu_count(),
+            "kind": "numpy/scipy LAPACK FP64 pipeline (context, not the oracle)",
+            "lvalue_max_rel_vs_oracle": float(np.max(np.abs(lv_lapack - ref["Lvalues"]) /
+                                                     ref["Lvalues"]))}
         for form in forms_out:
             forms_out[form]["lvalue_err_vs_oracle"] = _lvalue_err(outs[form], ref)
-        # the forms not timed above: one untimed factorization each, for its error
-        for form in ("bf16", "tf32", "fp8"):
-            if form in forms_out:
-                continue
-            o = R.rqlp(A, pr.k, pr.p, Om, q=Q_POW, d=D_INNER, pivot2=False, prec=form,
-                       rvalues=False)
-            forms_out[form] = {"lvalue_err_vs_oracle": _lvalue_err(o, ref), "timed": False}
-
-    # last, once every number of the line is in host memory
-    extra = None
-    if rank == 0 and world == 1 and not args.no_extra:
-        extra = _run_extra(R, W, torch, A, args.steps)
+        del A_np, ref
+        # the extra rows' errors against the oracle on the same inputs
+        from oracle import rqlp_ref as O
+        if extra:
+            ref2 = None
+            for form in ("bf16x3", "fp64"):
+                key = "c2_q2_" + form
+                if key in held:
+                    if ref2 is None:
+                        ref2 = O.rqlp(A.cpu().numpy(), pr.k, pr.p, Om_np, q=2, d=D_INNER,
+                                      pivot2=False)
+                    extra[key]["lvalue_err_vs_oracle"] = _lvalue_err_np(held[key], ref2)
+            if "c3_problem" in held:
+                pr3, Om3 = held.pop("c3_problem")
+                A3 = pr3.A.double().cpu().numpy()
+                del pr3
+                torch.cuda.empty_cache()
+                ref3 = O.rqlp(A3, 200, 10, Om3, q=2, d=2, pivot2=False)
+                del A3
+                for form in ("bf16", "fp8", "bf16x3"):
+                    if "c3_" + form in held and isinstance(extra["c3"].get(form), dict):
+                        extra["c3"][form]["lvalue_err_vs_oracle"] = _lvalue_err_np(
+                            held["c3_" + form], ref3, sigma_floor=1e-3)
 
     if rank == 0:
         line = {
