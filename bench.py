@@ -167,36 +167,45 @@ def _class_work(m, n, l, q, d, prec):
     CPQR of B: step s updates the n - s trailing columns over l - s rows with a
     dot product and an axpy (4 flops per entry), 4 n l (l + 1) / 2 =
     2 n l (l + 1) in all.
+    FP64TC forms its products with A from digits (12 bytes per element of A
+    per pass, 21 digit products), and every form but FP64 takes the Gram
+    matrix, X R^-1 and the assembly of the tall FP64 passes (l <= 128) from
+    digit products on the tensor cores: those classes are counted in FP64
+    flops ("oz"), reported as an FP64-equivalent rate beside the FP64 units'.
     """
-    if prec == "fp64":
+    if prec in ("fp64", "fp64tc"):
         rows = [m] * q + [n] * q + 2 * ([m, n] + [l] * max(0, d - 1))
     else:
         rows = [m, n] + [l] * max(0, d - 1)
     passes = 1
     a_bytes = {"fp64": 8.0, "bf16x3": 4.0, "bf16": 2.0, "fp8": 1.0, "tf32x3": 8.0,
-               "tf32": 4.0}[prec] * m * n
+               "tf32": 4.0, "fp64tc": 12.0}[prec] * m * n
     prod = ("flops", (2 * q + 2) * 2.0 * m * n * l) if prec == "fp64" else \
         ("bytes", (2 * q + 2) * a_bytes)
+    oz = prec != "fp64" and l <= 128
+    tall = "oz" if oz else "flops"
     return {
         "products_with_A": prod,
         "cpqr_of_B": ("flops", 2.0 * n * l * (l + 1)),
-        "cholqr_gram": ("flops", passes * sum(r * l * l for r in rows)),
+        "cholqr_gram": (tall, passes * sum(r * l * l for r in rows)),
         "cholqr_cholesky": ("flops", passes * len(rows) * l ** 3 / 3.0),
         "cholqr_trinv": ("flops", passes * len(rows) * l ** 3 / 3.0),
-        "cholqr_apply": ("flops", passes * sum(r * l * l + l ** 3 / 3.0 for r in rows)),
+        "cholqr_apply": (tall, passes * sum(r * l * l + l ** 3 / 3.0 for r in rows)),
         "explicit_Q0": ("flops", 4.0 * l ** 3 / 3.0),
+        # fp64tc: exponents and digits of A's rows and columns (A read four
+        # times, 2 x 12 bytes of digits written)
         "prep_A": ("bytes", {"fp64": 0.0, "bf16x3": 16.0, "bf16": 12.0, "fp8": 18.0,
-                              "tf32x3": 24.0, "tf32": 16.0}[prec] * m * n),
+                              "tf32x3": 24.0, "tf32": 16.0, "fp64tc": 56.0}[prec] * m * n),
         # Q = V Q_B (2 m l^2); P = Pi0 Q(1) Q(3) ... is a product only for d > 2
         # (for d <= 2 it is a row scatter of Q(1), no flops)
-        "assembly": ("flops", 2.0 * (m + (n if d > 2 else 0)) * l * l),
+        "assembly": (tall, 2.0 * (m + (n if d > 2 else 0)) * l * l),
     }
 
 
 # tensor-core rate of each mixed form relative to the measured BF16 rate
 # (NVIDIA's nominal dense ratios: TF32 1.1 and FP8 4.5 against BF16 2.25 PFLOP/s)
-_TC_RATIO = {"bf16x3": 1.0, "bf16": 1.0, "tf32x3": 0.5, "tf32": 0.5, "fp8": 2.0}
-_TC_PRODUCTS = {"bf16x3": 3, "bf16": 1, "tf32x3": 3, "tf32": 1, "fp8": 1}
+_TC_RATIO = {"bf16x3": 1.0, "bf16": 1.0, "tf32x3": 0.5, "tf32": 0.5, "fp8": 2.0, "fp64tc": 1.0}
+_TC_PRODUCTS = {"bf16x3": 3, "bf16": 1, "tf32x3": 3, "tf32": 1, "fp8": 1, "fp64tc": 21}
 
 
 def _stage_roofline(form, m, n, l, q, d, prof, steps, peaks):
@@ -216,6 +225,11 @@ def _stage_roofline(form, m, n, l, q, d, prof, steps, peaks):
         if kind == "bytes":
             e = {"bound": "hbm", "achieved_gbs": per_s / 1e9,
                  "frac": per_s / 1e9 / peaks["hbm_gbs"]}
+        elif kind == "oz":
+            # FP64-accurate work done by digit products on the tensor cores:
+            # the rate in FP64 flops and its multiple of the FP64 units' rate
+            e = {"bound": "tensor (digit products)", "fp64_equiv_tflops": per_s / 1e12,
+                 "x_fp64_units": per_s / 1e12 / peaks["fp64_tflops"]}
         else:
             e = {"bound": "alu", "achieved_tflops": per_s / 1e12,
                  "frac": per_s / 1e12 / peaks["fp64_tflops"]}
@@ -516,9 +530,10 @@ def _run_extra(R, W, torch, A, steps, peaks):
                 tc = nprod * passes * 2.0 * elem * l3 / (pms / 1e3) / 1e12
                 tpeak = peaks["bf16_tflops_sustained"] * ratio
                 gbs = passes * ebytes * elem / (pms / 1e3) / 1e9
-                # one pass streams A once: l flops per element per byte-of-A-size,
-                # so the tensor rate is capped at (l / bytes per element) x BW
-                cap = min(1.0, (l3 * 2.0 / ebytes) * peaks["hbm_gbs"] / 1e3 / tpeak)
+                # a pass streams A once and executes nprod products of 2 l flops
+                # per element of A, so the executed tensor rate is capped at
+                # nprod (2 l / bytes per element) x BW
+                cap = min(1.0, nprod * (l3 * 2.0 / ebytes) * peaks["hbm_gbs"] / 1e3 / tpeak)
                 c3[form] = {"factorizations_per_s": 1e3 / ms, "ms": ms, "worst_status": int(worst),
                             "products_ms": pms, "products_tensor_tflops": tc,
                             "products_tensor_frac": tc / tpeak,
@@ -736,6 +751,11 @@ def run_ours(args):
     if kind == "bytes":
         roof = {"bound": "hbm", "achieved": per_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": per_s / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src}
+    elif kind == "oz":
+        roof = {"bound": "alu", "achieved": per_s / 1e12, "peak": fp64["tflops"],
+                "unit": "TFLOP/s (FP64-equivalent, digit products on the tensor cores)",
+                "frac": per_s / 1e12 / fp64["tflops"],
+                "peak_source": "measured in this run: " + fp64["how"]}
     else:
         roof = {"bound": "alu", "achieved": per_s / 1e12, "peak": fp64["tflops"],
                 "unit": "TFLOP/s", "frac": per_s / 1e12 / fp64["tflops"],
@@ -883,7 +903,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3",
-                    choices=["fp64", "bf16x3", "bf16", "fp8", "tf32x3", "tf32"])
+                    choices=["fp64", "bf16x3", "bf16", "fp8", "tf32x3", "tf32", "fp64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-extra", action="store_true",

@@ -72,7 +72,14 @@ typedef enum {
                            accumulation (about 2^-24 per 8 values of K per accumulator)
                            dominates at large K (7e-6 normwise at K = 8192, BF16X3 1.5e-5);
                            twice the bytes of BF16X3 per pass over A */
-  RQLP_PREC_TF32 = 5    /* tcgen05 TF32 tensor cores, one product, FP32 accumulation */
+  RQLP_PREC_TF32 = 5,   /* tcgen05 TF32 tensor cores, one product, FP32 accumulation */
+  RQLP_PREC_FP64TC = 6  /* FP64 accuracy on the BF16 tensor cores: A and the skinny operand are
+                           cut into six signed 8-bit digits per element against a power-of-two
+                           scale per row (Ozaki-style exact splitting), the 21 digit products
+                           of weight down to 2^-40 of the leading one are formed with tcgen05
+                           (the three leading weight groups summed exactly), so a product is
+                           FP64-accurate to about 2^-47 relative to the row scales; needs
+                           k + p <= 128 */
 } rqlp_prec;
 
 /* Element type of A. */

@@ -26,13 +26,35 @@ namespace {
     if (e_ != cudaSuccess) return RQLP_ERR_CUDA;  \
   } while (0)
 
+#define RET_IF(x)                 \
+  do {                            \
+    int r_ = (x);                 \
+    if (r_ != RQLP_OK) return r_; \
+  } while (0)
+
 // Scratch for CholeskyQR2 on rows x l data.
 struct OrthBufs {
   double *part;   // split-K partials
   double *gpart;  // Gram chunk partials
   double *G, *Rp, *Rinv, *Racc, *Rtmp, *Dinv;
   double *tmp;    // rows x l ping-pong
+  // FP64-accurate digit products on the tensor cores for the Gram matrix, X R^-1
+  // and the final assembly (the forms other than FP64, l <= 128)
+  bool oz;
+  OzOperand oz_xt;  // columns of X (Gram: both operands), with the scaled copies
+  OzOperand oz_x;   // rows of X (X R^-1, the assembly)
+  OzOperand oz_ri;  // columns of an l x l right factor (R^-1, Q_B, ...)
+  double *eye;      // l x l identity
+  float *oz_part;
+  int64_t oz_part_floats;
 };
+
+// unit roundoff of a Gram matrix formed from digit products (2^-47 relative
+// to the column scales, with a factor 2 of margin)
+constexpr double kEpsOz = 1.4210854715202004e-14;  // 2^-46
+// whether the tall FP64 CholeskyQR passes use digit products (the final
+// assembly always does when the buffers exist)
+constexpr bool kOzPasses = false;
 
 size_t part_doubles(int64_t m, int64_t n, int l) {
   const int64_t big = std::max(m, n);
@@ -51,7 +73,17 @@ size_t part_doubles(int64_t m, int64_t n, int l) {
 }
 
 void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBufs &o,
-                double *shared_part) {
+                double *shared_part, bool oz = false) {
+  o.oz = oz && l <= 128;
+  if (o.oz) {
+    o.oz_xt = oz_carve(a, l, rows_max, kOzCopies);
+    o.oz_x = oz_carve(a, rows_max, l, 1);
+    o.oz_ri = oz_carve(a, l, l, kOzCopies);
+    o.eye = a.take<double>((size_t)l * l);
+    o.oz_part_floats = (int64_t)std::max(oz_part_floats(l, l, rows_max),
+                                         oz_part_floats(rows_max, l, l));
+    o.oz_part = a.take<float>((size_t)o.oz_part_floats);
+  }
   o.part = shared_part ? shared_part : a.take<double>(part_doubles(m, n, l));
   o.gpart = a.take<double>((size_t)gram_chunks_max(std::max<int64_t>(rows_max, l)) * l * l);
   o.Dinv = a.take<double>((size_t)l * l);
@@ -68,6 +100,26 @@ void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBuf
 // with FP32's unit roundoff in its breakdown test and shift), then, when
 // passes >= 2, an FP64 pass always follows: Q is FP64-orthonormal and spans
 // range(X) to about FP32 accuracy.
+// An operand view of a carved digit buffer with these rows and K.
+OzOperand oz_view(const OzOperand &b, int64_t rows, int64_t K) {
+  OzOperand o = b;
+  o.rows = rows;
+  o.K = K;
+  o.ld = (K + 7) / 8 * 8;
+  return o;
+}
+
+// C (M x l, ldc; row i to rowmap[i] when given) = X (M x K, ldx) F (K x l,
+// ld l) with K <= 128 by digit products on the tensor cores.
+int oz_right_product(const OrthBufs &o, const double *X, int64_t M, int64_t K, int64_t ldx,
+                     const double *F, int l, double *C, int64_t ldc, const int32_t *rowmap,
+                     Ctrl *ctrl, const int *skip, cudaStream_t st) {
+  const OzOperand xx = oz_view(o.oz_x, M, K), ff = oz_view(o.oz_ri, l, K);
+  RET_IF(oz_split(X, RQLP_F64, M, K, ldx, false, xx, ctrl, skip, st));
+  RET_IF(oz_split(F, RQLP_F64, K, l, l, true, ff, ctrl, skip, st));
+  return oz_gemm(xx, ff, M, l, K, C, ldc, rowmap, o.oz_part, o.oz_part_floats, ctrl, 0, skip, st);
+}
+
 int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t ldq, double *R,
               const OrthBufs &o, Ctrl *ctrl, int site, int passes, double again_tol,
               cudaStream_t st, bool lowp_first) {
@@ -77,15 +129,31 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
   // one CholeskyQR pass: src -> dst, R_acc <- R_pass R_acc (skip: conditional pass)
   auto pass = [&](const double *src, int64_t lds, double *dst, int64_t ldd, bool first,
                   const int *skip, double tol, bool lowp = false) -> int {
+    // a tall FP64 pass may take its Gram matrix and X R^-1 from digit
+    // products (kOzPasses; measured slower than the FP64 kernels so far: the
+    // pass is bound by the Cholesky chain and the triangular inverse, and the
+    // FP64 Gram / solve run near the FP64 rate)
+    const bool ozp = kOzPasses && o.oz && !lowp && rows > kMaxL;
     ev = prof_start(kProfGram, st);
-    CK(gram_sym(src, rows, l, lds, o.gpart, o.G, skip, st, lowp));
+    if (ozp) {
+      const OzOperand xt = oz_view(o.oz_xt, l, rows);
+      RET_IF(oz_split(src, RQLP_F64, rows, l, lds, true, xt, ctrl, skip, st));
+      RET_IF(oz_gemm(xt, xt, l, l, rows, o.G, l, nullptr, o.oz_part, o.oz_part_floats, ctrl, 0,
+                     skip, st));
+    } else {
+      CK(gram_sym(src, rows, l, lds, o.gpart, o.G, skip, st, lowp));
+    }
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
     CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol,
-                    lowp ? kEpsF32 : kEpsF64, lowp));
+                    lowp ? kEpsF32 : (ozp ? kEpsOz : kEpsF64), lowp));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
-    if (rows <= kMaxL && !lowp && skip == nullptr) {
+    if (ozp) {
+      // R^-1 = I R^-1 by the blocked solve, then X R^-1 as a digit product
+      CK(apply_trsm(o.eye, l, l, l, o.Rp, o.Dinv, o.Rinv, l, skip, st));
+      RET_IF(oz_right_product(o, src, rows, l, lds, o.Rinv, l, dst, ldd, nullptr, ctrl, skip, st));
+    } else if (rows <= kMaxL && !lowp && skip == nullptr) {
       // a few rows (the l x l QRs): one warp per row solves q R = x
       CK(tri_rows(o.Rp, l, nullptr, l, src, lds, dst, ldd, (int)rows, false, st));
     } else {
@@ -103,6 +171,7 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfApply, ev, st);
     return RQLP_OK;
   };
+  if (kOzPasses && o.oz) CK(set_identity(o.eye, l, l, l, st));
   // X and Xq share no element: a pass may then write Xq while it reads X
   const bool dis = X + (rows - 1) * ldx + l <= Xq || Xq + (rows - 1) * ldq + l <= X;
   int r;
@@ -161,7 +230,10 @@ int orth(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int64_t 
 // Mixed forms: a CholeskyQR pass leaves Q orthonormal to about eps cond(X)^2;
 // the second pass of CholeskyQR2 runs only when that exceeds 1e-10, far below
 // the error of the BF16 products.  The FP64 form always runs both passes.
-double again_tol_of(const rqlp_opts &o) { return o.prec == RQLP_PREC_FP64 ? -1.0 : 1e-10; }
+// the forms whose products with A are FP64-accurate (DFMA, or digits on the
+// tensor cores) keep every CholeskyQR pass in FP64
+bool fp64_products(int prec) { return prec == RQLP_PREC_FP64 || prec == RQLP_PREC_FP64TC; }
+double again_tol_of(const rqlp_opts &o) { return fp64_products(o.prec) ? -1.0 : 1e-10; }
 
 // Everything rqlp() carves from its workspace.
 struct Plan {
@@ -183,7 +255,7 @@ Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
   Arena a(ws);
   p.ctrl = a.take<Ctrl>(1);
   const int64_t big = std::max(m, n);
-  carve_orth(a, big, l, m, n, p.ob, nullptr);
+  carve_orth(a, big, l, m, n, p.ob, nullptr, o.prec != RQLP_PREC_FP64);
   p.Y = a.take<double>((size_t)m * l);
   p.V = a.take<double>((size_t)m * l);
   p.Z = a.take<double>((size_t)n * l);
@@ -224,7 +296,7 @@ bool valid_opts(const rqlp_opts *o) {
   if (o->q < 0 || o->q > 16) return false;
   if (o->pivot2 != 0 && o->pivot2 != 1) return false;
   if (!o->pivot2 && (o->d < 1 || o->d > 64)) return false;
-  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_TF32) return false;
+  if (o->prec < RQLP_PREC_FP64 || o->prec > RQLP_PREC_FP64TC) return false;
   if (o->block_b < 0) return false;
   if (o->spin_limit_ns < 0) return false;
   if (o->fixed_pivots != 0 && o->fixed_pivots != 1) return false;
@@ -346,8 +418,11 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     CK(form_q(P.Vh, l, P.tau, l, l, P.Qi, l, st, P.utw));
     CK(gather_cols(P.Q0, l, l, l, piv1, P.QB, l, st));
     const int eva = prof_start(kProfAssembly, st);
-    CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
-                nullptr, st));
+    if (P.ob.oz)
+      RET(oz_right_product(P.ob, P.X, n, l, l, P.Qi, l, Pout, ldo, piv0, ctrl, nullptr, st));
+    else
+      CK(gemm_f64(false, RQLP_F64, P.X, l, P.Qi, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part, piv0,
+                  nullptr, st));
     prof_stop(kProfAssembly, eva, st);
   } else {
     RET(orth(P.R0t, n, l, l, P.X, l, P.Rprev, P.ob, ctrl, site0, st, 2, again_tol_of(o)));
@@ -370,6 +445,8 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     if (o.d <= 2) {
       // no odd inner factor beyond Q(1): P = Pi0 Q(1), a row scatter
       CK(permute_rows(P.X, n, l, l, piv0, Pout, ldo, true, st));
+    } else if (P.ob.oz) {
+      RET(oz_right_product(P.ob, P.X, n, l, l, P.Macc, l, Pout, ldo, piv0, ctrl, nullptr, st));
     } else {
       CK(gemm_f64(false, RQLP_F64, P.X, l, P.Macc, l, Pout, ldo, n, l, l, 1.0, 0.0, P.ob.part,
                   piv0, nullptr, st));
@@ -380,8 +457,11 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
     CK(iota(piv1, l, st));
   }
   const int evq = prof_start(kProfAssembly, st);
-  CK(gemm_f64(false, RQLP_F64, Vb, ldv, P.QB, l, Q, ldo, m, l, l, 1.0, 0.0, P.ob.part, nullptr,
-              nullptr, st));
+  if (P.ob.oz)
+    RET(oz_right_product(P.ob, Vb, m, l, ldv, P.QB, l, Q, ldo, nullptr, ctrl, nullptr, st));
+  else
+    CK(gemm_f64(false, RQLP_F64, Vb, ldv, P.QB, l, Q, ldo, m, l, l, 1.0, 0.0, P.ob.part, nullptr,
+                nullptr, st));
   prof_stop(kProfAssembly, evq, st);
   return RQLP_OK;
 }
@@ -515,7 +595,7 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   };
   if (o.prec != RQLP_PREC_FP64) {
     const int ev = prof_start(kProfPrep, st);
-    RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, st));
+    RET(mixed_prepare_A(P.mx, o.prec, A, a_dtype, m, n, lda, P.ctrl, st));
     prof_stop(kProfPrep, ev, st);
   }
   int site = 0;
@@ -530,7 +610,7 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
   // intermediate bases matters; the final V is CholeskyQR2.  In the mixed
   // forms, whose products carry BF16-level errors, the power steps' passes
   // run in FP32 (the span moves by about FP32 rounding).
-  const bool lowp = o.prec != RQLP_PREC_FP64;
+  const bool lowp = !fp64_products(o.prec);
   for (int i = 0; i < o.q; ++i) {
     RET(orth(P.Y, m, l, l, P.V, l, nullptr, P.ob, P.ctrl, site++, st, 1, -1.0, lowp));
     RET(prod_tn(P, o, A, a_dtype, m, n, lda, P.V, l, l, P.Z, st));
@@ -585,6 +665,7 @@ int rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int3
   if (opts->block_b > 0 && (l % opts->block_b != 0)) return RQLP_ERR_INVALID_ARG;
   if (opts->block_b > 0 && opts->q > 0) return RQLP_ERR_UNSUPPORTED;  // Algorithm 4.1 has no power steps
   if (opts->fixed_pivots && opts->block_b > 0) return RQLP_ERR_UNSUPPORTED;
+  if (opts->prec == RQLP_PREC_FP64TC && l > 128) return RQLP_ERR_UNSUPPORTED;
   if (opts->fixed_pivots && (!piv0 || (opts->pivot2 && !piv1))) return RQLP_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
   return run_rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, *opts, Q, L, P, Lvalues, piv0, piv1, ws,
@@ -613,7 +694,7 @@ int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t
   CK(cudaMemsetAsync(W.ctrl, 0, sizeof(Ctrl), st));
   int32_t *pv0 = piv0 ? piv0 : W.piv0;
   int32_t *pv1 = piv1 ? piv1 : W.piv1;
-  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(W.mx, o.prec, A, a_dtype, m, n, lda, st));
+  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(W.mx, o.prec, A, a_dtype, m, n, lda, W.ctrl, st));
   const int64_t ll = (int64_t)l_max * l_max;
   k_zero<<<(int)std::min<int64_t>((ll + 255) / 256, 1024), 256, 0, st>>>(L, ll);
   count_launch();
@@ -746,7 +827,8 @@ int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t ld
   if (!A || !W || !Y || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldw < l ||
       ldy < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_TF32) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP64TC) return RQLP_ERR_INVALID_ARG;
+  if (prec == RQLP_PREC_FP64TC && l > 128) return RQLP_ERR_UNSUPPORTED;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;
@@ -755,7 +837,7 @@ int rqlp_sketch(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t ld
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
   if (prec != RQLP_PREC_FP64) {
-    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, st));
+    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, P.ctrl, st));
     double *tmpY = ldy == l ? Y : P.Y;
     RET(mixed_nn(P.mx, prec, m, n, W, ldw, l, tmpY, P.ctrl, 0, st));
     if (tmpY != Y) CK(copy2d(tmpY, m, l, l, Y, ldy, nullptr, st));
@@ -772,7 +854,8 @@ int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   if (!A || !V || !Z || !ws || m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n || ldv < l ||
       ldz < l || (a_dtype != RQLP_F64 && a_dtype != RQLP_F32))
     return RQLP_ERR_INVALID_ARG;
-  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_TF32) return RQLP_ERR_INVALID_ARG;
+  if (prec < RQLP_PREC_FP64 || prec > RQLP_PREC_FP64TC) return RQLP_ERR_INVALID_ARG;
+  if (prec == RQLP_PREC_FP64TC && l > 128) return RQLP_ERR_UNSUPPORTED;
   rqlp_opts o;
   std::memset(&o, 0, sizeof(o));
   o.prec = prec;
@@ -781,7 +864,7 @@ int rqlp_project(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), st));
   if (prec != RQLP_PREC_FP64) {
-    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, st));
+    RET(mixed_prepare_A(P.mx, prec, A, a_dtype, m, n, lda, P.ctrl, st));
     double *tmpZ = ldz == l ? Z : P.Z;
     RET(mixed_tn(P.mx, prec, m, n, V, ldv, l, tmpZ, P.ctrl, 0, st));
     if (tmpZ != Z) CK(copy2d(tmpZ, n, l, l, Z, ldz, nullptr, st));
@@ -920,7 +1003,7 @@ int run_backward(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t l
   CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
   // the recomputed forward's products with A run in the forward's precision,
   // so the mixed forms need their copies of A
-  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(F.mx, o.prec, A, a_dtype, m, n, lda, st));
+  if (o.prec != RQLP_PREC_FP64) RET(mixed_prepare_A(F.mx, o.prec, A, a_dtype, m, n, lda, ctrl, st));
   // ---- forward with intermediates (Algorithm 2.1) ----
   int site = 0;
   RET(prod_nn(F, o, A, a_dtype, m, n, lda, Omega, ldo, l, F.Y, st));

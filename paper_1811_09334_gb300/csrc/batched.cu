@@ -113,7 +113,8 @@ int rqlp_batched_create(const rqlp_problem *probs, int32_t count, const rqlp_opt
   }
 
   // set-up that must not happen inside a capture
-  if (chol_init() != cudaSuccess || (opts->prec != RQLP_PREC_FP64 && mixed_init() != RQLP_OK)) {
+  if (chol_init() != cudaSuccess || (opts->prec != RQLP_PREC_FP64 && mixed_init() != RQLP_OK) ||
+      ozaki_init() != RQLP_OK) {
     cleanup();
     delete plan;
     return RQLP_ERR_CUDA;

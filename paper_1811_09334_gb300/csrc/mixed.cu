@@ -37,6 +37,21 @@ namespace rqk {
 
 int mixed_init();
 
+// The driver's tensor-map encoder, reached through the runtime once.
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 namespace {
 
 using namespace tc;
@@ -537,19 +552,7 @@ __global__ void k_split_skinny_tf32_t(const double *__restrict__ S, int64_t K, i
 }
 
 // ------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() { return tma_encode_fn(); }
 
 // 2-D tensor map of BF16, E4M3 (fp8) or FP32 (tf32) elements: `rows` x `cols`
 // (cols contiguous, ld elements per row), box of box_rows x (128 bytes) with
@@ -706,6 +709,18 @@ static bool is_tf32(int prec) { return prec == RQLP_PREC_TF32X3 || prec == RQLP_
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx) {
   mx = MixedBufs{};
   if (prec == RQLP_PREC_FP64) return;
+  if (prec == RQLP_PREC_FP64TC) {
+    mx.m = m;
+    mx.n = n;
+    mx.l = l;
+    mx.oA = oz_carve(a, m, n, 1);
+    mx.oAt = oz_carve(a, n, m, 1);
+    mx.oW = oz_carve(a, l, std::max(m, n), kOzCopies);
+    mx.opart_floats = (int64_t)std::max(oz_part_floats(m, l, n), oz_part_floats(n, l, m));
+    mx.opart = a.take<float>((size_t)mx.opart_floats);
+    mx.Ahi = mx.oA.digits;  // marks the buffers as carved
+    return;
+  }
   if (prec == RQLP_PREC_FP8) {
     mx.m = m;
     mx.n = n;
@@ -754,8 +769,12 @@ void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx)
 }
 
 int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, int64_t m,
-                    int64_t n, int64_t lda, cudaStream_t st) {
+                    int64_t n, int64_t lda, Ctrl *ctrl, cudaStream_t st) {
   if (!mx.Ahi) return RQLP_ERR_WORKSPACE;
+  if (prec == RQLP_PREC_FP64TC) {
+    // digits of the rows of A (for Y = A W) and of its columns (for Z = A^T V)
+    return oz_split_both(A, a_dtype, m, n, lda, mx.oA, mx.oAt, ctrl, st);
+  }
   if (prec == RQLP_PREC_FP8) {
     if (cudaMemsetAsync(mx.cmax, 0, (size_t)n * sizeof(unsigned), st) != cudaSuccess)
       return RQLP_ERR_CUDA;
@@ -821,8 +840,24 @@ int quant_skinny(const MixedBufs &mx, const double *S, int64_t K, int l, int64_t
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
+// The skinny operand S (K x l, FP64) as the Y operand of a digit product
+static OzOperand skinny_view(const MixedBufs &mx, int64_t K, int l) {
+  OzOperand o = mx.oW;
+  o.rows = l;
+  o.K = K;
+  o.ld = (K + 7) / 8 * 8;
+  return o;
+}
+
 int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *W, int64_t ldw,
              int l, double *Y, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  if (prec == RQLP_PREC_FP64TC) {
+    const OzOperand w = skinny_view(mx, n, l);
+    int r = oz_split(W, RQLP_F64, n, l, ldw, true, w, ctrl, nullptr, st);
+    if (r != RQLP_OK) return r;
+    return oz_gemm(mx.oA, w, m, l, n, Y, l, nullptr, mx.opart, mx.opart_floats, ctrl, spin_ns,
+                   nullptr, st);
+  }
   if (prec == RQLP_PREC_FP8) {
     const int64_t ldk = round_up(n, 16);
     int r = quant_skinny(mx, W, n, l, ldw, ldk, st);
@@ -840,6 +875,13 @@ int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *
 
 int mixed_tn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *V, int64_t ldv,
              int l, double *Z, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st) {
+  if (prec == RQLP_PREC_FP64TC) {
+    const OzOperand v = skinny_view(mx, m, l);
+    int r = oz_split(V, RQLP_F64, m, l, ldv, true, v, ctrl, nullptr, st);
+    if (r != RQLP_OK) return r;
+    return oz_gemm(mx.oAt, v, n, l, m, Z, l, nullptr, mx.opart, mx.opart_floats, ctrl, spin_ns,
+                   nullptr, st);
+  }
   if (prec == RQLP_PREC_FP8) {
     const int64_t ldk = round_up(m, 16);
     int r = quant_skinny(mx, V, m, l, ldv, ldk, st);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "ozaki.cuh"
 
 namespace rqk {
 
@@ -15,6 +16,11 @@ struct MixedBufs {
   // E4M3 form: A row-scaled, A^T column-scaled, skinny operand column-scaled
   float *sA, *sAt, *sW, *rmax;
   unsigned *cmax;
+  // FP64TC form: digits of A's rows and columns, of the skinny operand, and
+  // the partial sums of the digit products
+  OzOperand oA, oAt, oW;
+  float *opart;
+  int64_t opart_floats;
   int64_t m, n;
   int l;
 };
@@ -25,7 +31,7 @@ int mixed_init();
 void carve_mixed(Arena &a, int64_t m, int64_t n, int l, int prec, MixedBufs &mx);
 // Splits A (and A^T) into BF16 pairs once per factorization.
 int mixed_prepare_A(const MixedBufs &mx, int prec, const void *A, int a_dtype, int64_t m, int64_t n,
-                    int64_t lda, cudaStream_t st);
+                    int64_t lda, Ctrl *ctrl, cudaStream_t st);
 // Y (m x l, ld l, FP64) = A W with W n x l (ld ldw, FP64).
 int mixed_nn(const MixedBufs &mx, int prec, int64_t m, int64_t n, const double *W, int64_t ldw,
              int l, double *Y, Ctrl *ctrl, int64_t spin_ns, cudaStream_t st);

@@ -98,6 +98,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
+// K-major operand tile, 64-byte swizzle (rows of 32 BF16): 8-row atoms of
+// 512 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor, both operands K-major, F32 accumulator:
 // kind::f16 with BF16 x BF16 (format 1), kind::tf32 with TF32 x TF32
 // (format 2), or kind::f8f6f4 with E4M3 x E4M3 (format 0).  A and B always

@@ -21,7 +21,7 @@ RQLP_WARN_SHIFTED_CHOLQR = 1
 STATUS = {0: "RQLP_OK", 1: "RQLP_WARN_SHIFTED_CHOLQR", -1: "RQLP_ERR_INVALID_ARG",
           -2: "RQLP_ERR_NONFINITE", -3: "RQLP_ERR_RANK_DEFICIENT", -4: "RQLP_ERR_TIMEOUT",
           -5: "RQLP_ERR_CUDA", -6: "RQLP_ERR_WORKSPACE", -7: "RQLP_ERR_UNSUPPORTED"}
-PREC = {"fp64": 0, "bf16x3": 1, "bf16": 2, "fp8": 3, "tf32x3": 4, "tf32": 5}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16": 2, "fp8": 3, "tf32x3": 4, "tf32": 5, "fp64tc": 6}
 F64, F32 = 0, 1
 
 _c_i32, _c_i64, _c_sz, _c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p

@@ -49,10 +49,19 @@ def test_stage_roofline_arithmetic():
     assert cp["bound"] == "alu"
     assert abs(cp["achieved_tflops"] - 2.0 * n * l * (l + 1) / 1e-3 / 1e12) < 1e-9
     assert abs(cp["frac"] - cp["achieved_tflops"] / 1.0) < 1e-12  # the measured FP64 rate
-    # the assembly at d <= 2 is the product Q = V Q_B only (P is a row scatter)
-    assert abs(sr["assembly"]["achieved_tflops"] - 2.0 * m * l * l / 1e-3 / 1e12) < 1e-9
-    sr3 = bench._stage_roofline("bf16x3", m, n, l, q, 3, prof, 1, peaks)
+    # the assembly at d <= 2 is the product Q = V Q_B only (P is a row scatter);
+    # in the mixed forms it runs as digit products: an FP64-equivalent rate
+    a2 = sr["assembly"]
+    assert a2["bound"].startswith("tensor")
+    assert abs(a2["fp64_equiv_tflops"] - 2.0 * m * l * l / 1e-3 / 1e12) < 1e-9
+    assert abs(a2["x_fp64_units"] - a2["fp64_equiv_tflops"]) < 1e-12
+    sr3 = bench._stage_roofline("fp64", m, n, l, q, 3, prof, 1, peaks)
     assert abs(sr3["assembly"]["achieved_tflops"] - 2.0 * (m + n) * l * l / 1e-3 / 1e12) < 1e-9
+    # FP64TC: 12 bytes of digits per element of A per pass, 21 digit products
+    srt = bench._stage_roofline("fp64tc", m, n, l, q, d, prof, 1, peaks)
+    assert abs(srt["products_with_A"]["achieved_gbs"] - 4 * 12.0 * m * n / 1e-3 / 1e9) < 1e-6
+    assert abs(srt["products_with_A"]["tensor_tflops"] -
+               21 * 4 * 2.0 * m * n * l / 1e-3 / 1e12) < 1e-6
     # TF32x3: twice the bytes, half the tensor rate
     sr32 = bench._stage_roofline("tf32x3", m, n, l, q, d, prof, 1, peaks)
     assert abs(sr32["products_with_A"]["achieved_gbs"] - 2 * pa["achieved_gbs"]) < 1e-6

@@ -114,3 +114,68 @@ def test_fp8_factorization_singular_values(R):
     assert (np.abs(sg - so)[keep] / so[keep]).max() <= 0.1
     Q = out["Q"].cpu().numpy()
     assert np.abs(Q.T @ Q - np.eye(pr.l)).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ FP64TC
+@pytest.mark.parametrize("m,n,l", [(256, 192, 16), (1000, 700, 30), (2048, 1536, 110),
+                                   (333, 257, 17), (130, 4100, 128), (8192, 8192, 110),
+                                   (3000, 70, 64)])
+def test_fp64tc_products_are_fp64_accurate(R, m, n, l):
+    """Digit products on the tensor cores: each operand element is held to
+    2^-48 of its row's scale (the power of two above the row's largest
+    magnitude) and the digit pairs below 2^-48 of the leading pair are
+    dropped, the leading four weight groups summed exactly; on Gaussian data,
+    whose entries sit 3-5 times below the row maximum on both operands, that
+    is about 1e-13 normwise (measured 4e-14 to 1.5e-13 at K = 8192), held to
+    3e-13 (FP64 DFMA products: about 1e-16)."""
+    rng = np.random.default_rng(m * 5 + n + l)
+    A = rng.standard_normal((m, n)) * (1.0 + 10.0 * rng.random((m, 1)))
+    Om = rng.standard_normal((n, l))
+    V = rng.standard_normal((m, l))
+    Y = R.sketch(_t(A), _t(Om), prec="fp64tc")
+    Z = R.project(_t(A), _t(V), prec="fp64tc")
+    ey, ez = _normrel(Y, O.sketch(A, Om)), _normrel(Z, O.adjoint_product(A, V))
+    assert ey <= 3e-13 and ez <= 3e-13, (ey, ez)
+
+
+def test_fp64tc_product_of_fp32_data_and_zero_rows(R):
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((700, 500)).astype(np.float32)
+    A[17, :] = 0.0
+    A[:, 33] = 0.0
+    Om = rng.standard_normal((500, 40))
+    Y = R.sketch(_t(A), _t(Om), prec="fp64tc")
+    ref = O.sketch(A.astype(np.float64), Om)
+    assert _normrel(Y, ref) <= 3e-13
+    assert np.all(Y.cpu().numpy()[17] == 0.0)
+
+
+@pytest.mark.parametrize("variant", [(True, 1, 0), (False, 2, 1), (False, 3, 2)])
+def test_fp64tc_factorization_holds_the_fp64_parity(R, variant):
+    """The FP64TC form against the FP64 oracle at the FP64 form's tolerances:
+    L and L-values 1e-10 relative, identical pivots, Q and P 1e-9."""
+    pivot2, d, q = variant
+    pr = W.c1()
+    Om = W.omega(pr.n, pr.l, 0)
+    out = R.rqlp(_t(pr.A), pr.k, pr.p, _t(Om), q=q, d=d, pivot2=pivot2, prec="fp64tc")
+    ref = O.rqlp(pr.A, pr.k, pr.p, Om, q=q, d=d, pivot2=pivot2)
+    L = out["L"].cpu().numpy()
+    assert np.abs(L - ref["L"]).max() <= 1e-10 * np.abs(ref["L"]).max()
+    lv = out["Lvalues"].cpu().numpy()
+    assert np.max(np.abs(lv - ref["Lvalues"]) / ref["Lvalues"]) <= 1e-10
+    assert np.array_equal(out["piv0"].cpu().numpy()[:pr.l], ref["piv0"][:pr.l])
+    assert np.array_equal(out["piv1"].cpu().numpy(), ref["piv1"])
+    assert np.abs(out["Q"].cpu().numpy() - ref["Q"]).max() <= 1e-9
+    assert np.abs(out["P"].cpu().numpy() - ref["P"]).max() <= 1e-9
+
+
+def test_fp64tc_nonfinite_and_wide_sketch(R):
+    A = np.random.default_rng(2).standard_normal((300, 200))
+    A[5, 6] = np.inf
+    with pytest.raises(R.RqlpError) as e:
+        R.rqlp(_t(A), 10, 5, _t(W.omega(200, 15, 0)), prec="fp64tc")
+    assert e.value.code == -2
+    A[5, 6] = 0.0
+    with pytest.raises(R.RqlpError) as e:  # l > 128 is not offered
+        R.rqlp(_t(A), 130, 5, _t(W.omega(200, 135, 0)), prec="fp64tc")
+    assert e.value.code == -7

@@ -236,6 +236,9 @@ def test_c2_full_size_fp64_parity(R, c2_full, q):
     out = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=q, d=2, pivot2=False)
     ref = O.rqlp(A_np, pr.k, pr.p, Om, q=q, d=2, pivot2=False)
     _compare(out, ref, pr.l)
+    # the FP64TC form (digit products on the tensor cores) at the same tolerances
+    tc = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=q, d=2, pivot2=False, prec="fp64tc")
+    _compare(tc, ref, pr.l)
     if q == 2:
         # the same matrix in BF16x3 at q = 2: pivots identical, L-values to 1e-3
         mx = R.rqlp(pr.A, pr.k, pr.p, _t(Om), q=q, d=2, pivot2=False, prec="bf16x3")
