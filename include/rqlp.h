@@ -245,6 +245,36 @@ int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, 
               double *Q0, void *ws, size_t ws_bytes, rqlp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Deterministic truncated pivoted QLP (the comparison method of Section 5).
+ * ---------------------------------------------------------------------- */
+/* Workspace of rqlp_qlp() (0 if invalid: needs 1 <= t <= min(m, n, 256),
+ * m <= 16384). */
+size_t rqlp_qlp_workspace_size(int64_t m, int64_t n, int32_t t, const rqlp_opts *opts);
+
+/*
+ * Stewart's pivoted QLP (Section 1, eq. 1.2) truncated at t steps, the
+ * deterministic "QLP" of Section 5 and Tables 1-4: the first t steps of the
+ * column-pivoted Householder QR of A, A Pi0 ~= Q0 R0 with R0 the first t rows
+ * of R, then the QR of R0^T = Q1 R1 (unpivoted for opts->pivot2 = 0; with
+ * opts->pivot2 = 1 pivoted on its t x t R factor as in Algorithm 2.1), so that
+ * A ~= Q L P^T with L = R1^T lower triangular.  The column norms of A are
+ * exact at every step like rqlp()'s; ties go to the lowest column index.
+ *  A       [in]  m x n FP64 (a_dtype RQLP_F64), lda >= n; m <= 16384.
+ *  Q       [out] m x t (ld t); L t x t (ld t); P n x t (ld t); Lvalues t (may
+ *                be NULL); piv0 n and piv1 t (may be NULL).
+ *  ws      [in]  device workspace of rqlp_qlp_workspace_size() bytes (holds a
+ *                transposed copy of A).
+ * Every step rewrites the trailing columns of A (a BLAS-2 sweep: t passes over
+ * A), so it costs far more than rqlp() at the same t; it is the reference the
+ * randomized methods are measured against.  Only opts->pivot2 and
+ * opts->spin_limit_ns are read.  Returns RQLP_OK once enqueued, or an argument
+ * error; device errors go to the status word (rqlp_read_status()).
+ */
+int rqlp_qlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t t,
+             const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+             int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes, rqlp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint (reverse-mode derivative) of RQLP.  The paper has no derivative;
  * this differentiates Algorithm 2.1 (pivot2 = 1) with the column pivots held
  * fixed (they are piecewise constant in A).

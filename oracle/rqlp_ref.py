@@ -105,7 +105,7 @@ def orth(X: np.ndarray) -> np.ndarray:
     return householder_qr(X)[0]
 
 
-def cpqr(X: np.ndarray):
+def cpqr(X: np.ndarray, steps: int = None):
     """Householder QR with column pivoting, X Pi = Q R (Section 1, CPQR).
 
     At step s the column of largest exact trailing norm ||X(s:, j)|| among
@@ -116,11 +116,12 @@ def cpqr(X: np.ndarray):
     Returns (Q, R, piv): Q is rows x t with orthonormal columns
     (t = min(rows, cols)), R is t x cols upper trapezoidal with diag >= 0 and
     piv[i] is the original index of the column at position i
-    (X[:, piv] = Q R).
+    (X[:, piv] = Q R).  With `steps`, only the first t = min(steps, rows,
+    cols) pivot steps run (a truncated CPQR: R is the first t rows of R).
     """
     W = np.array(X, dtype=np.float64, copy=True)
     rows, cols = W.shape
-    t = min(rows, cols)
+    t = min(rows, cols) if steps is None else min(rows, cols, int(steps))
     remaining = list(range(cols))
     order = []
     refl = []
@@ -148,6 +149,29 @@ def cpqr(X: np.ndarray):
             Q[s:, :] -= tau * np.outer(v, v @ Q[s:, :])
     sgn = np.where(np.diag(R[:, :t]) < 0.0, -1.0, 1.0)
     return Q * sgn[None, :], R * sgn[:, None], piv
+
+
+def qlp_truncated(A: np.ndarray, t: int, pivot2: bool = False):
+    """Stewart's pivoted QLP truncated at t steps (Section 1, eq. 1.2): the
+    first t steps of the CPQR of A, A Pi0 ~= Q0 R0 (R0 = the first t rows of
+    R), then the QR of R0^T = Q1 R1, pivoted (cpqr) when pivot2.  Returns Q
+    (m x t), L = R1^T, P = Pi0 Q1 (n x t), Lvalues, piv0, piv1 with
+    A ~= Q L P^T (exact for t = min(m, n))."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    Q0, R0, piv0 = cpqr(A, steps=t)
+    X = R0.T
+    if pivot2:
+        Q1, R1, piv1 = cpqr(X)
+        Q = Q0[:, piv1]
+    else:
+        Q1, R1 = householder_qr(X)
+        piv1 = np.arange(R1.shape[0], dtype=np.int64)
+        Q = Q0
+    P = np.zeros((n, Q1.shape[1]))
+    P[piv0, :] = Q1
+    L = R1.T
+    return dict(Q=Q, L=L, P=P, Lvalues=np.diag(L).copy(), piv0=piv0, piv1=piv1)
 
 
 # ----------------------------------------------------------- range finder

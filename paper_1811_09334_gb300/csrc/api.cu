@@ -905,6 +905,125 @@ int rqlp_cpqr(const double *Bt, int64_t n, int32_t l, int64_t ldb, double *R0t, 
 
 }  // extern "C"
 
+// ---------------------------------------------- deterministic truncated QLP
+// Stewart's pivoted QLP truncated at t steps (Section 1, eq. 1.2; the "QLP"
+// the paper's Section 5 compares the randomized methods with): the first t
+// steps of the column-pivoted Householder QR of A, A Pi0 ~= Q0 R0 with R0 the
+// first t rows of R (t x n), then R0^T = Q1 R1 (an unpivoted CholeskyQR2, or,
+// with pivot2, the CPQR of its t x t R factor as in Algorithm 2.1), so that
+// A ~= Q L P^T with L = R1^T.
+namespace {
+
+struct QlpPlan {
+  Ctrl *ctrl;
+  OrthBufs ob;
+  double *At, *R0t, *Vh, *tau, *S, *Wt, *WtT, *Q0, *X, *Racc, *Rt, *Tl, *Qi, *Vh2, *tau2, *utw;
+  int32_t *piv0, *piv1;
+  void *tall_scratch, *small_scratch;
+  size_t bytes;
+};
+
+QlpPlan carve_qlp(void *ws, int64_t m, int64_t n, int t) {
+  QlpPlan q;
+  Arena a(ws);
+  q.ctrl = a.take<Ctrl>(1);
+  carve_orth(a, n, t, m, n, q.ob, nullptr);
+  const size_t tt = (size_t)t * t;
+  q.At = a.take<double>((size_t)n * m);
+  q.R0t = a.take<double>((size_t)n * t);
+  q.Vh = a.take<double>((size_t)m * t);
+  q.tau = a.take<double>((size_t)t);
+  q.S = a.take<double>(tt);
+  q.Wt = a.take<double>(tt);
+  q.WtT = a.take<double>(tt);
+  q.Q0 = a.take<double>((size_t)m * t);
+  q.X = a.take<double>((size_t)n * t);
+  q.Racc = a.take<double>(tt);
+  q.Rt = a.take<double>(tt);
+  q.Tl = a.take<double>(tt);
+  q.Qi = a.take<double>(tt);
+  q.Vh2 = a.take<double>(tt);
+  q.tau2 = a.take<double>((size_t)t);
+  q.utw = a.take<double>(2 * tt);
+  q.piv0 = a.take<int32_t>((size_t)n);
+  q.piv1 = a.take<int32_t>((size_t)t);
+  q.tall_scratch = a.take<char>(cpqr_tall_ws_bytes(n, m));
+  q.small_scratch = a.take<char>(cpqr_ws_bytes(t, t));
+  q.bytes = a.off;
+  return q;
+}
+
+// Q0 = H_0 ... H_{t-1} [I; 0] (m x t) from the reflectors Vh (m x t, ld t)
+// by the compact-WY form I - V T V^T with T^-1 = diag(1 / tau) + striu(V^T V):
+// Q0 = [I; 0] - V (T V(:t, :)^T).
+int form_q_tall(const QlpPlan &q, int64_t m, int t, double *Q0, cudaStream_t st) {
+  CK(gemm_f64(true, RQLP_F64, q.Vh, t, q.Vh, t, q.S, t, t, t, m, 1.0, 0.0, q.ob.part, nullptr,
+              nullptr, st));
+  CK(tri_rows(q.S, t, q.tau, t, q.Vh, t, q.Wt, t, t, true, st));
+  CK(transpose(q.Wt, t, t, t, q.WtT, t, st));
+  CK(set_identity(Q0, m, t, t, st));
+  CK(gemm_f64(false, RQLP_F64, q.Vh, t, q.WtT, t, Q0, t, m, t, t, -1.0, 1.0, q.ob.part, nullptr,
+              nullptr, st));
+  return RQLP_OK;
+}
+
+int run_qlp(const void *A, int64_t m, int64_t n, int64_t lda, int t, const rqlp_opts &o,
+            double *Q, double *L, double *Pout, double *Lvalues, int32_t *piv0, int32_t *piv1,
+            void *ws, size_t ws_bytes, cudaStream_t st) {
+  QlpPlan q = carve_qlp(ws, m, n, t);
+  if (q.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
+  CK(cudaMemsetAsync(q.ctrl, 0, sizeof(Ctrl), st));
+  const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
+  int32_t *pv0 = piv0 ? piv0 : q.piv0;
+  int32_t *pv1 = piv1 ? piv1 : q.piv1;
+  // columns of A as rows
+  CK(transpose(static_cast<const double *>(A), m, n, lda, q.At, m, st));
+  const int ev = prof_start(kProfCpqr, st);
+  CK(cpqr_tall(q.At, n, m, t, m, q.R0t, t, pv0, q.Vh, t, q.tau, q.tall_scratch, q.ctrl, lim, st));
+  prof_stop(kProfCpqr, ev, st);
+  RET(form_q_tall(q, m, t, o.pivot2 ? q.Q0 : Q, st));
+  if (o.pivot2) {
+    RET(orth(q.R0t, n, t, t, q.X, t, q.Racc, q.ob, q.ctrl, 0, st, 2, -1.0));
+    CK(transpose(q.Racc, t, t, t, q.Rt, t, st));
+    CK(cpqr_wide(q.Rt, t, t, t, q.Tl, t, pv1, q.Vh2, q.tau2, q.small_scratch, q.ctrl, lim, 0, st));
+    CK(copy2d(q.Tl, t, t, t, L, t, nullptr, st));
+    CK(form_q(q.Vh2, t, q.tau2, t, t, q.Qi, t, st, q.utw));
+    CK(gather_cols(q.Q0, m, t, t, pv1, Q, t, st));
+    CK(gemm_f64(false, RQLP_F64, q.X, t, q.Qi, t, Pout, t, n, t, t, 1.0, 0.0, q.ob.part, pv0,
+                nullptr, st));
+  } else {
+    RET(orth(q.R0t, n, t, t, q.X, t, q.Racc, q.ob, q.ctrl, 0, st, 2, -1.0));
+    CK(transpose(q.Racc, t, t, t, L, t, st));
+    CK(permute_rows(q.X, n, t, t, pv0, Pout, t, true, st));
+    CK(iota(pv1, t, st));
+  }
+  if (Lvalues) CK(diag_of(L, t, t, Lvalues, st));
+  return RQLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rqlp_qlp_workspace_size(int64_t m, int64_t n, int32_t t, const rqlp_opts *opts) {
+  if (!opts || m <= 0 || n <= 0 || t < 1 || t > kMaxL || t > m || t > n || m > 16384) return 0;
+  return carve_qlp(nullptr, m, n, t).bytes + 256;
+}
+
+int rqlp_qlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t t,
+             const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+             int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes, rqlp_stream_t stream) {
+  if (!opts || !A || !Q || !L || !P || !ws || lda < n) return RQLP_ERR_INVALID_ARG;
+  if (rqlp_qlp_workspace_size(m, n, t, opts) == 0) return RQLP_ERR_INVALID_ARG;
+  if (opts->pivot2 != 0 && opts->pivot2 != 1) return RQLP_ERR_INVALID_ARG;
+  if (a_dtype != RQLP_F64) return RQLP_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return RQLP_ERR_WORKSPACE;
+  return run_qlp(A, m, n, lda, t, *opts, Q, L, P, Lvalues, piv0, piv1, ws, ws_bytes,
+                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
 // ------------------------------------------------------------------ adjoint
 // Reverse-mode derivative of RQLP (Algorithm 2.1, pivot2 = 1) with the
 // column pivots held fixed: dA = J^T (dQ, dL, dP).  The forward is recomputed

@@ -54,7 +54,9 @@ constexpr int kRecWords = 4;
 struct CpqrParams {
   const double *Bt;
   int64_t n;
-  int l;
+  int l;              // column length (rows of the matrix whose columns are the rows of Bt)
+  int steps;          // pivot steps, <= l (l for the full QR; fewer for a truncated one)
+  int ldv;            // leading dimension of Vh (l x steps)
   int64_t ldb;
   double *R0t;
   int64_t ldr;
@@ -152,7 +154,6 @@ __device__ __forceinline__ bool expired(Ctrl *c, Deadline &d, unsigned long long
 template <bool USE_SMEM>
 __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   extern __shared__ double sm[];
-  __shared__ double s_v[kMaxL];
   __shared__ double s_bn[kWarps];
   __shared__ int s_bi[kWarps];
   __shared__ int s_win_cta, s_win_idx;
@@ -164,8 +165,13 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c0 = (int64_t)b * P.cpb;
   const int nc = (int)max((int64_t)0, min(P.n, c0 + P.cpb) - c0);
-  double *cols = USE_SMEM ? sm : P.gcols + (int64_t)b * P.cpb * l;
-  double *nrm = USE_SMEM ? sm + (int64_t)P.cpb * l : sm;
+  const int steps = P.steps;
+  // the winner's column x(s:), unscaled (l doubles, 16-byte rounded), then
+  // the slab when it sits in shared memory, then the per-column state
+  double *s_v = sm;
+  double *sm1 = sm + ((l + 1) & ~1);
+  double *cols = USE_SMEM ? sm1 : P.gcols + (int64_t)b * P.cpb * l;
+  double *nrm = USE_SMEM ? sm1 + (int64_t)P.cpb * l : sm1;
   // 1% of the norm^2 when it was last computed exactly: below that the
   // downdated value has lost too many digits and is recomputed
   double *thr = nrm + P.cpb;
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   if (!wait_winner(1u, 1) || s_err) return;
 
   const int sub = lane >> 2, gl = lane & 3;
-  for (int s = 0; s < l; ++s) {
+  for (int s = 0; s < steps; ++s) {
     const int buf = s & 1;
     // ---- 1. winner (every CTA picked the same one) and its sigma ----
     const int wc = s_win_cta, wi = s_win_idx;
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       const int jw = (int)(wi - c0);
       const double *col = cols + (int64_t)jw * l;
       double *out = P.R0t + (int64_t)s * P.ldr;
-      for (int r = lane; r < l; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
+      for (int r = lane; r < steps; r += 32) out[r] = (r < s) ? col[r] : (r == s ? beta : 0.0);
       if (lane == 0) { pivoted[jw] = 1; nrm[jw] = -1.0; }
     }
     // ---- 3. dot products v^T col and downdated norms (the axpys wait) ----
@@ -514,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
           thr[jj] = 0.01 * nd;
           axdone[jj] = 1;
         }
-        const double key = s + 1 < l ? pick_key(P.fpiv, s + 1, (int)(c0 + jj), nd) : nd;
+        const double key = s + 1 < steps ? pick_key(P.fpiv, s + 1, (int)(c0 + jj), nd) : nd;
         if (better(key, (int)(c0 + jj), bn, bi)) { bn = key; bi = (int)(c0 + jj); }
       }
     }
@@ -524,14 +530,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     // this CTA's candidate for step s + 1 (every thread reads the same table)
     int jc = -1;
     double cn = -1.0;
-    if (s + 1 < l) {
+    if (s + 1 < steps) {
       int ci = -1;
       for (int w = 0; w < kWarps; ++w)
         if (better(s_bn[w], s_bi[w], cn, ci)) { cn = s_bn[w]; ci = s_bi[w]; }
       jc = ci >= 0 ? (int)(ci - c0) : -1;
     }
     // ---- 4. warp 0: update the candidate and publish it ----
-    if (warp == 0 && s + 1 < l) {
+    if (warp == 0 && s + 1 < steps) {
       const unsigned k = (unsigned)(s + 2);
       double sg, x0;
       publish(buf ^ 1, k, jc, cn, s + 1, (jc >= 0 && !axdone[jc]) ? wdot[jc] : 0.0, sg, x0);
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     if (b == 0 && warp == kWarps - 1) {
       // this step's reflector, off the path to the exchange
       for (int r = lane; r < l; r += 32)
-        P.Vh[(int64_t)r * l + s] = (r < s) ? 0.0 : (r == s ? 1.0 : s_v[r - s] * rv0);
+        P.Vh[(int64_t)r * P.ldv + s] = (r < s) ? 0.0 : (r == s ? 1.0 : s_v[r - s] * rv0);
       if (lane == 0) { P.tau[s] = tau; P.piv[s] = wi; }
     }
     for (int jb = (warp - 1) * 8; warp > 0 && jb < nc; jb += (kWarps - 1) * 8) {
@@ -555,15 +561,15 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
       }
     }
     // (the wait's block barrier orders these axpys before the next column load)
-    if (s + 1 < l && (!wait_winner((unsigned)(s + 2), 2) || s_err)) return;
+    if (s + 1 < steps && (!wait_winner((unsigned)(s + 2), 2) || s_err)) return;
   }
 
-  // ---- unchosen columns keep their order behind the l pivots ----
-  // one more exchange (l + 1, record word 0): the number of unchosen columns
-  // of every CTA; CTA b needs those of CTAs 0..b-1
+  // ---- unchosen columns keep their order behind the pivots ----
+  // one more exchange (steps + 1, record word 0): the number of unchosen
+  // columns of every CTA; CTA b needs those of CTAs 0..b-1
   if (warp == 0) {
-    const unsigned kf = (unsigned)(l + 1);
-    const int fb = l & 1;
+    const unsigned kf = (unsigned)(steps + 1);
+    const int fb = steps & 1;
     int mine = 0;
     for (int jj = lane; jj < nc; jj += 32) mine += pivoted[jj] ? 0 : 1;
     mine = __reduce_add_sync(0xffffffffu, mine);
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
   if (!s_ok) return;
   if (warp == 0) {
     // rank of each unpivoted column within the slab, in index order
-    int pos = l + s_prefix;
+    int pos = steps + s_prefix;
     for (int jj0 = 0; jj0 < nc; jj0 += 32) {
       const int jj = jj0 + lane;
       const int un = (jj < nc && !pivoted[jj]) ? 1 : 0;
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr_wide(CpqrParams P) {
     const int64_t dst = -(int64_t)code - 1;
     if (dst >= P.n) continue;
     const double *col = cols + (int64_t)jj * l;
-    for (int r = lane; r < l; r += 32) P.R0t[dst * P.ldr + r] = col[r];
+    for (int r = lane; r < steps; r += 32) P.R0t[dst * P.ldr + r] = col[r];
   }
 }
 
@@ -640,10 +646,11 @@ Plan plan_for(int64_t n, int l) {
   if (G < 1) G = 1;
   int cpb = (int)((n + G - 1) / G);
   G = (int)((n + cpb - 1) / cpb);
+  const size_t sv = (size_t)((l + 1) & ~1) * sizeof(double);  // the winner's column
   const size_t state = (size_t)cpb * (3 * sizeof(double) + 2 * sizeof(int));
   const size_t slab = (size_t)cpb * l * sizeof(double);
-  p.use_smem = (slab + state <= 190 * 1024) ? 1 : 0;
-  p.smem = (p.use_smem ? slab : 0) + state;
+  p.use_smem = (sv + slab + state <= 190 * 1024) ? 1 : 0;
+  p.smem = sv + (p.use_smem ? slab : 0) + state;
   p.G = G;
   p.cpb = cpb;
   return p;
@@ -654,7 +661,7 @@ Plan plan_for(int64_t n, int l) {
 // per-launch exchange state, zeroed before every launch: the arrival
 // counter (one 128-byte line), the winner lines (one per CTA), the tagged
 // candidate records and the tagged published columns (both double-buffered)
-static size_t tagged_bytes(int G, int l) {
+static size_t tagged_bytes(int G, int64_t l) {
   return 128 + 128 * (size_t)G + 2 * (size_t)G * kRecWords * sizeof(ulonglong2) +
          2 * (size_t)G * l * sizeof(ulonglong2);
 }
@@ -671,13 +678,23 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
   return (tagged_bytes(pl.G, l) + 255) / 256 * 256;
 }
 
-cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
-                      int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
-                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
-                      const int32_t *fixed_piv) {
-  if (n <= 0 || l <= 0 || l > kMaxL || l > n) return cudaErrorInvalidValue;
-  Plan pl = plan_for(n, l);
-  if (pl.G > kMaxGrid) return cudaErrorInvalidValue;
+size_t cpqr_tall_ws_bytes(int64_t n, int64_t L) {
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>(n, num_sms()));
+  const int64_t cpb = (n + G - 1) / G;
+  size_t b = (tagged_bytes(G, L) + 255) / 256 * 256;
+  b += ((size_t)G * cpb * L * sizeof(double) + 255) / 256 * 256;
+  return b + 8192;
+}
+
+// The launch shared by the wide CPQR of B (l = column length = steps) and the
+// truncated CPQR of a tall matrix (column length L, `steps` pivots).
+static cudaError_t cpqr_launch(const double *Bt, int64_t n, int64_t L, int steps, int64_t ldb,
+                               double *R0t, int64_t ldr, int32_t *piv, double *Vh, int64_t ldv,
+                               double *tau, void *scratch, Ctrl *ctrl,
+                               unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
+                               const int32_t *fixed_piv) {
+  Plan pl = plan_for(n, (int)L);
+  if (pl.G > kMaxGrid || pl.smem > 220 * 1024) return cudaErrorInvalidValue;
   void *kfn = pl.use_smem ? (void *)k_cpqr_wide<true> : (void *)k_cpqr_wide<false>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)std::max<size_t>(pl.smem, 1));
@@ -690,15 +707,16 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
   char *p = reinterpret_cast<char *>(scratch);
   auto take = [&](size_t bytes) { char *r = p; p += (bytes + 255) / 256 * 256; return r; };
   CpqrParams P;
-  P.Bt = Bt; P.n = n; P.l = l; P.ldb = ldb; P.R0t = R0t; P.ldr = ldr; P.piv = piv;
+  P.Bt = Bt; P.n = n; P.l = (int)L; P.steps = steps; P.ldv = (int)ldv; P.ldb = ldb;
+  P.R0t = R0t; P.ldr = ldr; P.piv = piv;
   P.Vh = Vh; P.tau = tau;
-  const size_t tb = tagged_bytes(pl.G, l);
+  const size_t tb = tagged_bytes(pl.G, L);
   char *tagged = take(tb);
   P.arrive = reinterpret_cast<unsigned *>(tagged);
   P.win = reinterpret_cast<ulonglong2 *>(tagged + 128);
   P.rec = reinterpret_cast<ulonglong2 *>(tagged + 128 + 128 * (size_t)pl.G);
   P.pcol = P.rec + 2 * (size_t)pl.G * kRecWords;
-  P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * l * sizeof(double)));
+  P.gcols = reinterpret_cast<double *>(take((size_t)pl.G * pl.cpb * L * sizeof(double)));
   P.ctrl = ctrl;
   P.limit_ns = limit_ns ? limit_ns : kDefaultSpinNs;
   P.extra = debug_extra;
@@ -725,6 +743,25 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
                                   st);
   count_launch();
   return e;
+}
+
+cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
+                      int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
+                      unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
+                      const int32_t *fixed_piv) {
+  if (n <= 0 || l <= 0 || l > kMaxL || l > n) return cudaErrorInvalidValue;
+  return cpqr_launch(Bt, n, l, l, ldb, R0t, ldr, piv, Vh, l, tau, scratch, ctrl, limit_ns,
+                     debug_extra, st, fixed_piv);
+}
+
+cudaError_t cpqr_tall(const double *At, int64_t n, int64_t L, int steps, int64_t ldat, double *R0t,
+                      int64_t ldr, int32_t *piv, double *Vh, int64_t ldv, double *tau,
+                      void *scratch, Ctrl *ctrl, unsigned long long limit_ns, cudaStream_t st) {
+  if (n <= 0 || L <= 0 || steps < 1 || steps > kMaxL || steps > n || steps > L || ldr < steps ||
+      ldv < steps || L > 16384)
+    return cudaErrorInvalidValue;
+  return cpqr_launch(At, n, L, steps, ldat, R0t, ldr, piv, Vh, ldv, tau, scratch, ctrl, limit_ns,
+                     0, st, nullptr);
 }
 
 }  // namespace rqk

@@ -162,5 +162,14 @@ cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
                       unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
                       const int32_t *fixed_piv = nullptr);
+// The first `steps` pivot steps of the column-pivoted Householder QR of an
+// L x n matrix (L <= 16384, steps <= 256) given as At = its transpose (n x L,
+// ld ldat): R0t (n x steps, ld ldr) holds the first `steps` rows of R as
+// columns (pivot order), piv (n) the column order, Vh (L x steps, ld ldv) and
+// tau (steps) the reflectors.  Scratch: cpqr_tall_ws_bytes(n, L).
+size_t cpqr_tall_ws_bytes(int64_t n, int64_t L);
+cudaError_t cpqr_tall(const double *At, int64_t n, int64_t L, int steps, int64_t ldat, double *R0t,
+                      int64_t ldr, int32_t *piv, double *Vh, int64_t ldv, double *tau,
+                      void *scratch, Ctrl *ctrl, unsigned long long limit_ns, cudaStream_t st);
 
 }  // namespace rqk

@@ -243,58 +243,57 @@ k_oz_digits_t(const T *__restrict__ S, int64_t r, int64_t c, int64_t ld,
 }
 
 // Both orientations of one matrix at once (the digits of A's rows and of its
-// columns, each against its own exponents).  Exponents: CTAs of 32 rows
-// (8 warps, lanes along the rows), the row maxima in registers, one atomic
-// max per column and CTA; cexp starts at INT_MIN.
+// columns, each against its own exponents).  Exponents: tiles of 32 rows x
+// 128 columns (8 warps, lanes along the rows, four columns each), one atomic
+// max per row and per column and tile; rexp and cexp start at INT_MIN.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_oz_exps_both(const T *__restrict__ S, int64_t r, int64_t c, int64_t ld, int32_t *rexp,
                int32_t *cexp, Ctrl *ctrl) {
-  __shared__ unsigned long long red[32][9];
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int nr = (int)min((int64_t)32, r - i0);
+  __shared__ unsigned long long red[8][128];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 128;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long rmx[4] = {0, 0, 0, 0};  // rows warp, warp + 8, warp + 16, warp + 24
-  // every thread runs every chunk (the loop holds block barriers)
-  for (int64_t jc = 0; jc < c; jc += 32) {
-    const int64_t j = jc + lane;
-    unsigned long long cm = 0;
+  unsigned long long cm[4] = {0, 0, 0, 0}, rm[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int p4 = 0; p4 < 4; ++p4) {
+    const int64_t i = i0 + warp + 8 * p4;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int rr = warp + 8 * q;
-      if (rr < nr && j < c) {
+      const int64_t j = j0 + lane + 32 * q;
+      if (i < r && j < c) {
         const unsigned long long ab =
-            (unsigned long long)__double_as_longlong(as_f64(S[(i0 + rr) * ld + j])) &
-            0x7fffffffffffffffull;
-        cm = ab > cm ? ab : cm;
-        rmx[q] = ab > rmx[q] ? ab : rmx[q];
+            (unsigned long long)__double_as_longlong(as_f64(S[i * ld + j])) & 0x7fffffffffffffffull;
+        cm[q] = ab > cm[q] ? ab : cm[q];
+        rm[p4] = ab > rm[p4] ? ab : rm[p4];
       }
     }
-    // the column's maximum over the CTA's rows: 8 warps hold 4 rows each
-    red[lane][warp] = cm;
-    __syncthreads();
-    if (warp == 0 && j < c) {
-      unsigned long long t = red[lane][0];
-      for (int w = 1; w < 8; ++w) t = red[lane][w] > t ? red[lane][w] : t;
-      const int ee = exp_bound(t);
-      if (ee == 2000) set_status(ctrl, RQLP_ERR_NONFINITE);
-      atomicMax(cexp + j, ee);
-    }
-    __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    unsigned long long v = rmx[q];
+  for (int p4 = 0; p4 < 4; ++p4) {
+    unsigned long long v = rm[p4];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long w2 = __shfl_xor_sync(0xffffffffu, v, o);
       v = w2 > v ? w2 : v;
     }
-    const int rr = warp + 8 * q;
-    if (lane == 0 && rr < nr) {
+    const int64_t i = i0 + warp + 8 * p4;
+    if (lane == 0 && i < r) {
       const int ee = exp_bound(v);
       if (ee == 2000) set_status(ctrl, RQLP_ERR_NONFINITE);
-      rexp[i0 + rr] = ee;
+      atomicMax(rexp + i, ee);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[warp][lane + 32 * q] = cm[q];
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    const int64_t j = j0 + threadIdx.x;
+    unsigned long long t = red[0][threadIdx.x];
+    for (int w = 1; w < 8; ++w) t = red[w][threadIdx.x] > t ? red[w][threadIdx.x] : t;
+    if (j < c) {
+      const int ee = exp_bound(t);
+      if (ee == 2000) set_status(ctrl, RQLP_ERR_NONFINITE);
+      atomicMax(cexp + j, ee);
     }
   }
 }
@@ -409,6 +408,11 @@ k_oz_mma(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtenso
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer: the X digit tile and this digit's Y tiles ----
+      // (the job's table in registers: no parameter loads inside the loop)
+      const int nw = jb.nw;
+      int widx[kMaxW];
+#pragma unroll
+      for (int w = 0; w < kMaxW; ++w) widx[w] = w < nw ? jb.widx[w] : 0;
       int issued = 0;
       for (int i = 0; i < nkb; ++i) {
         const int s = i % a.stages;
@@ -421,8 +425,9 @@ k_oz_mma(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtenso
         mbar_expect_tx(&bar_full[s], tx_bytes);
         const int kx = (kb0 + i) * kTK;
         tma_load_3d(st, &tX, kx, m_tile * kTM, di, &bar_full[s]);
-        for (int w = 0; w < jb.nw; ++w)
-          tma_load_3d(st + xbytes + w * ybytes, &tY, kx, 0, jb.widx[w], &bar_full[s]);
+#pragma unroll
+        for (int w = 0; w < kMaxW; ++w)
+          if (w < nw) tma_load_3d(st + xbytes + w * ybytes, &tY, kx, 0, widx[w], &bar_full[s]);
         issued = i + 1;
       }
       for (int s = 0; s < a.stages && s < issued; ++s) {
@@ -434,7 +439,18 @@ k_oz_mma(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtenso
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
+      // accumulator address, B-tile offset and opening flag of every pair in
+      // registers before the loop (the issuing thread would otherwise wait on
+      // a parameter load before each MMA)
       const uint32_t idesc = instr_desc(kTM, a.n_pad);
+      const int nw = jb.nw;
+      uint32_t td[kMaxW], boff[kMaxW], opens[kMaxW];
+#pragma unroll
+      for (int w = 0; w < kMaxW; ++w) {
+        td[w] = tmem + (uint32_t)((w < nw ? jb.wacc[w] : 0) * a.acc_cols);
+        boff[w] = xbytes + (uint32_t)w * ybytes;
+        opens[w] = (w < nw && jb.first[w]) ? 1u : 0u;
+      }
       for (int i = 0; i < nkb; ++i) {
         const int s = i % a.stages;
         const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
@@ -448,11 +464,12 @@ k_oz_mma(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtenso
         for (int k = 0; k < kTK / 16; ++k) {
           // 16 BF16 values (32 bytes) along K inside the 64-byte swizzled row
           const uint32_t off = k * 32;
-          for (int w = 0; w < jb.nw; ++w) {
-            const uint32_t td = tmem + (uint32_t)(jb.wacc[w] * a.acc_cols);
-            const uint32_t accum = (i == 0 && k == 0 && jb.first[w]) ? 0u : 1u;
-            mma_bf16(td, smem_desc_sw64(xa + off),
-                     smem_desc_sw64(xa + xbytes + w * ybytes + off), idesc, accum);
+          const uint64_t adesc = smem_desc_sw64(xa + off);
+#pragma unroll
+          for (int w = 0; w < kMaxW; ++w) {
+            if (w >= nw) break;
+            const uint32_t accum = (i == 0 && k == 0 && opens[w]) ? 0u : 1u;
+            mma_bf16(td[w], adesc, smem_desc_sw64(xa + boff[w] + off), idesc, accum);
           }
         }
         mma_commit(&bar_empty[s]);
@@ -470,16 +487,27 @@ k_oz_mma(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtenso
     if (tid == 0) set_status(a.ctrl, RQLP_ERR_TIMEOUT);
   } else {
     const int row = m_tile * kTM + warp * 32 + lane;
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
     for (int q = 0; q < jb.nacc; ++q) {
       float *out = a.part + (int64_t)(jb.slot0 + q) * a.slot_stride +
                    (int64_t)split * a.split_stride + (int64_t)row * a.ldp;
-      for (int c0 = 0; c0 < a.n_pad; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * a.acc_cols + c0), r);
+      // 64 columns per round: two loads in flight, one wait
+      for (int c0 = 0; c0 < a.n_pad; c0 += 64) {
+        uint32_t r0[32], r1[32];
+        const uint32_t base = tmem + lanes + (uint32_t)(q * a.acc_cols + c0);
+        tmem_ld32_nowait(base, r0);
+        tmem_ld32_nowait(base + 32, r1);  // columns past n_pad stay inside the accumulator
+        tmem_ld_wait();
         if (row < a.M) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<uint4 *>(out + c0 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+          for (int j = 0; j < 32; j += 4)
+            if (c0 + j < a.n_pad)
+              *reinterpret_cast<uint4 *>(out + c0 + j) = make_uint4(r0[j], r0[j + 1], r0[j + 2], r0[j + 3]);
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (c0 + 32 + j < a.n_pad)
+              *reinterpret_cast<uint4 *>(out + c0 + 32 + j) =
+                  make_uint4(r1[j], r1[j + 1], r1[j + 2], r1[j + 3]);
         }
       }
     }
@@ -769,15 +797,16 @@ int oz_split_both(const void *S, int dtype, int64_t r, int64_t c, int64_t ld,
   if (rows.rows != r || rows.K != c || cols.rows != c || cols.K != r || rows.copies != 1 ||
       cols.copies != 1)
     return RQLP_ERR_INVALID_ARG;
-  if (cudaMemsetAsync(cols.exps, 0x80, (size_t)c * sizeof(int32_t), st) != cudaSuccess)
+  if (cudaMemsetAsync(cols.exps, 0x80, (size_t)c * sizeof(int32_t), st) != cudaSuccess ||
+      cudaMemsetAsync(rows.exps, 0x80, (size_t)r * sizeof(int32_t), st) != cudaSuccess)
     return RQLP_ERR_CUDA;
   const bool f32 = dtype == RQLP_F32;
-  const unsigned rb = (unsigned)((r + 31) / 32);
+  const dim3 ge((unsigned)((c + 127) / 128), (unsigned)((r + 31) / 32));
   if (f32)
-    k_oz_exps_both<float><<<rb, 256, 0, st>>>(static_cast<const float *>(S), r, c, ld, rows.exps,
+    k_oz_exps_both<float><<<ge, 256, 0, st>>>(static_cast<const float *>(S), r, c, ld, rows.exps,
                                               cols.exps, ctrl);
   else
-    k_oz_exps_both<double><<<rb, 256, 0, st>>>(static_cast<const double *>(S), r, c, ld, rows.exps,
+    k_oz_exps_both<double><<<ge, 256, 0, st>>>(static_cast<const double *>(S), r, c, ld, rows.exps,
                                                cols.exps, ctrl);
   count_launch();
   const dim3 g((unsigned)((c + 31) / 32), (unsigned)((r + 31) / 32));

@@ -97,6 +97,9 @@ _SIGS = {
     "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
                                ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i64,
                                _c_p, _c_sz, _c_p]),
+    "rqlp_qlp_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, ctypes.POINTER(Opts)]),
+    "rqlp_qlp": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, ctypes.POINTER(Opts), _c_p,
+                          _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
     "rqlp_launch_count": (ctypes.c_longlong, []),
     "rqlp_profile_begin": (_c_i32, []),
     "rqlp_profile_end": (_c_i32, [_c_p, _c_p, _c_i32]),
@@ -404,6 +407,36 @@ def host_wait(res: dict) -> int:
     _check(code, "rqlp_host_async (device status)")
     res["status"] = code
     return code
+
+
+def qlp(A, t: int, pivot2: bool = False, ws=None, stream=None, check: bool = True) -> dict:
+    """Deterministic pivoted QLP of A truncated at t steps (Section 1, eq. 1.2;
+    the comparison method of Section 5) on the GPU.  A: (m, n) float64 CUDA
+    tensor.  Returns Q (m, t), L (t, t), P (n, t), Lvalues, piv0, piv1, status."""
+    torch = _torch()
+    m, n = A.shape
+    o = opts(pivot2=pivot2)
+    L_ = lib()
+    need = L_.rqlp_qlp_workspace_size(m, n, t, ctypes.byref(o))
+    if need == 0:
+        raise RqlpError(-1, "rqlp_qlp_workspace_size")
+    dev = A.device
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    out = dict(Q=torch.empty((m, t), dtype=torch.float64, device=dev),
+               L=torch.empty((t, t), dtype=torch.float64, device=dev),
+               P=torch.empty((n, t), dtype=torch.float64, device=dev),
+               Lvalues=torch.empty((t,), dtype=torch.float64, device=dev),
+               piv0=torch.empty((n,), dtype=torch.int32, device=dev),
+               piv1=torch.empty((t,), dtype=torch.int32, device=dev))
+    st = _stream(stream)
+    _check(L_.rqlp_qlp(_ptr(A), _dtype_code(A), m, n, _row_major(A, "A"), t, ctypes.byref(o),
+                       _ptr(out["Q"]), _ptr(out["L"]), _ptr(out["P"]), _ptr(out["Lvalues"]),
+                       _ptr(out["piv0"]), _ptr(out["piv1"]), _ptr(ws), ws.numel(), st), "rqlp_qlp")
+    out["ws"] = ws
+    if check:
+        out["status"] = _check(L_.rqlp_read_status(_ptr(ws), st), "rqlp_qlp (device status)")
+    return out
 
 
 # ------------------------------------------------------------------ stages

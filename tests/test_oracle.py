@@ -382,3 +382,30 @@ def test_rvalues_are_lapack_pivoted_qr_diagonal():
     t = R.truncate(out, 20)
     assert t["Q"].shape == (150, 20) and t["L"].shape == (20, 20) and t["P"].shape == (100, 20)
     assert np.array_equal(t["Lvalues"], out["Lvalues"][:20])
+
+
+# ---------------------------------------------------------- deterministic QLP
+@pytest.mark.parametrize("t", [12, 25, 40])
+def test_truncated_qlp_matches_lapack_pivoted_qlp(t):
+    # the truncated QLP (Section 1, eq. 1.2): pivots and R-rows of the first t
+    # steps are LAPACK dgeqp3's, and with the pivoted second QR the L-values
+    # are those of LAPACK's two-step pivoted QLP truncated at t
+    A, _ = _decaying(60, 40, 21, decay=0.8)
+    out = R.qlp_truncated(A, t, pivot2=True)
+    lv, p0, p1 = _scipy_pivoted_qlp(A, t)
+    assert list(out["piv0"][:t]) == list(p0[:t])
+    assert list(out["piv1"]) == list(p1)
+    assert np.allclose(out["Lvalues"], lv, rtol=1e-10)
+    # Q L P^T = Q0 Q0^T A: the residual identity of eq. 2.1 for the projector
+    Q, L, P = out["Q"], out["L"], out["P"]
+    E = A - Q @ L @ P.T
+    assert abs(np.linalg.norm(E) ** 2 - (np.linalg.norm(A) ** 2 - np.linalg.norm(Q.T @ A) ** 2)) \
+        <= 1e-12 * np.linalg.norm(A) ** 2
+    assert np.allclose(Q.T @ Q, np.eye(t), atol=1e-13)
+    assert np.allclose(P.T @ P, np.eye(t), atol=1e-13)
+    assert np.allclose(np.triu(L, 1), 0.0)
+    # unpivoted second QR: the same projector, L-values of an unpivoted QR of R0^T
+    un = R.qlp_truncated(A, t, pivot2=False)
+    assert np.allclose(un["Q"] @ un["L"] @ un["P"].T, Q @ L @ P.T, atol=1e-12)
+    if t == 40:  # t = n: the full pivoted QLP reproduces A
+        assert np.abs(E).max() <= 1e-13
