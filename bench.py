@@ -581,6 +581,25 @@ def _run_extra(R, W, torch, A, steps, peaks):
                              "mean_rel_R": float(np.mean(np.abs(sig - rv[:k6]) / sig)),
                              "paper_err": row[name],
                              "paper_T_s": row.get("T_%s_s" % name)}
+            # the deterministic truncated pivoted QLP (the paper's "QLP" column),
+            # t = k + p steps, pivoted second QR
+            keep = {}
+
+            def runq():
+                r = R.qlp(pr6.A, pr6.k + pr6.p, pivot2=True, ws=keep.get("ws"), check=False)
+                keep["ws"] = r["ws"]
+                keep["out"] = r
+                return r
+
+            ms = _timed(torch, runq, 2)
+            st = R.read_status(keep["ws"])
+            lv = keep["out"]["Lvalues"].cpu().numpy()
+            k6 = pr6.k
+            sig = pr6.sigma[:k6]
+            ent["QLP"] = {"ms": ms, "status": int(st),
+                          "err_L": float(np.max(np.abs(sig - np.abs(lv[:k6])))),
+                          "mean_rel_L": float(np.mean(np.abs(sig - lv[:k6]) / sig)),
+                          "paper_err": row["QLP"], "paper_T_s": row.get("T_QLP_s")}
             rows.append(ent)
             del pr6
         out["w6_paper_shaped"] = {

@@ -52,9 +52,12 @@ struct OrthBufs {
 // unit roundoff of a Gram matrix formed from digit products (2^-47 relative
 // to the column scales, with a factor 2 of margin)
 constexpr double kEpsOz = 1.4210854715202004e-14;  // 2^-46
-// whether the tall FP64 CholeskyQR passes use digit products (the final
-// assembly always does when the buffers exist)
-constexpr bool kOzPasses = false;
+// which parts of a tall FP64 CholeskyQR pass use digit products (the final
+// assembly always does when the buffers exist): the Gram matrix (one
+// product with K = rows), and X R^-1 (needs R^-1 first: measured slower than
+// the FP64 blocked solve, whose triangular structure halves the work)
+constexpr bool kOzGram = true;
+constexpr bool kOzApply = false;
 
 size_t part_doubles(int64_t m, int64_t n, int l) {
   const int64_t big = std::max(m, n);
@@ -72,18 +75,23 @@ size_t part_doubles(int64_t m, int64_t n, int l) {
   return b;
 }
 
+// The digit-product buffers of the orthonormalizations and the assembly,
+// carved last so that every other piece of a workspace keeps its offset.
+void carve_orth_oz(Arena &a, int64_t rows_max, int l, OrthBufs &o, bool oz) {
+  o.oz = oz && l <= 128 && !tuning().no_digit_products;
+  if (!o.oz) return;
+  o.oz_xt = oz_carve(a, l, rows_max, kOzCopies);
+  o.oz_x = oz_carve(a, rows_max, l, 1);
+  o.oz_ri = oz_carve(a, l, l, kOzCopies);
+  o.eye = a.take<double>((size_t)l * l);
+  o.oz_part_floats = (int64_t)std::max(oz_part_floats(l, l, rows_max),
+                                       oz_part_floats(rows_max, l, l));
+  o.oz_part = a.take<float>((size_t)o.oz_part_floats);
+}
+
 void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBufs &o,
-                double *shared_part, bool oz = false) {
-  o.oz = oz && l <= 128;
-  if (o.oz) {
-    o.oz_xt = oz_carve(a, l, rows_max, kOzCopies);
-    o.oz_x = oz_carve(a, rows_max, l, 1);
-    o.oz_ri = oz_carve(a, l, l, kOzCopies);
-    o.eye = a.take<double>((size_t)l * l);
-    o.oz_part_floats = (int64_t)std::max(oz_part_floats(l, l, rows_max),
-                                         oz_part_floats(rows_max, l, l));
-    o.oz_part = a.take<float>((size_t)o.oz_part_floats);
-  }
+                double *shared_part) {
+  o.oz = false;
   o.part = shared_part ? shared_part : a.take<double>(part_doubles(m, n, l));
   o.gpart = a.take<double>((size_t)gram_chunks_max(std::max<int64_t>(rows_max, l)) * l * l);
   o.Dinv = a.take<double>((size_t)l * l);
@@ -129,13 +137,10 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
   // one CholeskyQR pass: src -> dst, R_acc <- R_pass R_acc (skip: conditional pass)
   auto pass = [&](const double *src, int64_t lds, double *dst, int64_t ldd, bool first,
                   const int *skip, double tol, bool lowp = false) -> int {
-    // a tall FP64 pass may take its Gram matrix and X R^-1 from digit
-    // products (kOzPasses; measured slower than the FP64 kernels so far: the
-    // pass is bound by the Cholesky chain and the triangular inverse, and the
-    // FP64 Gram / solve run near the FP64 rate)
-    const bool ozp = kOzPasses && o.oz && !lowp && rows > kMaxL;
+    // a tall FP64 pass may take its Gram matrix and X R^-1 from digit products
+    const bool ozp = o.oz && !lowp && rows > kMaxL;
     ev = prof_start(kProfGram, st);
-    if (ozp) {
+    if (ozp && kOzGram) {
       const OzOperand xt = oz_view(o.oz_xt, l, rows);
       RET_IF(oz_split(src, RQLP_F64, rows, l, lds, true, xt, ctrl, skip, st));
       RET_IF(oz_gemm(xt, xt, l, l, rows, o.G, l, nullptr, o.oz_part, o.oz_part_floats, ctrl, 0,
@@ -146,10 +151,10 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
     CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol,
-                    lowp ? kEpsF32 : (ozp ? kEpsOz : kEpsF64), lowp));
+                    lowp ? kEpsF32 : ((ozp && kOzGram) ? kEpsOz : kEpsF64), lowp));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
-    if (ozp) {
+    if (ozp && kOzApply) {
       // R^-1 = I R^-1 by the blocked solve, then X R^-1 as a digit product
       CK(apply_trsm(o.eye, l, l, l, o.Rp, o.Dinv, o.Rinv, l, skip, st));
       RET_IF(oz_right_product(o, src, rows, l, lds, o.Rinv, l, dst, ldd, nullptr, ctrl, skip, st));
@@ -171,7 +176,7 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfApply, ev, st);
     return RQLP_OK;
   };
-  if (kOzPasses && o.oz) CK(set_identity(o.eye, l, l, l, st));
+  if (kOzApply && o.oz) CK(set_identity(o.eye, l, l, l, st));
   // X and Xq share no element: a pass may then write Xq while it reads X
   const bool dis = X + (rows - 1) * ldx + l <= Xq || Xq + (rows - 1) * ldq + l <= X;
   int r;
@@ -255,7 +260,7 @@ Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
   Arena a(ws);
   p.ctrl = a.take<Ctrl>(1);
   const int64_t big = std::max(m, n);
-  carve_orth(a, big, l, m, n, p.ob, nullptr, o.prec != RQLP_PREC_FP64);
+  carve_orth(a, big, l, m, n, p.ob, nullptr);
   p.Y = a.take<double>((size_t)m * l);
   p.V = a.take<double>((size_t)m * l);
   p.Z = a.take<double>((size_t)n * l);
@@ -287,6 +292,7 @@ Plan carve(void *ws, int64_t m, int64_t n, int l, const rqlp_opts &o) {
   p.piv1 = a.take<int32_t>((size_t)l);
   p.cpqr_scratch = a.take<char>(cpqr_ws_bytes(std::max<int64_t>(n, l), l));
   carve_mixed(a, m, n, l, o.prec, p.mx);
+  carve_orth_oz(a, big, l, p.ob, o.prec != RQLP_PREC_FP64);
   p.bytes = a.off;
   return p;
 }

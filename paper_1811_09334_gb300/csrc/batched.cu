@@ -124,6 +124,9 @@ int rqlp_batched_create(const rqlp_problem *probs, int32_t count, const rqlp_opt
   tuning().gemm_target_ctas = (tune && tune->gemm_target_ctas > 0) ? tune->gemm_target_ctas
                                                                     : num_sms() / 2;
   tuning().mma_max_splits = (tune && tune->mma_max_splits > 0) ? tune->mma_max_splits : 2;
+  // small problems side by side: the FP64 units' kernels share SMs, a digit
+  // product's CTAs each hold a whole SM
+  tuning().no_digit_products = 1;
 
   if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = RQLP_ERR_CUDA;
   if (rc == RQLP_OK && cudaEventRecord(fork, s0) != cudaSuccess) rc = RQLP_ERR_CUDA;

@@ -21,6 +21,8 @@ struct Tuning {
   int mma_max_splits;    // tcgen05 products: at most this many K splits (0: fill the SMs)
   int chol_ctas;         // Cholesky of the Gram matrix: cluster of 16 or 8 CTAs, or 1 CTA
                          // (0: 16 where such a cluster fits, else 8)
+  int no_digit_products; // 1: the FP64 Gram matrices and the assembly stay on the FP64 units
+                         // (batches: a digit product takes a whole SM per CTA)
 };
 Tuning &tuning();
 

@@ -15,17 +15,18 @@
 //     1024 of them is exact in the FP32 accumulator: the product of digit
 //     pair (i, j) over a K slice of 1024 is exact;
 //   * C = 2^(ex+ey) sum_{i,j} 2^(-14-8(i+j)) D_i E_j^T; the pairs of weight
-//     group t = i + j = 0, 1, 2 are kept exact (one accumulator per pair, the
-//     K slices summed as integers), the pairs with t = 3, 4, 5 go into one
-//     FP32 accumulator with E_j pre-scaled by 2^(-8(t-3)) (their rounding is
-//     2^-24 of a term that is itself 2^-24 of the result), and pairs with
-//     t >= 6 are dropped (2^-48 of the result);
-//   * one CTA per (128-row tile of C, K slice of 1024, digit i of X): a TMA
-//     producer streams the X digit tile and the Y digit tiles its pairs need,
-//     one thread issues tcgen05.mma kind::f16 into up to four TMEM
-//     accumulators, and the epilogue writes FP32 partial sums; a second
-//     kernel adds them (exact groups in 64-bit integers), applies the
-//     weights and the scales, and writes C in FP64.
+//     group t = i + j = 0..3 are kept exact (one accumulator per pair, the K
+//     slices summed as 64-bit integers), the pairs with t = 4, 5 go into one
+//     FP32 accumulator with E_j pre-scaled by 2^(-8(t-4)) (their rounding is
+//     2^-24 of a term that is itself 2^-32 of the result), and pairs with
+//     t >= 6 are dropped (2^-48 of the row scales);
+//   * one CTA per job (the pairs of one X digit, at most four accumulators;
+//     digit 0's rounded pairs form a seventh job), 128-row tile of C and K
+//     slice of 1024: a TMA producer streams 64-byte-swizzled tiles of the X
+//     digit and of the Y digits the job needs through a ring of stages, one
+//     thread issues tcgen05.mma kind::f16 into the TMEM accumulators, and the
+//     epilogue writes FP32 partial sums; a second kernel adds them, applies
+//     the weights and the scales, and writes C in FP64.
 //
 // Every mbarrier wait is bounded (RQLP_ERR_TIMEOUT).
 #include <cuda.h>

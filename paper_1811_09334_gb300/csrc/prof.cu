@@ -24,7 +24,7 @@ size_t g_used[kProfClasses] = {};
 }  // namespace
 
 Tuning &tuning() {
-  static thread_local Tuning t = {0, 0, 0, 0};
+  static thread_local Tuning t = {0, 0, 0, 0, 0};
   return t;
 }
 
