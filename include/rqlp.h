@@ -316,30 +316,48 @@ typedef struct {
   int32_t *piv0, *piv1;
 } rqlp_problem;
 
-/* Launch shapes of a batch (0 selects a default): parallel branches (problems
- * in flight), CTAs the FP64 products aim for, K splits of the tensor-core
- * products.  The autotuner of the Python package picks them per batch shape. */
+/* How a batch runs (0 selects a default) and its launch shapes.
+ *
+ * engine: RQLP_BATCH_PERSISTENT (one persistent kernel: one CTA per SM takes
+ * (problem, stage, tile) work items from an ordered device list, waiting for
+ * each item's previous stage on per-problem counters with a bounded poll),
+ * RQLP_BATCH_GRAPH (every problem's kernels recorded into one CUDA graph over
+ * parallel branches), or RQLP_BATCH_AUTO (0: the persistent kernel where it
+ * supports the batch, else the graph).  The persistent kernel supports the
+ * FP64 and BF16x3 forms with l = k + p <= 128, n <= 6000, d <= 4 (d = 1 with
+ * pivot2), no given pivots and no truncation.
+ * For the graph engine: parallel branches (problems in flight), CTAs the FP64
+ * products aim for, K splits of the tensor-core products.  The autotuner of
+ * the Python package picks the engine and the shapes per batch shape. */
+enum { RQLP_BATCH_AUTO = 0, RQLP_BATCH_GRAPH = 1, RQLP_BATCH_PERSISTENT = 2 };
 typedef struct {
   int32_t branches;
   int32_t gemm_target_ctas;
   int32_t mma_max_splits;
-  int32_t reserved;
+  int32_t engine;
 } rqlp_batch_tuning;
 
 typedef struct rqlp_batch *rqlp_batch_t;
 
-/* Device workspace of a batch (one rqlp() workspace per branch plus the
- * per-problem status array); 0 if a problem or the options are invalid
- * (block_b must be 0: BRQLP is not batched). */
+/* Device workspace of a batch: the graph engine needs one rqlp() workspace
+ * per branch, the persistent engine every problem's buffers at once (plus its
+ * work-item tables), both a per-problem status array; 0 if a problem or the
+ * options are invalid (block_b must be 0: BRQLP is not batched) or the
+ * requested engine does not support them. */
 size_t rqlp_batched_workspace_size(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts,
                                    const rqlp_batch_tuning *tune);
 
-/* Records the factorizations of all `count` problems (Algorithms 2.1 / 2.2 with
- * the options in `opts`) into one CUDA graph over tune->branches parallel
- * streams and instantiates it.  Problems run with small launch shapes so that
- * many fit on the GPU at once; results are those of rqlp() on each problem.
- * Not thread-safe with other calls of this library on the same host thread
- * while it records.  The problem table is read during this call only. */
+/* Prepares the factorizations of all `count` problems (Algorithms 2.1 / 2.2
+ * with the options in `opts`) as one CUDA graph and instantiates it.  Graph
+ * engine: every problem's kernels over tune->branches parallel streams, with
+ * small launch shapes so that many fit on the GPU at once.  Persistent
+ * engine: one zeroing node and one kernel node; the work-item list, the
+ * problem and stage tables and the tensor maps are written into the
+ * workspace here (synchronous copies).  Results are those of rqlp() on each
+ * problem (the persistent engine's l x l QRs are Householder QRs, equal to
+ * rqlp()'s up to rounding).  Not thread-safe with other calls of this library
+ * on the same host thread while it records.  The problem table is read during
+ * this call only. */
 int rqlp_batched_create(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts,
                         const rqlp_batch_tuning *tune, void *ws, size_t ws_bytes,
                         rqlp_batch_t *plan);
@@ -353,6 +371,10 @@ int rqlp_batched_status(rqlp_batch_t plan, rqlp_stream_t stream, int32_t *status
 
 /* Number of kernel nodes in the batch's graph (kernels per launch). */
 int rqlp_batched_kernel_nodes(rqlp_batch_t plan);
+
+/* The engine the batch runs on (RQLP_BATCH_GRAPH or RQLP_BATCH_PERSISTENT)
+ * and, for the persistent engine, its work items per launch (else 0). */
+int rqlp_batched_engine(rqlp_batch_t plan, int64_t *items);
 
 /* Frees the graph (not the workspace, which the caller owns). */
 void rqlp_batched_destroy(rqlp_batch_t plan);

@@ -1,11 +1,12 @@
 """Autotuner for batched factorizations.
 
-Picks the launch shapes of a batch (parallel branches, the CTA target of
-the FP64 products, the K splits of the tensor-core products) by timing
-candidates on the GPU on a sample of the batch, one knob at a time, and
-caches the choice in a JSON file keyed by the batch's shape bucket
-(number of problems, largest m, n and l, precision, q, d).  The cache file
-is $RQLP_TUNE_CACHE, else ~/.cache/rqlp_gb300_tune.json.
+Picks how a batch runs by timing candidates on the GPU on a sample of the
+batch: the launch shapes of the graph engine (parallel branches, the CTA
+target of the FP64 products, the K splits of the tensor-core products), one
+knob at a time, then the persistent engine where it supports the batch; the
+faster engine wins.  The choice is cached in a JSON file keyed by the
+batch's shape bucket (number of problems, largest m, n and l, precision, q,
+d).  The cache file is $RQLP_TUNE_CACHE, else ~/.cache/rqlp_gb300_tune.json.
 """
 from __future__ import annotations
 
@@ -61,7 +62,8 @@ def _time_batch(As, ks, p, Oms, q, d, pivot2, prec, tune, reps=3):
 
 def tune(As, ks, p, Oms, q=0, d=1, pivot2=True, prec="fp64", sample=64, use_cache=True,
          log=None) -> dict:
-    """Launch shapes for this batch: dict(branches, gemm_target_ctas, mma_max_splits)."""
+    """Engine and launch shapes for this batch: dict(branches, gemm_target_ctas,
+    mma_max_splits, engine)."""
     key = shape_key(As, ks, p, prec, q, d, pivot2)
     path = _cache_path()
     cache = {}
@@ -76,7 +78,7 @@ def tune(As, ks, p, Oms, q=0, d=1, pivot2=True, prec="fp64", sample=64, use_cach
     sA = [As[i] for i in idx]
     sk = [ks[i] for i in idx]
     sO = [Oms[i] for i in idx]
-    best = {"branches": 64, "gemm_target_ctas": 76, "mma_max_splits": 2}
+    best = {"branches": 64, "gemm_target_ctas": 76, "mma_max_splits": 2, "engine": "graph"}
     trials = []
     for knob, values in (("branches", BRANCHES), ("gemm_target_ctas", GEMM_TARGETS),
                          ("mma_max_splits", MMA_SPLITS)):
@@ -91,6 +93,18 @@ def tune(As, ks, p, Oms, q=0, d=1, pivot2=True, prec="fp64", sample=64, use_cach
             if log:
                 log("autotune %s=%s: %.3f ms" % (knob, v, times[v]))
         best[knob] = min(times, key=times.get)
+    graph_ms = min(ms for t, ms in trials if all(t[k] == best[k] for k in best))
+    try:
+        cand = dict(best)
+        cand["engine"] = "persistent"
+        pms = _time_batch(sA, sk, p, sO, q, d, pivot2, prec, cand)
+        trials.append((dict(cand), pms))
+        if log:
+            log("autotune engine=persistent: %.3f ms (graph %.3f ms)" % (pms, graph_ms))
+        if pms < graph_ms:
+            best["engine"] = "persistent"
+    except R.RqlpError:
+        pass  # the persistent engine does not support this batch
     if use_cache:
         cache[key] = {"tuning": best, "sample": len(sA),
                       "trials": [{"tuning": t, "ms": ms} for t, ms in trials]}

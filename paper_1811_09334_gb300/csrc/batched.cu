@@ -1,22 +1,27 @@
 // Batched randomized QLP: many independent problems of uneven m, n, k in one
-// CUDA-graph launch.
+// CUDA-graph launch, on one of two engines.
 //
-// rqlp_batched_create() records every problem's whole pipeline (the same
-// kernels as rqlp()) into one graph, spread over `branches` parallel streams
-// so that independent problems run side by side, and instantiates it once;
-// rqlp_batched_launch() replays it with a single cudaGraphLaunch.  While
-// recording, launch shapes are lowered so that one problem does not claim the
-// whole GPU: the CPQR of B runs as one CTA (its exchanges never wait on
-// another CTA), and the split-K targets of the FP64 and tensor-core products
-// come from the tuning record (picked by the autotuner).  Problems of one
-// branch run one after another and share one workspace; each problem's status
-// word is copied into a per-problem array.
+// Persistent engine (persist.cu): one kernel of one CTA per SM takes
+// (problem, stage, tile) work items from an ordered device list; the graph
+// holds a zeroing node and that kernel.
+//
+// Graph engine: rqlp_batched_create() records every problem's whole pipeline
+// (the same kernels as rqlp()) into one graph, spread over `branches`
+// parallel streams so that independent problems run side by side, and
+// instantiates it once; rqlp_batched_launch() replays it with a single
+// cudaGraphLaunch.  While recording, launch shapes are lowered so that one
+// problem does not claim the whole GPU: the CPQR of B runs as one CTA (its
+// exchanges never wait on another CTA), and the split-K targets of the FP64
+// and tensor-core products come from the tuning record (picked by the
+// autotuner).  Problems of one branch run one after another and share one
+// workspace; each problem's status word is copied into a per-problem array.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "kernels.cuh"
 #include "mixed.cuh"
+#include "persist.cuh"
 
 using namespace rqk;
 
@@ -27,6 +32,8 @@ struct rqlp_batch {
   int branches = 0;
   int kernel_nodes = 0;
   int32_t *d_status = nullptr;
+  int engine = RQLP_BATCH_GRAPH;
+  PersistLaunch pl = {};
 };
 
 namespace {
@@ -39,11 +46,66 @@ bool valid_problem(const rqlp_problem &p, const rqlp_opts *o) {
   return rqlp_workspace_size(p.m, p.n, p.k, p.p, o) > 0 && p.lda >= p.n && p.ldo >= p.k + p.p;
 }
 
+// the engine a batch runs on: RQLP_BATCH_PERSISTENT, RQLP_BATCH_GRAPH, or
+// 0 when the requested engine cannot run it
+int engine_of(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts,
+              const rqlp_batch_tuning *t) {
+  const int want = t ? t->engine : RQLP_BATCH_AUTO;
+  if (want != RQLP_BATCH_AUTO && want != RQLP_BATCH_GRAPH && want != RQLP_BATCH_PERSISTENT)
+    return 0;
+  if (want != RQLP_BATCH_GRAPH && persist_ws_bytes(probs, count, opts) > 0)
+    return RQLP_BATCH_PERSISTENT;
+  return want == RQLP_BATCH_PERSISTENT ? 0 : RQLP_BATCH_GRAPH;
+}
+
 int branches_of(const rqlp_batch_tuning *t, int count) {
   int b = (t && t->branches > 0) ? t->branches : 64;
   if (b > count) b = count;
   if (b < 1) b = 1;
   return b;
+}
+
+// Persistent engine: plan the work items into the workspace, then capture
+// the zeroing and the kernel into a graph of two nodes.
+int create_persistent(const rqlp_problem *probs, int32_t count, const rqlp_opts *opts, void *ws,
+                      size_t ws_bytes, rqlp_batch_t *out) {
+  char *base = reinterpret_cast<char *>(ws);
+  int32_t *d_status = reinterpret_cast<int32_t *>(base);
+  const size_t head = up256((size_t)count * sizeof(int32_t));
+  rqlp_batch *plan = new rqlp_batch;
+  plan->count = count;
+  plan->branches = 1;
+  plan->d_status = d_status;
+  plan->engine = RQLP_BATCH_PERSISTENT;
+  int rc = persist_setup(probs, count, opts, base + head, ws_bytes - head, d_status, &plan->pl);
+  cudaStream_t s0 = nullptr;
+  if (rc == RQLP_OK && cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking) != cudaSuccess)
+    rc = RQLP_ERR_CUDA;
+  if (rc == RQLP_OK && cudaMemsetAsync(d_status, 0, sizeof(int32_t) * count, s0) != cudaSuccess)
+    rc = RQLP_ERR_CUDA;
+  if (rc == RQLP_OK && cudaStreamSynchronize(s0) != cudaSuccess) rc = RQLP_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  if (rc == RQLP_OK) {
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = RQLP_ERR_CUDA;
+    } else {
+      const int r = persist_enqueue(plan->pl, s0);
+      const cudaError_t ec = cudaStreamEndCapture(s0, &graph);
+      if (r != RQLP_OK) rc = r;
+      else if (ec != cudaSuccess) rc = RQLP_ERR_CUDA;
+    }
+  }
+  if (rc == RQLP_OK && cudaGraphInstantiate(&plan->exec, graph, 0) != cudaSuccess)
+    rc = RQLP_ERR_CUDA;
+  plan->graph = graph;
+  plan->kernel_nodes = 1;
+  if (s0) cudaStreamDestroy(s0);
+  if (rc != RQLP_OK) {
+    rqlp_batched_destroy(plan);
+    return rc;
+  }
+  *out = plan;
+  return RQLP_OK;
 }
 
 }  // namespace
@@ -58,6 +120,10 @@ size_t rqlp_batched_workspace_size(const rqlp_problem *probs, int32_t count, con
     if (!valid_problem(probs[i], opts)) return 0;
     per = std::max(per, rqlp_workspace_size(probs[i].m, probs[i].n, probs[i].k, probs[i].p, opts));
   }
+  const int eng = engine_of(probs, count, opts, tune);
+  if (eng == 0) return 0;
+  if (eng == RQLP_BATCH_PERSISTENT)
+    return up256((size_t)count * sizeof(int32_t)) + persist_ws_bytes(probs, count, opts) + 256;
   const int b = branches_of(tune, count);
   return up256((size_t)count * sizeof(int32_t)) + (size_t)b * up256(per) + 256;
 }
@@ -70,6 +136,8 @@ int rqlp_batched_create(const rqlp_problem *probs, int32_t count, const rqlp_opt
   const size_t need = rqlp_batched_workspace_size(probs, count, opts, tune);
   if (need == 0) return RQLP_ERR_INVALID_ARG;
   if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return RQLP_ERR_WORKSPACE;
+  if (engine_of(probs, count, opts, tune) == RQLP_BATCH_PERSISTENT)
+    return create_persistent(probs, count, opts, ws, ws_bytes, out);
   size_t per = 0;
   for (int i = 0; i < count; ++i)
     per = std::max(per, rqlp_workspace_size(probs[i].m, probs[i].n, probs[i].k, probs[i].p, opts));
@@ -224,8 +292,15 @@ int rqlp_batched_status(rqlp_batch_t plan, rqlp_stream_t stream, int32_t *status
 
 int rqlp_batched_kernel_nodes(rqlp_batch_t plan) { return plan ? plan->kernel_nodes : 0; }
 
+int rqlp_batched_engine(rqlp_batch_t plan, int64_t *items) {
+  if (!plan) return 0;
+  if (items) *items = plan->engine == RQLP_BATCH_PERSISTENT ? plan->pl.items : 0;
+  return plan->engine;
+}
+
 void rqlp_batched_destroy(rqlp_batch_t plan) {
   if (!plan) return;
+  persist_release(&plan->pl);
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
   delete plan;

@@ -43,7 +43,11 @@ class Problem(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("branches", _c_i32), ("gemm_target_ctas", _c_i32), ("mma_max_splits", _c_i32),
-                ("reserved", _c_i32)]
+                ("engine", _c_i32)]
+
+
+# batch engines (include/rqlp.h, rqlp_batch_tuning.engine)
+ENGINES = {"auto": 0, "graph": 1, "persistent": 2}
 
 
 class RqlpError(RuntimeError):
@@ -92,6 +96,7 @@ _SIGS = {
     "rqlp_batched_launch": (_c_i32, [_c_p, _c_p]),
     "rqlp_batched_status": (_c_i32, [_c_p, _c_p, _c_p]),
     "rqlp_batched_kernel_nodes": (_c_i32, [_c_p]),
+    "rqlp_batched_engine": (_c_i32, [_c_p, ctypes.POINTER(_c_i64)]),
     "rqlp_batched_destroy": (None, [_c_p]),
     "rqlp_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
     "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
@@ -514,17 +519,21 @@ def cpqr(B, ws=None, stream=None):
 
 # ----------------------------------------------------------------- batches
 class Batch:
-    """Many independent factorizations recorded into one CUDA graph.
+    """Many independent factorizations in one CUDA graph launch.
 
     As: list of (m_i, n_i) CUDA tensors (float64/float32, row-major); ks: the
     target ranks; p: oversampling; Omegas: list of (n_i, k_i + p) float64
-    CUDA tensors.  Outputs are allocated here (self.out[i] holds Q, L, P,
-    Lvalues, piv0, piv1).  launch() runs the whole batch with one
-    cudaGraphLaunch; status() synchronizes and returns (worst, per-problem).
+    CUDA tensors.  engine: "persistent" (one persistent kernel taking work
+    items from a device list), "graph" (every problem's kernels recorded into
+    the graph over `branches` parallel streams) or "auto" (the persistent
+    kernel where it supports the batch).  Outputs are allocated here
+    (self.out[i] holds Q, L, P, Lvalues, piv0, piv1).  launch() runs the whole
+    batch with one cudaGraphLaunch; status() synchronizes and returns (worst,
+    per-problem).
     """
 
     def __init__(self, As, ks, p, Omegas, q=0, d=1, pivot2=True, prec="fp64", branches=0,
-                 gemm_target_ctas=0, mma_max_splits=0):
+                 gemm_target_ctas=0, mma_max_splits=0, engine="auto"):
         torch = _torch()
         L_ = lib()
         self.count = len(As)
@@ -547,7 +556,8 @@ class Batch:
                                _ptr(o["P"]), _ptr(o["Lvalues"]), _ptr(o["piv0"]), _ptr(o["piv1"]))
         self._probs = probs
         self.opts = opts(q, d, pivot2, prec)
-        self.tuning = BatchTuning(int(branches), int(gemm_target_ctas), int(mma_max_splits), 0)
+        self.tuning = BatchTuning(int(branches), int(gemm_target_ctas), int(mma_max_splits),
+                                  ENGINES[engine])
         need = L_.rqlp_batched_workspace_size(probs, self.count, ctypes.byref(self.opts),
                                               ctypes.byref(self.tuning))
         if need == 0:
@@ -562,6 +572,17 @@ class Batch:
     @property
     def kernel_nodes(self) -> int:
         return int(lib().rqlp_batched_kernel_nodes(self.handle))
+
+    @property
+    def engine(self) -> str:
+        code = int(lib().rqlp_batched_engine(self.handle, None))
+        return {1: "graph", 2: "persistent"}.get(code, "unknown")
+
+    @property
+    def work_items(self) -> int:
+        n = _c_i64(0)
+        lib().rqlp_batched_engine(self.handle, ctypes.byref(n))
+        return int(n.value)
 
     def launch(self, stream=None):
         _check(lib().rqlp_batched_launch(self.handle, _stream(stream)), "rqlp_batched_launch")

@@ -1,4 +1,5 @@
-"""Batched factorizations in one CUDA-graph launch against the oracle."""
+"""Batched factorizations in one CUDA-graph launch against the oracle (the
+graph engine, and the full 512-problem workload on both engines)."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,7 @@ def _batch(count, mmax, seed):
                                              ("bf16x3", 1, 2, False)])
 def test_batched_matches_oracle(R, prec, q, d, pivot2):
     As, Ans, ks, Oms, Onp = _batch(20, 700, 77)
-    b = R.Batch(As, ks, 8, Oms, q=q, d=d, pivot2=pivot2, prec=prec, branches=6)
+    b = R.Batch(As, ks, 8, Oms, q=q, d=d, pivot2=pivot2, prec=prec, branches=6, engine="graph")
     for rep in range(2):  # the graph can be replayed
         b.launch()
         worst, st = b.status()
@@ -74,7 +75,7 @@ def test_batched_matches_oracle(R, prec, q, d, pivot2):
 def test_batched_status_per_problem(R):
     As, Ans, ks, Oms, Onp = _batch(6, 400, 78)
     As[3][5, 7] = float("nan")
-    b = R.Batch(As, ks, 8, Oms, q=1, d=2, pivot2=False, branches=3)
+    b = R.Batch(As, ks, 8, Oms, q=1, d=2, pivot2=False, branches=3, engine="graph")
     b.launch()
     worst, st = b.status()
     assert worst == -2
@@ -118,11 +119,13 @@ def _check_against_oracle(prec, out, ref, l, where):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
-def test_full_512_problem_batch_sampled_against_the_oracle(R, prec, tmp_path, monkeypatch):
+@pytest.mark.parametrize("prec,engine", [("bf16x3", "persistent"), ("fp64", "persistent"),
+                                         ("bf16x3", "graph")])
+def test_full_512_problem_batch_sampled_against_the_oracle(R, prec, engine, tmp_path,
+                                                            monkeypatch):
     """The whole 512-problem workload (m ~ U[256, 4096], n ~ U[128, m],
-    k ~ U[8, 64], p = 8, ERQLP q = 1, d = 2) in the launch configuration the
-    benchmark times (autotuned shapes, one graph launch), with a seeded
+    k ~ U[8, 64], p = 8, ERQLP q = 1, d = 2) on each engine the benchmark
+    times (autotuned shapes for the graph, one graph launch), with a seeded
     sample of 20 problems and the 4 largest compared with the FP64 oracle."""
     from paper_1811_09334_gb300 import autotune
     monkeypatch.setenv("RQLP_TUNE_CACHE", str(tmp_path / "tune.json"))
@@ -135,7 +138,9 @@ def test_full_512_problem_batch_sampled_against_the_oracle(R, prec, tmp_path, mo
         Oms.append(torch.from_numpy(W.omega(n, k + 8, i)).cuda())
     torch.cuda.synchronize()
     tune = autotune.tune(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, sample=128)
+    tune["engine"] = engine
     b = R.Batch(As, ks, 8, Oms, q=1, d=2, pivot2=False, prec=prec, **tune)
+    assert b.engine == engine
     b.launch()
     worst, st = b.status()
     assert worst >= 0 and all(s >= 0 for s in st)
