@@ -46,8 +46,10 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 nominal rate (2 FMA/clk/SM x 152 SMs x 
 # was captured (its SHA-256 below); otherwise the bench line reports null.
 _TRAFFIC = {
     "cpqr_of_B": {
-        "source": "paper_1811_09334_gb300/csrc/cpqr.cu",
-        "sha256": "9d6d630acbe26d8a0f3073f677ac83f1c426423082ba3becc4fef1e4f5bf3fb8",
+        # the kernel's launcher and its pivot-step loop (shared with the batch kernel)
+        "source": ["paper_1811_09334_gb300/csrc/cpqr.cu",
+                   "paper_1811_09334_gb300/csrc/cpqr_body.cuh"],
+        "sha256": "PENDING",
         "profile": "profiles/k_cpqr_wide_b110x4096.md",
         # dram__bytes_read.sum + dram__bytes_write.sum at n = 4096 columns
         # (3.72 MB + 9.7 KB), scaled by the columns processed
@@ -62,9 +64,12 @@ def _traffic(kind: str, n: int):
     if t is None:
         return None
     try:
-        with open(os.path.join(ROOT, t["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
-                return None
+        h = hashlib.sha256()
+        for src in t["source"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != t["sha256"]:
+            return None
     except OSError:
         return None
     return {"bytes": t["bytes_per_column"] * n, "profile": t["profile"],
@@ -296,10 +301,10 @@ def _run_batched(R, dev, count=512):
     Problems: m ~ U[256, 4096], n ~ U[128, m], k ~ U[8, 64], p = 8,
     A_i = X diag(j^-1.5) Y^T (FP32 QR of the Gaussian factors on the device,
     for generation speed).  Both engines are timed: the persistent kernel
-    (one kernel taking work items from a device list) and the graph of every
-    problem's kernels (launch shapes from the autotuner, cached); the
-    autotuner's choice is the headline of each form.  Compared with the FP64
-    per-matrix loop (rqlp() one problem at a time).
+    (one kernel taking work items from a device list, with its per-stage
+    CTA time) and the graph of every problem's kernels (launch shapes from
+    the autotuner, cached); the autotuner's choice is each form's headline.
+    Compared with the FP64 per-matrix loop (rqlp() one problem at a time).
     """
     import torch
     from paper_1811_09334_gb300 import autotune
@@ -336,6 +341,9 @@ def _run_batched(R, dev, count=512):
                           "work_items": b.work_items, "status": worst}
             if engine == "graph":
                 by[engine]["tuning"] = {k: v for k, v in tune.items() if k != "engine"}
+            else:
+                # where the persistent kernel's CTA time went (its own instrumentation)
+                by[engine]["stage_times"] = b.stage_times()
             b.close()
         pick = tune.get("engine", "graph")
         res[prec] = dict(by[pick], engine=pick)
@@ -673,6 +681,78 @@ def _oracle_one_core(A_np, Om_np, budget_s=120.0):
         os.unlink(opath)
 
 
+def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1, 2, 3, 4)):
+    """Throughput with P independent factorizations in flight: P streams, each
+    with its own workspace and outputs, taking the steps round robin (the
+    latency-bound kernels of one factorization leave SMs and memory idle that
+    another one uses).  A short sweep over P picks the count with the most
+    factorizations/s (a larger count only where it gains at least 3 %); K
+    steps are then timed with it, with the clocks sampled."""
+    import torch.distributed as dist
+    kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=form)
+    keys = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
+    streams = [torch.cuda.Stream() for _ in range(max(counts))]
+    slots = []
+    for s in streams:
+        o = R.rqlp(A, pr.k, pr.p, Om, stream=s, rvalues=False, **kw)
+        slots.append((o["ws"], {k: o[k] for k in keys}))
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+
+    def run(P, n):
+        for s in streams[:P]:
+            s.wait_stream(cur)
+        for i in range(n):
+            ws, buf = slots[i % P]
+            R.rqlp(A, pr.k, pr.p, Om, ws=ws, out=buf, check=False, stream=streams[i % P], **kw)
+        for s in streams[:P]:
+            cur.wait_stream(s)
+
+    def timed(P, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        run(P, n)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sweep = {}
+    for P in counts:
+        run(P, 2 * P)
+        sweep[P] = 4 * P / (timed(P, 4 * P) / 1e3)
+    best = counts[0]
+    for P in counts[1:]:
+        if sweep[P] > 1.03 * sweep[best]:
+            best = P
+    run(best, max(warmup, 1) * best)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    n0 = R.launch_count()
+    torch.cuda.nvtx.range_push("inflight_" + form)
+    ms = timed(best, steps)
+    torch.cuda.nvtx.range_pop()
+    launches = R.launch_count() - n0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    status = min(R.read_status(ws) for ws, _ in slots[:best])
+    if status < 0:
+        raise SystemExit("device status %d during the timed region" % status)
+    t = torch.tensor([ms], device=A.device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    out = dict(P=best, ms_total=float(t.item()), steps=steps, launches=launches, clocks=clk,
+               sweep={str(k): v for k, v in sweep.items()},
+               outputs={k: v.clone() for k, v in slots[0][1].items()})
+    del slots
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -713,9 +793,6 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = Clocks(local)
-        if form == args.prec:
-            clocks.start()
         n0 = R.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -731,7 +808,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         launches = R.launch_count() - n0
-        clk = clocks.stop() if form == args.prec else None
+        clk = None
         ms = e0.elapsed_time(e1)
         status = R.read_status(ws)
         if status < 0:
@@ -751,7 +828,12 @@ def run_ours(args):
         outs[form] = {k: v.clone() for k, v in buf.items()}
 
     main = results[args.prec]
-    value = world * main["steps"] / (main["ms_total"] / 1e3)
+    latency_ms = main["ms_total"] / main["steps"]
+    # the headline: factorizations/s with the best number of problems in flight
+    flight = _in_flight(R, torch, A, pr, Om, args.prec, args.steps, args.warmup, world, local)
+    same = all(torch.equal(flight["outputs"][k], outs[args.prec][k])
+               for k in ("Q", "L", "P", "Lvalues", "piv0", "piv1"))
+    value = world * flight["steps"] / (flight["ms_total"] / 1e3)
     flops = _sketch_flops(pr.m, pr.n, pr.l, Q_POW)
     peaks, peak_src = _peaks()
     # the FP64 rate is measured here (the peaks file has no FP64 entry)
@@ -905,13 +987,17 @@ def run_ours(args):
         line = {
             "metric": "erqlp_factorizations_per_s", "value": value, "unit": "factorizations/s",
             "n_gpus": world, "steps": main["steps"], "warmup": args.warmup,
-            "ms_per_step": main["ms_total"] / main["steps"], "higher_is_better": True,
+            "ms_per_step": flight["ms_total"] / flight["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else args.prec + "+f64",
             "data": "synthetic",
             "config": {"workload": workload_name(pr.m, pr.n), "m": pr.m, "n": pr.n,
                        "k": pr.k, "p": pr.p,
-                       "q": Q_POW, "d": D_INNER, "l2": _l2_note(pr.m, pr.n)},
+                       "q": Q_POW, "d": D_INNER, "l2": _l2_note(pr.m, pr.n),
+                       "problems_in_flight": flight["P"]},
+            "latency_ms_single_stream": latency_ms,
+            "in_flight_sweep": flight["sweep"],
+            "in_flight_outputs_identical": same,
             "sketch_tflops": forms_out[args.prec]["sketch_tflops"],
             "forms": forms_out,
             "roofline": roof,
@@ -919,8 +1005,8 @@ def run_ours(args):
             "batched": batched,
             "extra": extra,
             "e2e": e2e,
-            "gpu_launches": int(main["launches"]),
-            "clocks": main["clocks"],
+            "gpu_launches": int(flight["launches"]),
+            "clocks": flight["clocks"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -376,6 +376,18 @@ int rqlp_batched_kernel_nodes(rqlp_batch_t plan);
  * and, for the persistent engine, its work items per launch (else 0). */
 int rqlp_batched_engine(rqlp_batch_t plan, int64_t *items);
 
+/* Persistent engine only: where the last launch's CTA time went, per stage
+ * kind (16 slots; 1 preparation of A, 2 split of Omega, 3 products with A,
+ * 4 Gram tiles, 5 Cholesky, 6 solve tiles, 7 CPQR of B, 8 the l x l QLP
+ * part, 9 assembly, 10 status): busy_us[k], the microseconds CTAs spent
+ * running items of kind k, wait_us[k], the microseconds they spent taking
+ * such items (the queue and the wait for the previous stage), both summed
+ * over CTAs, and items[k], the items that ran (skipped conditional passes
+ * not counted).  Any pointer may be NULL.  Synchronizes `stream`;
+ * RQLP_ERR_INVALID_ARG for a graph-engine batch. */
+int rqlp_batched_stage_times(rqlp_batch_t plan, rqlp_stream_t stream, double *busy_us,
+                             double *wait_us, int64_t *items);
+
 /* Frees the graph (not the workspace, which the caller owns). */
 void rqlp_batched_destroy(rqlp_batch_t plan);
 

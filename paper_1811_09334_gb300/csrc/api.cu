@@ -359,21 +359,31 @@ struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
+// One side stream per caller stream (and host thread), so that problems in
+// flight on different streams do not queue behind each other's Q0.
 SideStream *side_for(cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return nullptr;
-  static thread_local SideStream sd;
-  if (!sd.s) {
-    if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess) {
-      sd.s = nullptr;
-      cudaGetLastError();
-      return nullptr;
-    }
+  struct Entry {
+    cudaStream_t main;
+    SideStream sd;
+  };
+  static thread_local std::vector<Entry> table;
+  if (table.capacity() < 64) table.reserve(64);  // entries never move
+  for (Entry &e : table)
+    if (e.main == st) return &e.sd;
+  if (table.size() >= 64) return nullptr;  // many streams: Q0 stays on the caller's stream
+  Entry e;
+  e.main = st;
+  if (cudaStreamCreateWithFlags(&e.sd.s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.sd.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.sd.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
   }
-  return &sd;
+  table.push_back(e);
+  return &table.back().sd;
 }
 
 // The pivoted QLP of the small w x n matrix B, given as Bt = B^T (n x w,

@@ -298,6 +298,12 @@ int rqlp_batched_engine(rqlp_batch_t plan, int64_t *items) {
   return plan->engine;
 }
 
+int rqlp_batched_stage_times(rqlp_batch_t plan, rqlp_stream_t stream, double *busy_us,
+                             double *wait_us, int64_t *items) {
+  if (!plan || plan->engine != RQLP_BATCH_PERSISTENT) return RQLP_ERR_INVALID_ARG;
+  return persist_stats(plan->pl, reinterpret_cast<cudaStream_t>(stream), busy_us, wait_us, items);
+}
+
 void rqlp_batched_destroy(rqlp_batch_t plan) {
   if (!plan) return;
   persist_release(&plan->pl);

@@ -74,6 +74,7 @@ enum StageKind : int {
   PK_ASM,        // Q = V Q_B and the rows of P
   PK_DONE        // the problem's status
 };
+constexpr int kPKinds = 16;  // stage kinds (index of the per-kind statistics)
 enum BufId : int { PB_OM = -1, PB_Y = 0, PB_V, PB_Z, PB_W, PB_R0T, PB_X, PB_COUNT };
 
 struct PStage {
@@ -118,6 +119,7 @@ struct PPlan {
   int *done;
   int *abort;
   const int32_t *iota;
+  unsigned long long *stats;  // [3][kPKinds]: busy ns, waiting ns, items per stage kind
   int nstages, nitems, tc, pivot2, d, ring;
   unsigned long long limit_ns;
 };
@@ -170,58 +172,156 @@ __device__ __forceinline__ void bf16_pair(float f, __nv_bfloat16 &h, __nv_bfloat
 
 // ---------------------------------------------------------------------------
 // Precision preparation (BF16x3 form): a 128 x 512 block of A into the BF16
-// pairs Ah, Al (row-major, ld ldn8) and A^T pairs Ath, Atl (ld ldm8), in
-// 128 x 128 pieces; the transposed halves go through shared memory.
+// pairs Ah, Al (row-major, ld ldn8) and A^T pairs Ath, Atl (ld ldm8).  The
+// block is copied into shared memory with cp.async as 16 pieces of 32 x 128
+// through a ring of 4 buffers (three pieces in flight while one is split: a
+// single CTA per SM needs that many bytes in flight), then split: lanes take
+// two neighbouring columns (BF16 pairs stored as 4-byte words), and the
+// transposed halves go through shared memory.
 constexpr int kTP = kPrepRows + 2;  // transposed rows of 130 BF16: 65 words, odd
+constexpr int kPieceRows = 32, kPrepRing = 4;
+
+__device__ __forceinline__ void cp_async_n(void *smem, const void *gmem, int bytes, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? bytes : 0;
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(sz)
+                 : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(sz)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(sz)
+                 : "memory");
+}
+
+// one 32 x 128 piece (rows pr0.., columns pc0..) into shared memory, zero
+// outside A, as one commit group
+template <typename T>
+__device__ __forceinline__ void prep_load(const PProb &p, const T *A, int64_t pr0, int nr,
+                                          int64_t pc0, int nc, bool v16, T *as) {
+  constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  if (v16) {
+    for (int e = threadIdx.x; e < kPieceRows * (128 / VE); e += kPT) {
+      const int r = e / (128 / VE), c = (e - r * (128 / VE)) * VE;
+      const bool ok = r < nr && c < nc;
+      const T *src = ok ? A + (pr0 + r) * p.lda + pc0 + c : A;
+      if (ok && c + VE > nc) {
+        for (int j = 0; j < VE; ++j)
+          cp_async_n(as + r * 128 + c + j, c + j < nc ? src + j : A, (int)sizeof(T), c + j < nc);
+      } else {
+        cp_async_n(as + r * 128 + c, src, 16, ok);
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < kPieceRows * 128; e += kPT) {
+      const int r = e >> 7, c = e & 127;
+      const bool ok = r < nr && c < nc;
+      cp_async_n(as + e, ok ? A + (pr0 + r) * p.lda + pc0 + c : A, (int)sizeof(T), ok);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 template <typename T>
 __device__ void prep_tile(const PProb &p, int tile, uint8_t *sm) {
   const int nbj = (int)cdiv(p.n, kPrepCols);
   const int64_t r0 = (int64_t)(tile / nbj) * kPrepRows, cb = (int64_t)(tile % nbj) * kPrepCols;
   const T *A = static_cast<const T *>(p.A);
-  __nv_bfloat16 *th = reinterpret_cast<__nv_bfloat16 *>(sm);  // [128 columns][kTP]
-  __nv_bfloat16 *tl = th + 128 * kTP;
+  T *ring = reinterpret_cast<T *>(sm);  // [kPrepRing][32][128]
+  __nv_bfloat16 *th =
+      reinterpret_cast<__nv_bfloat16 *>(sm + kPrepRing * kPieceRows * 128 * sizeof(T));
+  __nv_bfloat16 *tl = th + 128 * kTP;  // th, tl: [128 columns][kTP], 128 rows
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nr = (int)min((int64_t)kPrepRows, p.m - r0);
+  const int nrb = (int)min((int64_t)kPrepRows, p.m - r0);
   const int64_t cend = min(cb + kPrepCols, p.n);
-  for (int64_t c0 = cb; c0 < cend; c0 += 128) {
-    const int nc = (int)min((int64_t)128, p.n - c0);
-    for (int r = warp; r < nr; r += 8) {
-      const int64_t i = r0 + r;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = lane + 32 * q;
-        const float f = (c < nc) ? to_f32(A[i * p.lda + c0 + c]) : 0.0f;
-        __nv_bfloat16 h, lo;
-        bf16_pair(f, h, lo);
-        if (c < nc) {
-          p.Ah[i * p.ldn8 + c0 + c] = h;
-          p.Al[i * p.ldn8 + c0 + c] = lo;
-        }
-        th[c * kTP + r] = h;
-        tl[c * kTP + r] = lo;
-      }
+  const int ncp = (int)cdiv(cend - cb, 128);  // 128-column blocks
+  const bool v16 = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                   (((int64_t)p.lda * (int64_t)sizeof(T)) % 16 == 0);
+  constexpr int kQ = kPrepRows / kPieceRows;  // row pieces per column block
+  const int npc = kQ * ncp;
+  auto piece = [&](int k, int64_t &pr0, int &nr, int64_t &pc0, int &nc) {
+    const int cblk = k / kQ, q = k - cblk * kQ;
+    pc0 = cb + 128 * cblk;
+    nc = (int)min((int64_t)128, p.n - pc0);
+    pr0 = r0 + kPieceRows * q;
+    nr = (int)max((int64_t)0, min((int64_t)kPieceRows, p.m - pr0));
+  };
+  for (int k = 0; k < kPrepRing - 1; ++k) {
+    if (k < npc) {
+      int64_t pr0, pc0;
+      int nr, nc;
+      piece(k, pr0, nr, pc0, nc);
+      prep_load(p, A, pr0, nr, pc0, nc, v16, ring + (size_t)k * kPieceRows * 128);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");  // keep the group count
     }
-    __syncthreads();
-    for (int j = warp; j < nc; j += 8) {
-      __nv_bfloat16 *dh = p.Ath + (c0 + j) * p.ldm8 + r0;
-      __nv_bfloat16 *dl = p.Atl + (c0 + j) * p.ldm8 + r0;
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int ii = 2 * lane + 64 * hf;
-        if (ii + 1 < nr) {
-          *reinterpret_cast<__nv_bfloat162 *>(dh + ii) =
-              __halves2bfloat162(th[j * kTP + ii], th[j * kTP + ii + 1]);
-          *reinterpret_cast<__nv_bfloat162 *>(dl + ii) =
-              __halves2bfloat162(tl[j * kTP + ii], tl[j * kTP + ii + 1]);
-        } else if (ii < nr) {
-          dh[ii] = th[j * kTP + ii];
-          dl[ii] = tl[j * kTP + ii];
-        }
-      }
-    }
-    __syncthreads();
   }
+  for (int k = 0; k < npc; ++k) {
+    const int kn = k + kPrepRing - 1;
+    if (kn < npc) {
+      int64_t qr0, qc0;
+      int qnr, qnc;
+      piece(kn, qr0, qnr, qc0, qnc);
+      prep_load(p, A, qr0, qnr, qc0, qnc, v16,
+                ring + (size_t)(kn % kPrepRing) * kPieceRows * 128);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group 3;" ::: "memory");  // piece k has landed
+    __syncthreads();
+    int64_t pr0, pc0;
+    int nr, nc;
+    piece(k, pr0, nr, pc0, nc);
+    const T *a = ring + (size_t)(k % kPrepRing) * kPieceRows * 128;
+    const int rofs = kPieceRows * (k % kQ);  // rows of this piece within the transposed tile
+    for (int r = warp; r < nr; r += 8) {
+      const int64_t i = pr0 + r;
+#pragma unroll
+      for (int hq = 0; hq < 2; ++hq) {
+        const int c = 2 * lane + 64 * hq;
+        __nv_bfloat16 h0, l0, h1, l1;
+        bf16_pair(to_f32(a[r * 128 + c]), h0, l0);
+        bf16_pair(to_f32(a[r * 128 + c + 1]), h1, l1);
+        if (c + 1 < nc) {
+          *reinterpret_cast<__nv_bfloat162 *>(p.Ah + i * p.ldn8 + pc0 + c) =
+              __halves2bfloat162(h0, h1);
+          *reinterpret_cast<__nv_bfloat162 *>(p.Al + i * p.ldn8 + pc0 + c) =
+              __halves2bfloat162(l0, l1);
+        } else if (c < nc) {
+          p.Ah[i * p.ldn8 + pc0 + c] = h0;
+          p.Al[i * p.ldn8 + pc0 + c] = l0;
+        }
+        th[c * kTP + rofs + r] = h0;
+        tl[c * kTP + rofs + r] = l0;
+        th[(c + 1) * kTP + rofs + r] = h1;
+        tl[(c + 1) * kTP + rofs + r] = l1;
+      }
+    }
+    __syncthreads();
+    if (k % kQ == kQ - 1) {
+      // every row piece of this column block is in th / tl: write A^T
+      for (int j = warp; j < nc; j += 8) {
+        __nv_bfloat16 *dh = p.Ath + (pc0 + j) * p.ldm8 + r0;
+        __nv_bfloat16 *dl = p.Atl + (pc0 + j) * p.ldm8 + r0;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int ii = 2 * lane + 64 * hf;
+          if (ii + 1 < nrb) {
+            *reinterpret_cast<__nv_bfloat162 *>(dh + ii) =
+                __halves2bfloat162(th[j * kTP + ii], th[j * kTP + ii + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(dl + ii) =
+                __halves2bfloat162(tl[j * kTP + ii], tl[j * kTP + ii + 1]);
+          } else if (ii < nrb) {
+            dh[ii] = th[j * kTP + ii];
+            dl[ii] = tl[j * kTP + ii];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   fence_proxy_async();
 }
 
@@ -465,9 +565,12 @@ __device__ void prod_f64(const PProb &p, const PStage &s, int tile, uint8_t *sm)
 // CholeskyQR pass pieces (the algorithms of cholqr.cu on one CTA each).
 //
 // Gram tile: the upper triangle of X_t^T X_t for 128 rows, in 4 x 4 register
-// tiles of the triangle (at most 3 per thread for l <= 128), the rows staged
-// 32 at a time; T = float: each 32-row chunk is rounded to FP32 and summed in
-// FP32, the chunks in FP64 (as the FP32 pass of cholqr.cu).
+// tiles of the triangle, the rows staged 32 at a time.  When the triangle has
+// at most 128 tiles (l <= 60) the rows of each chunk are dealt to G = 256 /
+// tiles groups of threads (every thread busy) and the groups' sums are added
+// in a fixed order at the end; otherwise each thread takes up to 3 tiles.
+// T = float: each 32-row chunk is rounded to FP32 and summed in FP32, the
+// chunks in FP64 (as the FP32 pass of cholqr.cu).
 template <typename T>
 __device__ void gram_tile(const PProb &p, const PStage &s, int tile, uint8_t *sm) {
   const double *X = p.buf[s.src];
@@ -475,13 +578,16 @@ __device__ void gram_tile(const PProb &p, const PStage &s, int tile, uint8_t *sm
   const int64_t rows = stage_rows(p, s), r0 = (int64_t)tile * kGramRows;
   const int nr = (int)min((int64_t)kGramRows, rows - r0);
   const int lp = ((l + 3) / 4) * 4 + 1;
-  T *xs = reinterpret_cast<T *>(sm);  // [32][lp]
+  T *xs = reinterpret_cast<T *>(sm);                            // [32][lp]
+  double *red = reinterpret_cast<double *>(sm + 32 * 129 * 8);  // [G][tiles][16]
   const int nb = (l + 3) / 4, ntiles = nb * (nb + 1) / 2;
+  const int G = (2 * ntiles <= kPT) ? min(8, kPT / ntiles) : 1;
   const int tid = threadIdx.x;
+  const int g = G > 1 ? tid / ntiles : 0;
   int bi[3], bj[3];
 #pragma unroll
   for (int u = 0; u < 3; ++u) {
-    int t = tid + kPT * u, b = 0;
+    int t = G > 1 ? ((u == 0 && g < G) ? tid % ntiles : -1) : tid + kPT * u, b = 0;
     if (t >= ntiles) t = -1;
     if (t >= 0) {
       while (t >= nb - b) {
@@ -517,7 +623,7 @@ __device__ void gram_tile(const PProb &p, const PStage &s, int tile, uint8_t *sm
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-      for (int r = 0; r < cr; ++r) {
+      for (int r = g; r < cr; r += G) {
         const T *row = xs + r * lp;
         T x[4], y[4];
 #pragma unroll
@@ -534,6 +640,27 @@ __device__ void gram_tile(const PProb &p, const PStage &s, int tile, uint8_t *sm
 #pragma unroll
         for (int b = 0; b < 4; ++b) accd[u][a][b] += to_f64(acc[a][b]);
     }
+  }
+  if (G > 1) {
+    // the row groups' partial sums, added in group order
+    if (bi[0] >= 0) {
+      double *my = red + ((size_t)g * ntiles + tid % ntiles) * 16;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) my[a * 4 + b] = accd[0][a][b];
+    }
+    __syncthreads();
+    if (g == 0 && bi[0] >= 0) {
+      for (int h = 1; h < G; ++h) {
+        const double *o = red + ((size_t)h * ntiles + tid) * 16;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) accd[0][a][b] += o[a * 4 + b];
+      }
+    }
+    if (g != 0) bi[0] = -1;
   }
   double *out = p.gpart + (int64_t)tile * l * l;
 #pragma unroll
@@ -985,7 +1112,9 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(const __grid_constant__ PPla
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_skip;
   __shared__ int4 s_item;
+  __shared__ unsigned long long s_stat[3][kPKinds];
   const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid < 3 * kPKinds) (&s_stat[0][0])[tid] = 0ull;
   if (tid == 0) {
     s_abort = 0;
     if (P.tc) {
@@ -1008,8 +1137,10 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(const __grid_constant__ PPla
   tcx.tmem = P.tc ? s_tmem : 0u;
   tcx.s_abort = &s_abort;
   uint32_t ring = 0, accph = 0;
+  unsigned long long t_ready = 0;
   for (;;) {
     if (tid == 0) {
+      const unsigned long long t_ask = globaltimer_ns();
       const unsigned idx = atomicAdd(P.next, 1u);
       int4 it = make_int4(-1, 0, 0, 0);
       int skip = 0;
@@ -1047,6 +1178,8 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(const __grid_constant__ PPla
       }
       s_item = it;
       s_skip = skip;
+      t_ready = globaltimer_ns();
+      if (it.x >= 0) s_stat[1][P.stages[it.y].kind & (kPKinds - 1)] += t_ready - t_ask;
     }
     __syncthreads();
     const int4 it = s_item;
@@ -1056,8 +1189,13 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(const __grid_constant__ PPla
     if (tid == 0) {
       __threadfence();
       atomicAdd(P.done + P.probs[it.x].done0 + it.y, 1);
+      const int kd = P.stages[it.y].kind & (kPKinds - 1);
+      s_stat[0][kd] += globaltimer_ns() - t_ready;
+      s_stat[2][kd] += s_skip ? 0ull : 1ull;
     }
   }
+  __syncthreads();
+  if (tid < 3 * kPKinds && (&s_stat[0][0])[tid]) atomicAdd(P.stats + tid, (&s_stat[0][0])[tid]);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1158,6 +1296,7 @@ bool supported(const rqlp_problem *probs, int count, const rqlp_opts *o) {
 struct Layout {
   unsigned *next;
   int *abort, *done;
+  unsigned long long *stats;
   Ctrl *ctrls;
   size_t zero_bytes;
   PStage *stages;
@@ -1177,6 +1316,7 @@ void carve_all(void *ws, const rqlp_problem *probs, int count, const rqlp_opts &
   L.next = reinterpret_cast<unsigned *>(head);
   L.abort = reinterpret_cast<int *>(head ? head + 128 : nullptr);
   L.done = a.take<int>((size_t)count * nstages);
+  L.stats = a.take<unsigned long long>(3 * kPKinds);
   L.ctrls = a.take<Ctrl>((size_t)count);
   L.zero_bytes = a.off;
   L.stages = a.take<PStage>((size_t)nstages);
@@ -1454,6 +1594,7 @@ int persist_setup(const rqlp_problem *probs, int count, const rqlp_opts *o, void
   pp->done = L.done;
   pp->abort = L.abort;
   pp->iota = L.iota;
+  pp->stats = L.stats;
   pp->nstages = S;
   pp->nitems = (int)ni;
   pp->tc = tc ? 1 : 0;
@@ -1478,6 +1619,22 @@ int persist_enqueue(const PersistLaunch &pl, cudaStream_t st) {
   k_persist<<<pl.grid, kPT, pl.smem, st>>>(P);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+int persist_stats(const PersistLaunch &pl, cudaStream_t st, double *busy_us, double *wait_us,
+                  int64_t *items) {
+  if (!pl.params) return RQLP_ERR_INVALID_ARG;
+  const PPlan &P = *static_cast<const PPlan *>(pl.params);
+  unsigned long long h[3 * kPKinds];
+  if (cudaMemcpyAsync(h, P.stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  for (int k = 0; k < kPKinds; ++k) {
+    if (busy_us) busy_us[k] = (double)h[k] * 1e-3;
+    if (wait_us) wait_us[k] = (double)h[kPKinds + k] * 1e-3;
+    if (items) items[k] = (int64_t)h[2 * kPKinds + k];
+  }
+  return RQLP_OK;
 }
 
 void persist_release(PersistLaunch *pl) {

@@ -33,6 +33,12 @@ int persist_setup(const rqlp_problem *probs, int count, const rqlp_opts *o, void
 // Enqueues one launch (the zeroing and the kernel) on st; capturable.
 int persist_enqueue(const PersistLaunch &pl, cudaStream_t st);
 
+// Per stage kind (16 slots, kinds 1..10 used) of the last launch: the time
+// CTAs spent running items and waiting for them (dispatch and dependency
+// waits), summed over CTAs, and the items that ran.
+int persist_stats(const PersistLaunch &pl, cudaStream_t st, double *busy_us, double *wait_us,
+                  int64_t *items);
+
 void persist_release(PersistLaunch *pl);
 
 }  // namespace rqk

@@ -97,6 +97,7 @@ _SIGS = {
     "rqlp_batched_status": (_c_i32, [_c_p, _c_p, _c_p]),
     "rqlp_batched_kernel_nodes": (_c_i32, [_c_p]),
     "rqlp_batched_engine": (_c_i32, [_c_p, ctypes.POINTER(_c_i64)]),
+    "rqlp_batched_stage_times": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "rqlp_batched_destroy": (None, [_c_p]),
     "rqlp_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
     "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
@@ -577,6 +578,20 @@ class Batch:
     def engine(self) -> str:
         code = int(lib().rqlp_batched_engine(self.handle, None))
         return {1: "graph", 2: "persistent"}.get(code, "unknown")
+
+    STAGE_KINDS = {1: "prep_A", 2: "split_omega", 3: "products_with_A", 4: "gram", 5: "cholesky",
+                   6: "solve", 7: "cpqr_of_B", 8: "qlp_l_by_l", 9: "assembly", 10: "status"}
+
+    def stage_times(self, stream=None) -> dict:
+        """Persistent engine: per stage kind of the last launch, the CTA time
+        spent running items (busy_us) and taking them (wait_us: the queue and
+        the previous stage), summed over CTAs, and the items that ran."""
+        busy, wait, items = (ctypes.c_double * 16)(), (ctypes.c_double * 16)(), (_c_i64 * 16)()
+        _check(lib().rqlp_batched_stage_times(self.handle, _stream(stream), ctypes.cast(busy, _c_p),
+                                              ctypes.cast(wait, _c_p), ctypes.cast(items, _c_p)),
+               "rqlp_batched_stage_times")
+        return {name: {"busy_us": busy[k], "wait_us": wait[k], "items": int(items[k])}
+                for k, name in self.STAGE_KINDS.items()}
 
     @property
     def work_items(self) -> int:

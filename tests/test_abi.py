@@ -122,3 +122,37 @@ def test_batch_engine_selection_by_workspace_size(lib):
                                             ctypes.byref(R.BatchTuning(4, 0, 0, 1)))
     assert lib.rqlp_batched_workspace_size(probs, 3, ctypes.byref(o),
                                            ctypes.byref(R.BatchTuning(4, 0, 0, 7))) == 0
+
+
+def _problems(shapes):
+    # fake (never dereferenced) device pointers: the size queries only read shapes
+    probs = (R.Problem * len(shapes))()
+    for i, (m, n, k) in enumerate(shapes):
+        f = ctypes.c_void_p(4096 * (i + 1))
+        probs[i] = R.Problem(f, 0, k, m, n, n, 8, 0, f, k + 8, f, f, f, f, f, f)
+    return probs
+
+
+def test_batch_engine_selection_by_workspace_size(lib):
+    shapes = [(700, 500, 40), (300, 200, 20), (1000, 900, 64)]
+    probs = _problems(shapes)
+    o = R.opts(q=1, d=2, pivot2=False, prec="bf16x3")
+    size = {e: lib.rqlp_batched_workspace_size(probs, 3, ctypes.byref(o),
+                                               ctypes.byref(R.BatchTuning(4, 0, 0, c)))
+            for e, c in R.ENGINES.items()}
+    assert size["persistent"] > 0 and size["graph"] > 0
+    assert size["auto"] == size["persistent"]
+    # the persistent engine keeps every problem's BF16 copies of A at once
+    assert size["persistent"] > 8 * sum(m * n for m, n, _ in shapes)
+    # l = 136 > 128, a precision it lacks, a truncation: not for the persistent kernel
+    big = _problems([(700, 500, 128)])
+    for oo, pr in ((o, big), (R.opts(prec="tf32x3"), probs), (R.opts(truncate_k=True), probs)):
+        n = 1 if pr is big else 3
+        assert lib.rqlp_batched_workspace_size(pr, n, ctypes.byref(oo),
+                                               ctypes.byref(R.BatchTuning(4, 0, 0, 2))) == 0
+        assert lib.rqlp_batched_workspace_size(pr, n, ctypes.byref(oo),
+                                               ctypes.byref(R.BatchTuning(4, 0, 0, 0))) == \
+            lib.rqlp_batched_workspace_size(pr, n, ctypes.byref(oo),
+                                            ctypes.byref(R.BatchTuning(4, 0, 0, 1)))
+    assert lib.rqlp_batched_workspace_size(probs, 3, ctypes.byref(o),
+                                           ctypes.byref(R.BatchTuning(4, 0, 0, 7))) == 0

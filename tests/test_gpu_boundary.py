@@ -192,3 +192,27 @@ def test_autograd_of_a_bf16x3_forward_uses_its_pivots(R):
     ref = O.rqlp_vjp(A32.astype(np.float64), pr.k, pr.p, Om, None, dL, None, q=1, piv0=p0, piv1=p1)
     gn = g.double().cpu().numpy()
     assert np.linalg.norm(gn - ref) <= 1e-2 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64tc"])
+def test_factorizations_in_flight_on_several_streams_are_the_single_stream_one(R, prec):
+    # three problems at once on three streams (each its own workspace): every
+    # output equals the single-stream factorization bit for bit
+    pr = W.c1(m=3000, n=2500, k=40, p=10)
+    A = _t(pr.A)
+    Om = _t(W.omega(pr.n, pr.l, 6))
+    kw = dict(q=1, d=2, pivot2=False, prec=prec)
+    ref = R.rqlp(A, pr.k, pr.p, Om, **kw)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    outs = []
+    cur = torch.cuda.current_stream()
+    for s in streams:
+        s.wait_stream(cur)
+    for rep in range(2):
+        for s in streams:
+            outs.append(R.rqlp(A, pr.k, pr.p, Om, stream=s, check=False, **kw))
+    torch.cuda.synchronize()
+    for o in outs:
+        assert R.read_status(o["ws"]) == 0
+        for key in ("Q", "L", "P", "Lvalues", "piv0", "piv1"):
+            assert torch.equal(o[key], ref[key]), key
