@@ -213,6 +213,7 @@ def test_factorizations_in_flight_on_several_streams_are_the_single_stream_one(R
             outs.append(R.rqlp(A, pr.k, pr.p, Om, stream=s, check=False, **kw))
     torch.cuda.synchronize()
     for o in outs:
-        assert R.read_status(o["ws"]) == 0
+        # the same status too (this spectrum makes the shifted pass run: a warning)
+        assert R.read_status(o["ws"]) == ref["status"] >= 0
         for key in ("Q", "L", "P", "Lvalues", "piv0", "piv1"):
             assert torch.equal(o[key], ref[key]), key
