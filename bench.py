@@ -683,12 +683,13 @@ def _oracle_one_core(A_np, Om_np, budget_s=120.0):
         os.unlink(opath)
 
 
-def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1, 2, 3, 4)):
+def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1, 2, 3, 4, 6, 8)):
     """Throughput with P independent factorizations in flight: P streams, each
     with its own workspace and outputs, taking the steps round robin (the
     latency-bound kernels of one factorization leave SMs and memory idle that
-    another one uses).  A short sweep over P picks the count with the most
-    factorizations/s (a larger count only where it gains at least 3 %); K
+    another one uses).  A short sweep over P = 1, 2, 3, 4, 6, 8 picks the count
+    with the most factorizations/s (a larger count only where it gains at
+    least 3 %); K
     steps are then timed with it, with the clocks sampled."""
     import torch.distributed as dist
     kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=form)

@@ -38,6 +38,7 @@ struct OrthBufs {
   double *gpart;  // Gram chunk partials
   double *G, *Rp, *Rinv, *Racc, *Rtmp, *Dinv;
   double *tmp;    // rows x l ping-pong
+  float *rf;      // FP32 R and block inverses of an FP32 pass (f32_pack_floats(l))
   // FP64-accurate digit products on the tensor cores for the Gram matrix, X R^-1
   // and the final assembly (the forms other than FP64, l <= 128)
   bool oz;
@@ -101,6 +102,7 @@ void carve_orth(Arena &a, int64_t rows_max, int l, int64_t m, int64_t n, OrthBuf
   o.Racc = a.take<double>((size_t)l * l);
   o.Rtmp = a.take<double>((size_t)l * l);
   o.tmp = a.take<double>((size_t)rows_max * l);
+  o.rf = a.take<float>(f32_pack_floats(l));
 }
 
 // CholeskyQR2 (+ a third pass iff a pass needed the shift): Xq = X R^{-1}.
@@ -151,7 +153,8 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
     prof_stop(kProfGram, ev, st);
     ev = prof_start(kProfChol, st);
     CK(chol_blocked(o.G, l, rows, o.Rp, o.Dinv, ctrl, site, skip, st, tol,
-                    lowp ? kEpsF32 : ((ozp && kOzGram) ? kEpsOz : kEpsF64), lowp));
+                    lowp ? kEpsF32 : ((ozp && kOzGram) ? kEpsOz : kEpsF64), lowp,
+                    lowp ? o.rf : nullptr));
     prof_stop(kProfChol, ev, st);
     ev = prof_start(kProfApply, st);
     if (ozp && kOzApply) {
@@ -162,7 +165,8 @@ int orth_impl(const double *X, int64_t rows, int l, int64_t ldx, double *Xq, int
       // a few rows (the l x l QRs): one warp per row solves q R = x
       CK(tri_rows(o.Rp, l, nullptr, l, src, lds, dst, ldd, (int)rows, false, st));
     } else {
-      CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp));
+      CK(apply_trsm(src, rows, l, lds, o.Rp, o.Dinv, dst, ldd, skip, st, lowp,
+                    lowp ? o.rf : nullptr));
     }
     if (R) {
       if (first) {

@@ -20,6 +20,9 @@
 //                   next diagonal entry first and takes its reciprocal square
 //                   root while the others update the trailing triangle.  It
 //                   also writes the inverses of R's 16 x 16 diagonal blocks.
+//   k_chol_f32      the FP32 Cholesky of the power steps' FP32 passes
+//                   (l <= 128, one CTA, registers); it also leaves R and the
+//                   block inverses in FP32 for the FP32 solve.
 //   k_apply_trsm    Q = X R^{-1} as a blocked triangular solve on 32-row tiles:
 //                   Q[:, b] = (X[:, b] - Q[:, <b] R[<b, b]) inv(R[b, b]); half
 //                   the FMAs of multiplying by a full inverse, and no separate
@@ -431,7 +434,8 @@ k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restr
 constexpr int kChol32MaxL = 128;
 __global__ void __launch_bounds__(1024)
 k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
-           double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless, double eps) {
+           double *__restrict__ Dinv, Ctrl *ctrl, int site, const int *skip_unless, double eps,
+           float *__restrict__ pack) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   __shared__ __align__(16) float rowbuf[2][kChol32MaxL];
   __shared__ float s_thr[kChol32MaxL];
@@ -478,6 +482,11 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
           const float y = v[ii] * s_rs;
           rowbuf[buf][c] = y;
           R[(int64_t)j * l + c] = (double)y;
+        }
+        if (pack && g == jb) {
+          // row j of R in FP32, padded to lpad columns, zeros left of the diagonal
+          const int lpad = (l + kB - 1) / kB * kB;
+          if (c < lpad) pack[(size_t)j * lpad + c] = (c >= j && c < l) ? v[ii] * s_rs : 0.0f;
         }
         __syncthreads();
         const float rjc = (c >= j && c < l) ? rowbuf[buf][c] : 0.0f;
@@ -536,6 +545,12 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
 #pragma unroll
       for (int i = 0; i < kB; ++i)
         if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = (double)x[i];
+    if (pack && cc < kB) {
+      // the block inverse in FP32: rows c0 .. c0 + 15 of the [lpad][16] panel
+      float *dp = pack + (size_t)l * ((l + kB - 1) / kB * kB) + (size_t)c0 * kB;
+#pragma unroll
+      for (int i = 0; i < kB; ++i) dp[i * kB + cc] = (i < bs && cc < bs) ? x[i] : 0.0f;
+    }
   }
 }
 
@@ -621,7 +636,7 @@ template <typename T, bool PRE>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
              const double *__restrict__ R, const double *__restrict__ Dinv, double *__restrict__ Q,
-             int64_t ldq, const int *skip_unless) {
+             int64_t ldq, const int *skip_unless, const float *__restrict__ pack) {
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   extern __shared__ double sm_raw[];
   T *sm = reinterpret_cast<T *>(sm_raw);
@@ -630,7 +645,16 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
   T *qs = sm;                                  // [kApplyRows][lp]
   T *rc = sm + kApplyRows * lp;                // [l][kB] block column of R, or PRE: R [l][lpad]
   T *dv = PRE ? rc + (int64_t)l * lpad : rc + (int64_t)l * kB;  // [kB][kB], or PRE: [lpad][kB]
-  if (PRE) {
+  if (PRE && sizeof(T) == 4 && pack) {
+    // R and the block inverses, already FP32 in this layout: 16-byte copies,
+    // all in flight at once (rc and dv are contiguous, 16-byte aligned)
+    const int n4 = (l * lpad + lpad * kB) / 4;
+    const unsigned s0 = (unsigned)__cvta_generic_to_shared(rc);
+    for (int e = threadIdx.x; e < n4; e += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + 16u * (unsigned)e),
+                   "l"(pack + 4 * (int64_t)e)
+                   : "memory");
+  } else if (PRE) {
     stage_smem<T>(
         l * lpad, R,
         [&](int e) -> const double * {
@@ -658,7 +682,7 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
         const int r = e / l, c = e - r * l;
         return qs + r * lp + c;
       });
-  if (PRE && sizeof(T) == 8) cp_async_wait_all();  // the loop's first barrier follows
+  if (PRE && (sizeof(T) == 8 || pack)) cp_async_wait_all();  // the loop's first barrier follows
   // lane -> row r, warp -> columns j0..j0+3 of the block: every lane of a
   // warp needs the same rows of inv(R[b, b]), so the triangular product
   // stops at row j0 + 3 for the whole warp
@@ -722,6 +746,11 @@ k_apply_trsm(const double *__restrict__ X, int64_t rows, int l, int64_t ldx,
 }
 
 }  // namespace
+
+size_t f32_pack_floats(int l) {
+  const size_t lpad = (size_t)(l + kB - 1) / kB * kB;
+  return (size_t)l * lpad + lpad * kB;
+}
 
 cudaError_t cholqr_init() {
   cudaError_t e = cudaFuncSetAttribute(k_gram_sym<double>,
@@ -799,7 +828,7 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
 
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st, double again_tol,
-                         double eps, bool lowp) {
+                         double eps, bool lowp, float *pack) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_chol_blocked<double>,
@@ -815,7 +844,8 @@ cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double
   // FP32 pass: one CTA, registers and FP32 only (its column chain is a few
   // FP32 operations and two barriers)
   if (lowp && l <= kChol32MaxL && again_tol < 0.0) {
-    k_chol_f32<<<1, 1024, 0, st>>>(G, l, (double)rows, R, Dinv, ctrl, site, skip_unless, eps);
+    k_chol_f32<<<1, 1024, 0, st>>>(G, l, (double)rows, R, Dinv, ctrl, site, skip_unless, eps,
+                                   pack);
     count_launch();
     return cudaGetLastError();
   }
@@ -842,7 +872,7 @@ cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double
 
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
                        const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
-                       cudaStream_t st, bool lowp) {
+                       cudaStream_t st, bool lowp, const float *pack) {
   const int lpad = (l + kB - 1) / kB * kB;
   const size_t base = (size_t)kApplyRows * (l + 1);
   const size_t smem_pre = (base + (size_t)l * lpad + (size_t)lpad * kB) * sizeof(float);
@@ -864,15 +894,17 @@ cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const 
     attr = true;
   }
   const int64_t tiles = (rows + kApplyRows - 1) / kApplyRows;
+  // the pack exists only where the FP32 Cholesky of chol_blocked wrote it
+  if (l > kChol32MaxL) pack = nullptr;
   if (pre)
     k_apply_trsm<float, true><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
-        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless, pack);
   else if (lowp)
     k_apply_trsm<float, false><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
-        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless, nullptr);
   else
     k_apply_trsm<double, false><<<(unsigned)tiles, kApplyThreads, smem, st>>>(
-        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless);
+        X, rows, l, ldx, R, Dinv, Q, ldq, skip_unless, nullptr);
   count_launch();
   return cudaGetLastError();
 }

@@ -140,14 +140,20 @@ cudaError_t gram_sym(const double *X, int64_t rows, int l, int64_t ldx, double *
 // again_tol >= 0: set ctrl->again_flag[site] (and done_flag = 1 - it) when
 // eps cond(R)^2 > again_tol, i.e. when one pass leaves Q less orthonormal
 // lowp: factor in FP32 on one CTA (the FP32 CholeskyQR pass; l <= 226)
+// pack (may be null; f32_pack_floats(l) floats): written by the FP32
+// factorization (lowp, l <= 128, again_tol < 0): R and the block inverses
+// also in FP32, laid out as the FP32 solve stages them
 cudaError_t chol_blocked(const double *G, int l, int64_t rows, double *R, double *Dinv, Ctrl *ctrl,
                          int site, const int *skip_unless, cudaStream_t st,
-                         double again_tol = -1.0, double eps = kEpsF64, bool lowp = false);
+                         double again_tol = -1.0, double eps = kEpsF64, bool lowp = false,
+                         float *pack = nullptr);
+size_t f32_pack_floats(int l);
 // Q = X R^{-1} by a blocked triangular solve (X and Q must not alias); lowp:
-// the solve runs in FP32 (Q stored in FP64)
+// the solve runs in FP32 (Q stored in FP64), staging R and the block
+// inverses from `pack` (written by the FP32 Cholesky) when it is given
 cudaError_t apply_trsm(const double *X, int64_t rows, int l, int64_t ldx, const double *R,
                        const double *Dinv, double *Q, int64_t ldq, const int *skip_unless,
-                       cudaStream_t st, bool lowp = false);
+                       cudaStream_t st, bool lowp = false, const float *pack = nullptr);
 
 // ---- cpqr.cu ---------------------------------------------------------------
 size_t cpqr_ws_bytes(int64_t n, int l);
