@@ -896,29 +896,44 @@ def run_ours(args):
     if rank == 0 or world > 1:
         A_h = A.cpu().pin_memory()
         Om_h = torch.from_numpy(Om_np).pin_memory()
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=args.prec)
         out_keys = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
-        slots = [R.rqlp_host(A_h, pr.k, pr.p, Om_h, stream=streams[i], **kw) for i in range(2)]
-        hsteps = max(4, min(args.steps, 10))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(hsteps):
-            sl = slots[i % 2]
-            if i >= 2:
+        nmax = 4
+        streams = [torch.cuda.Stream() for _ in range(nmax)]
+        slots0 = [R.rqlp_host(A_h, pr.k, pr.p, Om_h, stream=streams[i], **kw)
+                  for i in range(nmax)]
+
+        def e2e_run(P, hsteps):
+            slots = list(slots0[:P])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(hsteps):
+                sl = slots[i % P]
+                if i >= P:
+                    R.host_wait(sl)
+                slots[i % P] = R.rqlp_host_async(A_h, pr.k, pr.p, Om_h, ws=sl["ws"],
+                                                 out={k: sl[k] for k in out_keys},
+                                                 stream=streams[i % P], **kw)
+            for sl in slots:
                 R.host_wait(sl)
-            slots[i % 2] = R.rqlp_host_async(A_h, pr.k, pr.p, Om_h, ws=sl["ws"],
-                                             out={k: sl[k] for k in out_keys},
-                                             stream=streams[i % 2], **kw)
-        for sl in slots:
-            R.host_wait(sl)
-        dt = time.perf_counter() - t0
+            return time.perf_counter() - t0
+
+        # the host-to-device link bounds this path: a few problems in flight
+        # keep it busy; the best of 2, 3, 4 is timed
+        e2e_sweep = {}
+        for P in (2, 3, 4):
+            e2e_sweep[P] = 3 * P / e2e_run(P, 3 * P)
+        pe = max(e2e_sweep, key=e2e_sweep.get)
+        hsteps = max(4, min(args.steps, 10), 2 * pe)
+        dt = e2e_run(pe, hsteps)
         l = pr.l
         h2d = A_h.numel() * A_h.element_size() + Om_h.numel() * 8
         d2h = (pr.m * l + l * l + pr.n * l + l) * 8 + (pr.n + l) * 4
         e2e = {"value": world * hsteps / dt, "unit": "factorizations/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "problems_in_flight": 2}
+               "problems_in_flight": pe,
+               "sweep": {str(k): v for k, v in e2e_sweep.items()}}
+        del slots0
 
     batched = None
     if not args.no_batched:
