@@ -17,8 +17,12 @@
 // GPU scope) and the waiting CTA reads (acquire).  The wait is bounded by
 // spin_limit_ns and records RQLP_ERR_TIMEOUT.  Items are taken in a
 // topological order and a CTA only ever waits for items that running CTAs
-// took before, so the kernel always makes progress, with or without every
-// CTA resident at once.
+// took before, so the kernel always makes progress.  The CPQR of B of a
+// problem whose columns do not fit in one CTA's shared memory is a gang of
+// up to 16 items that run together as the multi-CTA pivoting kernel of
+// cpqr.cu (one exchange per pivot step); the schedule hands a gang's items
+// out one after another, and the launch is cooperative, so every CTA is
+// resident and a gang always completes.
 //
 // Tiles write their results with ordinary stores and the products read the
 // BF16 copies through TMA (the async proxy), so every writer fences the
@@ -102,6 +106,7 @@ struct PProb {
   double *G, *Rp, *Dinv, *Racc, *Rtmp, *Q0, *QB, *Qi, *Macc, *T0, *T1, *Vh, *tau;
   int32_t *pscr;          // l pivots of the unpivoted QRs
   ulonglong2 *rec;        // the CPQR loop's record words (one CTA)
+  unsigned char *cpx;     // a gang's exchange state (zeroed before every launch)
   Ctrl *ctrl;
   int32_t *status_out;
   int done0;              // first stage counter of this problem
@@ -126,6 +131,18 @@ struct PPlan {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// CTAs of the CPQR of B (n columns of length l): as many as it takes for
+// every CTA's columns (l doubles each, plus 32 bytes of per-column state) to
+// sit in shared memory, at most kPGang; one when they fit in one CTA.
+constexpr int kPGang = 16;
+__host__ __device__ inline int cpqr_gang(int64_t n, int l) {
+  const int64_t sv = ((l + 1) & ~1) * 8;
+  const int64_t per = (int64_t)l * 8 + 32;
+  const int64_t cap = ((int64_t)kPSmem - sv) / per;  // columns per CTA in shared memory
+  const int64_t g = cdiv(n, cap > 0 ? cap : 1);
+  return (int)(g < 1 ? 1 : (g > kPGang ? kPGang : g));
+}
+
 __host__ __device__ inline int64_t stage_rows(const PProb &p, const PStage &s) {
   return s.rows_n ? p.n : p.m;
 }
@@ -142,6 +159,7 @@ __host__ __device__ inline int tiles_of(const PProb &p, const PStage &s, int tc)
     case PK_GRAM: return (int)cdiv(stage_rows(p, s), kGramRows);
     case PK_APPLY: return (int)cdiv(stage_rows(p, s), kApplyRowsP);
     case PK_ASM: return (int)(cdiv(p.m, kAsmRows) + cdiv(p.n, kAsmRows));
+    case PK_CPQR: return cpqr_gang(p.n, p.l);
     default: return 1;
   }
 }
@@ -905,7 +923,57 @@ __device__ void form_q_cta(const double *Vh, const double *tau, int l, double *Q
   __syncthreads();
 }
 
-__device__ void cpqr_item(const PPlan &P, const PProb &p, uint8_t *sm) {
+// Member b of the gang of G CTAs that factors B together (the multi-CTA
+// exchange of cpqr.cu: one tagged candidate record per CTA and pivot step,
+// the last arrival picks the winner); the member's columns stay in its
+// shared memory.  Member 0 then forms Q0.
+__device__ void cpqr_gang_item(const PPlan &P, const PProb &p, int G, int b, uint8_t *sm) {
+  const int l = p.l;
+  const int64_t n = p.n;
+  const int64_t cpb = cdiv(n, G);
+  const int64_t c0 = (int64_t)b * cpb, c1 = min(n, c0 + cpb);
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += kPT) p.piv0[i] = (int32_t)i;
+  __syncthreads();
+  cpqrk::CpqrParams c;
+  c.Bt = p.buf[PB_Z];
+  c.n = n;
+  c.l = l;
+  c.steps = l;
+  c.ldv = l;
+  c.ldb = l;
+  c.R0t = p.buf[PB_R0T];
+  c.ldr = l;
+  c.piv = p.piv0;
+  c.Vh = p.Vh;
+  c.tau = p.tau;
+  // the exchange state, laid out as cpqr.cu lays it out for G CTAs
+  c.arrive = reinterpret_cast<unsigned *>(p.cpx);
+  c.win = reinterpret_cast<ulonglong2 *>(p.cpx + 128);
+  c.rec = reinterpret_cast<ulonglong2 *>(p.cpx + 128 + 128 * (size_t)G);
+  c.pcol = c.rec + 2 * (size_t)G * cpqrk::kRecWords;
+  c.gcols = p.buf[PB_Z];  // the columns in place when they do not fit (not the case by construction)
+  c.ctrl = p.ctrl;
+  c.limit_ns = P.limit_ns;
+  c.extra = 0;
+  c.cpb = (int)cpb;
+  c.fpiv = nullptr;
+  const size_t sv = (size_t)((l + 1) & ~1) * sizeof(double);
+  const size_t need = sv + (size_t)cpb * l * sizeof(double) + (size_t)cpb * (3 * 8 + 2 * 4);
+  c.use_smem = need <= kPSmem ? 1 : 0;
+  double *w = reinterpret_cast<double *>(sm);
+  if (c.use_smem) cpqrk::cpqr_body<true>(c, G, b, w);
+  else cpqrk::cpqr_body<false>(c, G, b, w);
+  __syncthreads();
+  if (b != 0 || ld_volatile_i32(&p.ctrl->status) < 0) return;
+  form_q_cta(p.Vh, p.tau, l, p.Q0, sm);
+}
+
+__device__ void cpqr_item(const PPlan &P, const PProb &p, int tile, uint8_t *sm) {
+  const int G = cpqr_gang(p.n, p.l);
+  if (G > 1) {
+    cpqr_gang_item(P, p, G, tile, sm);
+    return;
+  }
   cpqr_cta(P, p, p.buf[PB_Z], p.n, p.buf[PB_R0T], p.piv0, nullptr, sm);
   if (ld_volatile_i32(&p.ctrl->status) < 0) return;
   form_q_cta(p.Vh, p.tau, p.l, p.Q0, sm);
@@ -1094,7 +1162,7 @@ __device__ void run_item(const PPlan &P, const PProb &p, const PStage &s, int ti
       if (s.lowp) apply_tile<float>(p, s, tile, sm);
       else apply_tile<double>(p, s, tile, sm);
       break;
-    case PK_CPQR: cpqr_item(P, p, sm); break;
+    case PK_CPQR: cpqr_item(P, p, tile, sm); break;
     case PK_TAIL: tail_item(P, p, sm); break;
     case PK_ASM: asm_tile(P, p, tile, sm); break;
     case PK_DONE:
@@ -1308,6 +1376,14 @@ struct Layout {
   size_t bytes;
 };
 
+// the exchange state of a gang of G CTAs (as cpqr.cu lays it out): the
+// arrival counter's line, one winner line per CTA, double-buffered tagged
+// candidate records and columns
+size_t gang_bytes(int G, int l) {
+  return 128 + 128 * (size_t)G + 2 * (size_t)G * cpqrk::kRecWords * sizeof(ulonglong2) +
+         2 * (size_t)G * l * sizeof(ulonglong2);
+}
+
 void carve_all(void *ws, const rqlp_problem *probs, int count, const rqlp_opts &o, int nstages,
                int64_t nitems, Layout &L) {
   Arena a(ws);
@@ -1318,6 +1394,12 @@ void carve_all(void *ws, const rqlp_problem *probs, int count, const rqlp_opts &
   L.done = a.take<int>((size_t)count * nstages);
   L.stats = a.take<unsigned long long>(3 * kPKinds);
   L.ctrls = a.take<Ctrl>((size_t)count);
+  // every gang's exchange state starts at zero in every launch
+  std::vector<unsigned char *> cpx((size_t)count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    const int G = cpqr_gang(probs[i].n, probs[i].k + probs[i].p);
+    if (G > 1) cpx[(size_t)i] = a.take<unsigned char>(gang_bytes(G, probs[i].k + probs[i].p));
+  }
   L.zero_bytes = a.off;
   L.stages = a.take<PStage>((size_t)nstages);
   L.probs = a.take<PProb>((size_t)count);
@@ -1360,6 +1442,7 @@ void carve_all(void *ws, const rqlp_problem *probs, int count, const rqlp_opts &
     p.tau = a.take<double>((size_t)l);
     p.pscr = a.take<int32_t>((size_t)l);
     p.rec = a.take<ulonglong2>(16);
+    p.cpx = cpx[(size_t)i];
     p.ctrl = L.ctrls ? L.ctrls + i : nullptr;
     if (tc) {
       p.ldn8 = (q.n + 7) / 8 * 8;
@@ -1394,7 +1477,12 @@ double tile_us(const PProb &p, const PStage &s, bool tc) {
     case PK_CHOL: return s.cond ? 1.0 : 5.0 + l * (s.lowp ? 0.6 : 1.5);
     case PK_APPLY:
       return s.cond ? 1.0 : 3.0 + kApplyRowsP * l * l * 0.5 / (s.lowp ? 40.0 * f64 : f64);
-    case PK_CPQR: return 20.0 + 1.5 * (double)p.n * l * l / f64 + 2.0 * l * l * l / f64;
+    case PK_CPQR: {
+      const int G = cpqr_gang(p.n, p.l);
+      if (G == 1) return 20.0 + 1.5 * (double)p.n * l * l / f64 + 2.0 * l * l * l / f64;
+      // a gang: its share of the FP64 work plus one exchange (~6 us) per pivot step
+      return 20.0 + 1.5 * (double)p.n * l * l / f64 / G + 6.0 * l;
+    }
     case PK_TAIL: return 20.0 + 4.0 * l * l * l / f64;
     case PK_ASM: return 2.0 + kAsmRows * l * l / f64;
     default: return 1.0;
@@ -1463,11 +1551,28 @@ std::vector<int4> schedule(const std::vector<PProb> &hp, const std::vector<PStag
     }
     const Ready r = ready.top();
     const size_t k = (size_t)r.p * S + r.s;
-    const int tile = handed[k]++;
-    order.push_back(make_int4(r.p, r.s, tile, 0));
-    const double end = now + dur[k];
-    finish[k] = std::max(finish[k], end);
-    workers.push(end);
+    if (st[(size_t)r.s].kind == PK_CPQR && tiles[k] > 1) {
+      // a gang: all its tiles one after another, to the next free workers,
+      // which start together
+      std::vector<double> starts(1, now);
+      for (int t = 1; t < tiles[k]; ++t) {
+        starts.push_back(workers.top());
+        workers.pop();
+      }
+      double t0 = now;
+      for (double x : starts) t0 = std::max(t0, x);
+      for (int t = 0; t < tiles[k]; ++t) {
+        order.push_back(make_int4(r.p, r.s, handed[k]++, 0));
+        workers.push(t0 + dur[k]);
+      }
+      finish[k] = t0 + dur[k];
+    } else {
+      const int tile = handed[k]++;
+      order.push_back(make_int4(r.p, r.s, tile, 0));
+      const double end = now + dur[k];
+      finish[k] = std::max(finish[k], end);
+      workers.push(end);
+    }
     if (handed[k] == tiles[k]) {
       ready.pop();
       if (r.s + 1 < S) pending.push({finish[k], r.p, r.s + 1});
@@ -1616,9 +1721,21 @@ int persist_enqueue(const PersistLaunch &pl, cudaStream_t st) {
   if (!pl.params) return RQLP_ERR_INVALID_ARG;
   if (cudaMemsetAsync(pl.zero_base, 0, pl.zero_bytes, st) != cudaSuccess) return RQLP_ERR_CUDA;
   const PPlan &P = *static_cast<const PPlan *>(pl.params);
-  k_persist<<<pl.grid, kPT, pl.smem, st>>>(P);
+  // a cooperative launch: every CTA is resident at once, which the gangs of
+  // the CPQR items (CTAs waiting for one another) need
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)pl.grid);
+  cfg.blockDim = dim3(kPT);
+  cfg.dynamicSmemBytes = (size_t)pl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_persist, P);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+  return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
 int persist_stats(const PersistLaunch &pl, cudaStream_t st, double *busy_us, double *wait_us,
