@@ -83,7 +83,7 @@ struct MmaArgs {
 // values per 128-byte K row (K tile of 128 elements instead of 64); TF32:
 // FP32 storage read as TF32, 32 values per 128-byte K row.  Every MMA
 // consumes 32 bytes of each K row (16 BF16, 8 TF32 or 32 E4M3 values).
-template <bool SPLIT, bool FP8 = false, bool TF32 = false>
+template <bool SPLIT, bool FP8 = false, bool TF32 = false, bool SW64 = false>
 __global__ void __launch_bounds__(128, 1)
 k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
            const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
@@ -95,9 +95,15 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  constexpr int KT = FP8 ? 128 : TF32 ? 32 : kTileK;  // K elements per stage
-  const uint32_t ybytes = (uint32_t)a.n_pad * 128;
-  const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (kXBytes + ybytes);
+  // SW64 (BF16 only): K tiles of 32 elements in the 64-byte swizzle, half the
+  // bytes per stage, so that a wide skinny operand still leaves room for
+  // several stages
+  constexpr int KT = FP8 ? 128 : TF32 ? 32 : SW64 ? 32 : kTileK;  // K elements per stage
+  constexpr uint32_t kXB = SW64 ? kXBytes / 2 : kXBytes;
+  constexpr uint32_t kRowB = SW64 ? 64u : 128u;  // bytes of one K row of a tile
+  constexpr int kSteps = SW64 ? 2 : 4;           // MMAs of K = 32 bytes per stage
+  const uint32_t ybytes = (uint32_t)a.n_pad * kRowB;
+  const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (kXB + ybytes);
   const int m_tile = blockIdx.x, split = blockIdx.y;
   const int kb0 = split * a.kb_per;
   const int nkb = min(a.kb_per, a.nk - kb0);
@@ -132,10 +138,10 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
         mbar_expect_tx(&bar_full[s], stage_bytes);
         const int kx = (kb0 + i) * KT, my = m_tile * kTileM;
         tma_load_2d(st, &tXh, kx, my, &bar_full[s]);
-        tma_load_2d(st + kXBytes, &tYh, kx, 0, &bar_full[s]);
+        tma_load_2d(st + kXB, &tYh, kx, 0, &bar_full[s]);
         if (SPLIT) {
-          tma_load_2d(st + kXBytes + ybytes, &tXl, kx, my, &bar_full[s]);
-          tma_load_2d(st + 2 * kXBytes + ybytes, &tYl, kx, 0, &bar_full[s]);
+          tma_load_2d(st + kXB + ybytes, &tXl, kx, my, &bar_full[s]);
+          tma_load_2d(st + 2 * kXB + ybytes, &tYl, kx, 0, &bar_full[s]);
         }
         issued = i + 1;
       }
@@ -159,14 +165,14 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
         }
         tc_fence_after();
         const uint32_t xh = smem_u32(smem + (size_t)s * stage_bytes);
-        const uint32_t yh = xh + kXBytes;
+        const uint32_t yh = xh + kXB;
         const uint32_t xl = yh + ybytes;
-        const uint32_t yl = xl + kXBytes;
+        const uint32_t yl = xl + kXB;
         // the accumulator of this k-block; its first k-block overwrites it
         const uint32_t td = tmem + (uint32_t)((i % a.nacc) * a.acc_cols);
         const uint32_t first = (i < a.nacc) ? 1u : 0u;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kSteps; ++k) {
           // 32 bytes along K inside the swizzled row: 16 BF16, 8 TF32 or 32 FP8 values
           const uint32_t off = k * 32;
           const uint32_t accum = (first && k == 0) ? 0u : 1u;
@@ -179,6 +185,14 @@ k_mma_bf16(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUte
             if (SPLIT) {
               mma_tf32(td, smem_desc(xh + off), smem_desc(yl + off), idesc, 1u);
               mma_tf32(td, smem_desc(xl + off), smem_desc(yh + off), idesc, 1u);
+            }
+            continue;
+          }
+          if (SW64) {
+            mma_bf16(td, smem_desc_sw64(xh + off), smem_desc_sw64(yh + off), idesc, accum);
+            if (SPLIT) {
+              mma_bf16(td, smem_desc_sw64(xh + off), smem_desc_sw64(yl + off), idesc, 1u);
+              mma_bf16(td, smem_desc_sw64(xl + off), smem_desc_sw64(yh + off), idesc, 1u);
             }
             continue;
           }
@@ -558,20 +572,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() { return tma_encode_fn(); }
 // (cols contiguous, ld elements per row), box of box_rows x (128 bytes) with
 // the 128-byte swizzle.
 bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld,
-              int box_rows, bool fp8 = false, bool tf32 = false) {
+              int box_rows, bool fp8 = false, bool tf32 = false, bool sw64 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int es = fp8 ? 1 : tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * es};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)((sw64 ? 64 : 128) / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = fp8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                  : tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUresult r = fn(map, dt, 2,
                   const_cast<void *>(base), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -580,6 +595,7 @@ int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct GemmPlan {
   int n_pad, stages, S, kb_per, nk;
+  bool sw64;  // BF16 tiles of 32 K elements in the 64-byte swizzle
   uint32_t tmem_cols;
   size_t smem;
 };
@@ -588,11 +604,19 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false,
                    bool tf32 = false) {
   GemmPlan g;
   g.n_pad = (int)round_up(l, 16);
-  const size_t ybytes = (size_t)g.n_pad * 128;
-  const size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
+  size_t ybytes = (size_t)g.n_pad * 128;
+  size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
   g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
+  // a wide skinny operand (the BF16 pair at l > 128) leaves room for two
+  // 128-byte stages only: take K tiles of 32 in the 64-byte swizzle instead
+  g.sw64 = !fp8 && !tf32 && g.stages < 3;
+  if (g.sw64) {
+    ybytes = (size_t)g.n_pad * 64;
+    stage = (split ? 2 : 1) * (kXBytes / 2 + ybytes);
+    g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
+  }
   g.smem = g.stages * stage + 1024;
-  const int kt = fp8 ? 128 : tf32 ? 32 : kTileK;
+  const int kt = fp8 ? 128 : tf32 ? 32 : g.sw64 ? 32 : kTileK;
   g.nk = (int)((K + kt - 1) / kt);
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   int S = (int)std::max<int64_t>(1, num_sms() / tiles);
@@ -614,12 +638,12 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   if (g.stages < 2) return RQLP_ERR_UNSUPPORTED;
   if ((int64_t)g.S * M * g.n_pad > mx.part_floats) return RQLP_ERR_WORKSPACE;
   CUtensorMap mXh, mXl, mYh, mYl;
-  if (!make_map(&mXh, Xh, M, K, ldx, kTileM, fp8, tf32) ||
-      !make_map(&mYh, Yh, l, K, ldy, g.n_pad, fp8, tf32))
+  if (!make_map(&mXh, Xh, M, K, ldx, kTileM, fp8, tf32, g.sw64) ||
+      !make_map(&mYh, Yh, l, K, ldy, g.n_pad, fp8, tf32, g.sw64))
     return RQLP_ERR_CUDA;
   if (split) {
-    if (!make_map(&mXl, Xl, M, K, ldx, kTileM, false, tf32) ||
-        !make_map(&mYl, Yl, l, K, ldy, g.n_pad, false, tf32))
+    if (!make_map(&mXl, Xl, M, K, ldx, kTileM, false, tf32, g.sw64) ||
+        !make_map(&mYl, Yl, l, K, ldy, g.n_pad, false, tf32, g.sw64))
       return RQLP_ERR_CUDA;
   } else {
     mXl = mXh;
@@ -649,6 +673,8 @@ int gemm_xyt(const MixedBufs &mx, bool split, int64_t M, int64_t K, int l, const
   if (fp8) k_mma_bf16<false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else if (tf32 && split) k_mma_bf16<true, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else if (tf32) k_mma_bf16<false, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else if (split && g.sw64) k_mma_bf16<true, false, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
+  else if (g.sw64) k_mma_bf16<false, false, false, true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else if (split) k_mma_bf16<true><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   else k_mma_bf16<false><<<grid, 128, g.smem, st>>>(mXh, mXl, mYh, mYl, a);
   count_launch();
@@ -695,6 +721,12 @@ int mixed_init() {
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess ||
       cudaFuncSetAttribute(k_mma_bf16<false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<true, false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemLimit - 1024)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mma_bf16<false, false, false, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(kSmemLimit - 1024)) != cudaSuccess)
     return RQLP_ERR_CUDA;
