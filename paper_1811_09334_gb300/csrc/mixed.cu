@@ -59,7 +59,7 @@ using namespace tc;
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;                // 64 BF16 = one 128-byte swizzle row
 constexpr uint32_t kXBytes = kTileM * kTileK * 2;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 5;  // ring stages: 4 for 128-byte K tiles, up to 5 for 64-byte ones
 constexpr size_t kSmemLimit = 227 * 1024;
 
 struct MmaArgs {
@@ -606,7 +606,7 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int l, bool split, bool fp8 = false,
   g.n_pad = (int)round_up(l, 16);
   size_t ybytes = (size_t)g.n_pad * 128;
   size_t stage = (split ? 2 : 1) * (kXBytes + ybytes);
-  g.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 2048) / stage);
+  g.stages = (int)std::min<size_t>(4, (kSmemLimit - 2048) / stage);
   // a wide skinny operand (the BF16 pair at l > 128) leaves room for two
   // 128-byte stages only: take K tiles of 32 in the 64-byte swizzle instead
   g.sw64 = !fp8 && !tf32 && g.stages < 3;
