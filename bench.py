@@ -689,8 +689,9 @@ def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1
     latency-bound kernels of one factorization leave SMs and memory idle that
     another one uses).  A short sweep over P = 1, 2, 3, 4, 6, 8 picks the count
     with the most factorizations/s (a larger count only where it gains at
-    least 3 %); K
-    steps are then timed with it, with the clocks sampled."""
+    least 3 %); K steps are then timed with it, with the clocks sampled.  Each
+    call passes the count as rqlp_opts.in_flight, which runs the pivoted QR of
+    B on half of the SMs (the same results bit for bit)."""
     import torch.distributed as dist
     kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=form)
     keys = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
@@ -707,7 +708,8 @@ def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1
             s.wait_stream(cur)
         for i in range(n):
             ws, buf = slots[i % P]
-            R.rqlp(A, pr.k, pr.p, Om, ws=ws, out=buf, check=False, stream=streams[i % P], **kw)
+            R.rqlp(A, pr.k, pr.p, Om, ws=ws, out=buf, check=False, stream=streams[i % P],
+                   in_flight=P, **kw)
         for s in streams[:P]:
             cur.wait_stream(s)
 
@@ -913,7 +915,7 @@ def run_ours(args):
                     R.host_wait(sl)
                 slots[i % P] = R.rqlp_host_async(A_h, pr.k, pr.p, Om_h, ws=sl["ws"],
                                                  out={k: sl[k] for k in out_keys},
-                                                 stream=streams[i % P], **kw)
+                                                 stream=streams[i % P], in_flight=P, **kw)
             for sl in slots:
                 R.host_wait(sl)
             return time.perf_counter() - t0

@@ -105,13 +105,20 @@ typedef struct {
   int32_t truncate_k;   /* 0: outputs l wide; 1: the rank-k truncation (the abstract's rank-k
                            L): Q m x k, L k x k, P n x k and k L-values, each with ld k
                            (Q[:, :k], L[:k, :k], P[:, :k] of the l-wide factorization) */
+  int32_t in_flight;    /* how many factorizations the caller keeps running at once, each on its
+                           own stream with its own workspace (0 or 1: one at a time).  With 2 or
+                           more, the column-pivoted QR of B, whose CTAs spend most of each
+                           pivot step waiting on the grid-wide exchange, runs on half of the
+                           SMs and leaves the others to the kernels of the other
+                           factorizations: a longer single factorization, more of them per
+                           second overall.  The results are identical bit for bit. */
 } rqlp_opts;
 
 /* Human-readable name of a status code. */
 const char *rqlp_status_string(int status);
 
 /* Library ABI version (major * 100 + minor); 200 added fixed_pivots, truncate_k,
- * rqlp_rvalues() and the pivot arguments of rqlp_backward(). */
+ * rqlp_rvalues() and the pivot arguments of rqlp_backward(); 201 added in_flight. */
 int rqlp_version(void);
 
 /* Bytes of device workspace rqlp() needs for these sizes and options

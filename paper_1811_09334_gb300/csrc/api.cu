@@ -311,6 +311,7 @@ bool valid_opts(const rqlp_opts *o) {
   if (o->spin_limit_ns < 0) return false;
   if (o->fixed_pivots != 0 && o->fixed_pivots != 1) return false;
   if (o->truncate_k != 0 && o->truncate_k != 1) return false;
+  if (o->in_flight < 0) return false;
   return true;
 }
 
@@ -405,9 +406,13 @@ int qlp_stage(const Plan &P, const rqlp_opts &o, int64_t m, int64_t n, int w, co
   const unsigned long long lim = (unsigned long long)o.spin_limit_ns;
   const unsigned extra = (o.debug_flags & 1) ? 1u : 0u;
   const int l = w;
+  // with other factorizations in flight the grid-wide pivoted QR takes half
+  // of the SMs: the others' kernels run on the rest while its CTAs wait on
+  // their exchanges
+  const int cpqr_ctas = o.in_flight >= 2 ? (num_sms() + 1) / 2 : 0;
   int ev = prof_start(kProfCpqr, st);
   CK(cpqr_wide(Bt, n, l, l, P.R0t, l, piv0, P.Vh, P.tau, P.cpqr_scratch, ctrl, lim, extra, st,
-               fp0));
+               fp0, cpqr_ctas));
   prof_stop(kProfCpqr, ev, st);
   CK(diag_of(P.R0t, l, l, rv, st));  // the R-values of Section 5
   // Q0 from the reflectors, beside the QR of R0^T (joined before Vh is
@@ -665,7 +670,7 @@ const char *rqlp_status_string(int s) {
   }
 }
 
-int rqlp_version(void) { return 200; }
+int rqlp_version(void) { return 201; }
 
 size_t rqlp_workspace_size(int64_t m, int64_t n, int32_t k, int32_t p, const rqlp_opts *opts) {
   if (!valid_dims(m, n, k, p) || !valid_opts(opts)) return 0;

@@ -57,10 +57,10 @@ struct Plan {
   size_t smem;
 };
 
-Plan plan_for(int64_t n, int l) {
+Plan plan_for(int64_t n, int l, int max_ctas) {
   Plan p;
   const int sms = num_sms();
-  const int cap = tuning().cpqr_max_ctas;
+  const int cap = max_ctas > 0 ? max_ctas : tuning().cpqr_max_ctas;
   int G = (int)std::min<int64_t>(n, (int64_t)((cap > 0 && cap < sms) ? cap : sms));
   if (G < 1) G = 1;
   int cpb = (int)((n + G - 1) / G);
@@ -72,6 +72,8 @@ Plan plan_for(int64_t n, int l) {
   p.smem = sv + (p.use_smem ? slab : 0) + state;
   p.G = G;
   p.cpb = cpb;
+  // a smaller grid asked for keeps the slabs in shared memory, or is not taken
+  if (max_ctas > 0 && !p.use_smem) return plan_for(n, l, 0);
   return p;
 }
 
@@ -92,7 +94,7 @@ size_t cpqr_ws_bytes(int64_t n, int l) {
 }
 
 size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits) {
-  const Plan pl = plan_for(n, l);
+  const Plan pl = plan_for(n, l, 0);
   *fits = pl.use_smem != 0 && pl.G <= kMaxGrid;
   return (tagged_bytes(pl.G, l) + 255) / 256 * 256;
 }
@@ -111,8 +113,8 @@ static cudaError_t cpqr_launch(const double *Bt, int64_t n, int64_t L, int steps
                                double *R0t, int64_t ldr, int32_t *piv, double *Vh, int64_t ldv,
                                double *tau, void *scratch, Ctrl *ctrl,
                                unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
-                               const int32_t *fixed_piv) {
-  Plan pl = plan_for(n, (int)L);
+                               const int32_t *fixed_piv, int max_ctas) {
+  Plan pl = plan_for(n, (int)L, max_ctas);
   if (pl.G > kMaxGrid || pl.smem > 220 * 1024) return cudaErrorInvalidValue;
   void *kfn = pl.use_smem ? (void *)k_cpqr_wide<true> : (void *)k_cpqr_wide<false>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -167,10 +169,10 @@ static cudaError_t cpqr_launch(const double *Bt, int64_t n, int64_t L, int steps
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
                       unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
-                      const int32_t *fixed_piv) {
+                      const int32_t *fixed_piv, int max_ctas) {
   if (n <= 0 || l <= 0 || l > kMaxL || l > n) return cudaErrorInvalidValue;
   return cpqr_launch(Bt, n, l, l, ldb, R0t, ldr, piv, Vh, l, tau, scratch, ctrl, limit_ns,
-                     debug_extra, st, fixed_piv);
+                     debug_extra, st, fixed_piv, max_ctas);
 }
 
 cudaError_t cpqr_tall(const double *At, int64_t n, int64_t L, int steps, int64_t ldat, double *R0t,
@@ -180,7 +182,7 @@ cudaError_t cpqr_tall(const double *At, int64_t n, int64_t L, int steps, int64_t
       ldv < steps || L > 16384)
     return cudaErrorInvalidValue;
   return cpqr_launch(At, n, L, steps, ldat, R0t, ldr, piv, Vh, ldv, tau, scratch, ctrl, limit_ns,
-                     0, st, nullptr);
+                     0, st, nullptr, 0);
 }
 
 }  // namespace rqk

@@ -166,10 +166,13 @@ size_t cpqr_scratch_bytes_smem_only(int64_t n, int l, bool *fits);
 // fixed_piv (device, l entries) step s takes column fixed_piv[s] instead of
 // the largest trailing norm: the unpivoted Householder QR of the permuted
 // matrix; an index out of range or repeated sets RQLP_ERR_INVALID_ARG.
+// max_ctas > 0: at most this many CTAs (one per SM otherwise), as long as
+// the column slabs still fit in shared memory; the results do not depend on
+// the grid.
 cudaError_t cpqr_wide(const double *Bt, int64_t n, int l, int64_t ldb, double *R0t, int64_t ldr,
                       int32_t *piv, double *Vh, double *tau, void *scratch, Ctrl *ctrl,
                       unsigned long long limit_ns, unsigned debug_extra, cudaStream_t st,
-                      const int32_t *fixed_piv = nullptr);
+                      const int32_t *fixed_piv = nullptr, int max_ctas = 0);
 // The first `steps` pivot steps of the column-pivoted Householder QR of an
 // L x n matrix (L <= 16384, steps <= 256) given as At = its transpose (n x L,
 // ld ldat): R0t (n x steps, ld ldr) holds the first `steps` rows of R as

@@ -30,7 +30,7 @@ _c_i32, _c_i64, _c_sz, _c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, c
 class Opts(ctypes.Structure):
     _fields_ = [("q", _c_i32), ("d", _c_i32), ("pivot2", _c_i32), ("prec", _c_i32),
                 ("block_b", _c_i32), ("debug_flags", _c_i32), ("spin_limit_ns", _c_i64),
-                ("fixed_pivots", _c_i32), ("truncate_k", _c_i32)]
+                ("fixed_pivots", _c_i32), ("truncate_k", _c_i32), ("in_flight", _c_i32)]
 
 
 class Problem(ctypes.Structure):
@@ -189,10 +189,10 @@ def lib():
 
 
 def opts(q=0, d=1, pivot2=True, prec="fp64", block_b=0, debug_flags=0, spin_limit_ns=0,
-         fixed_pivots=False, truncate_k=False) -> Opts:
+         fixed_pivots=False, truncate_k=False, in_flight=0) -> Opts:
     return Opts(int(q), int(d), 1 if pivot2 else 0, PREC[prec] if isinstance(prec, str) else int(prec),
                 int(block_b), int(debug_flags), int(spin_limit_ns), 1 if fixed_pivots else 0,
-                1 if truncate_k else 0)
+                1 if truncate_k else 0, int(in_flight))
 
 
 def _torch():
@@ -243,7 +243,8 @@ def read_status(ws, stream=None) -> int:
 def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
          prec: str = "fp64", block_b: int = 0, ws=None, out: Optional[dict] = None,
          stream=None, check: bool = True, debug_flags: int = 0, spin_limit_ns: int = 0,
-         piv0=None, piv1=None, truncate_k: bool = False, rvalues: bool = True) -> dict:
+         piv0=None, piv1=None, truncate_k: bool = False, rvalues: bool = True,
+         in_flight: int = 0) -> dict:
     """Randomized QLP A ~= Q L P^T on the GPU (Algorithms 2.1, 2.2 and 4.1).
 
     A: (m, n) float64/float32 CUDA tensor, row-major.  Omega: (n, k + p)
@@ -253,7 +254,9 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
     RqlpError.  Given piv0 (and piv1 for Algorithm 2.1), int32 CUDA tensors
     of at least k + p entries, the factorization is taken at those pivots
     (rqlp_opts.fixed_pivots).  truncate_k returns the rank-k truncation
-    (Q m x k, L k x k, P n x k).
+    (Q m x k, L k x k, P n x k).  in_flight: how many factorizations the
+    caller runs at once on separate streams (rqlp_opts.in_flight; the
+    results do not change).
     """
     torch = _torch()
     m, n = A.shape
@@ -271,7 +274,7 @@ def rqlp(A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
                 continue
             if t.dtype != torch.int32 or not t.is_contiguous() or t.numel() < need_n:
                 raise ValueError("given pivots must be contiguous int32 with >= k + p entries")
-    o = opts(q, d, pivot2, prec, block_b, debug_flags, spin_limit_ns, fixed, truncate_k)
+    o = opts(q, d, pivot2, prec, block_b, debug_flags, spin_limit_ns, fixed, truncate_k, in_flight)
     L_ = lib()
     need = L_.rqlp_workspace_size(m, n, k, p, ctypes.byref(o))
     if need == 0:
@@ -347,13 +350,13 @@ def brqlp_tol(A, b: int, l_max: int, tol: float, Omega, d: int = 1, pivot2: bool
 
 
 def _host_call(entry: str, A_host, k, p, Omega_host, q, d, pivot2, prec, block_b, ws, out,
-               device, stream) -> dict:
+               device, stream, in_flight=0) -> dict:
     torch = _torch()
     m, n = A_host.shape
     l = k + p
     if not A_host.is_contiguous() or not Omega_host.is_contiguous():
         raise ValueError("host inputs must be contiguous")
-    o = opts(q, d, pivot2, prec, block_b)
+    o = opts(q, d, pivot2, prec, block_b, in_flight=in_flight)
     L_ = lib()
     if stream is None:
         stream = torch.cuda.current_stream()  # the wait must use the same stream
@@ -397,14 +400,15 @@ def rqlp_host(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1, pivot2
 
 def rqlp_host_async(A_host, k: int, p: int, Omega_host, q: int = 0, d: int = 1,
                     pivot2: bool = True, prec: str = "fp64", block_b: int = 0, ws=None,
-                    out: Optional[dict] = None, device="cuda", stream=None) -> dict:
+                    out: Optional[dict] = None, device="cuda", stream=None,
+                    in_flight: int = 0) -> dict:
     """rqlp_host() without the final synchronization: everything is enqueued
     on `stream`.  The host tensors must stay alive and untouched, and the
     results are valid, only after host_wait() on the returned dict.  Calls
     with their own workspaces and streams overlap one problem's copies with
-    another's factorization."""
+    another's factorization (in_flight: how many such calls run at once)."""
     return _host_call("rqlp_host_async", A_host, k, p, Omega_host, q, d, pivot2, prec, block_b,
-                      ws, out, device, stream)
+                      ws, out, device, stream, in_flight)
 
 
 def host_wait(res: dict) -> int:

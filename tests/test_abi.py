@@ -156,3 +156,15 @@ def test_batch_engine_selection_by_workspace_size(lib):
                                             ctypes.byref(R.BatchTuning(4, 0, 0, 1)))
     assert lib.rqlp_batched_workspace_size(probs, 3, ctypes.byref(o),
                                            ctypes.byref(R.BatchTuning(4, 0, 0, 7))) == 0
+
+
+def test_in_flight_option_needs_no_other_workspace(lib):
+    # rqlp_opts.in_flight only changes the grid of the pivoted QR of B: the
+    # workspace covers every grid; a negative count is invalid
+    base = lib.rqlp_workspace_size(1000, 800, 20, 10, ctypes.byref(R.opts(q=1, d=2, pivot2=False)))
+    assert base > 0
+    for f in (1, 2, 8):
+        o = R.opts(q=1, d=2, pivot2=False, in_flight=f)
+        assert lib.rqlp_workspace_size(1000, 800, 20, 10, ctypes.byref(o)) == base
+    assert lib.rqlp_workspace_size(1000, 800, 20, 10, ctypes.byref(R.opts(in_flight=-1))) == 0
+    assert lib.rqlp_version() >= 201

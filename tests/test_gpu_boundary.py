@@ -196,8 +196,9 @@ def test_autograd_of_a_bf16x3_forward_uses_its_pivots(R):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp64tc"])
 def test_factorizations_in_flight_on_several_streams_are_the_single_stream_one(R, prec):
-    # three problems at once on three streams (each its own workspace): every
-    # output equals the single-stream factorization bit for bit
+    # three problems at once on three streams (each its own workspace, the
+    # count passed as in_flight: the pivoted QR of B then runs on half of the
+    # SMs): every output equals the single-stream factorization bit for bit
     pr = W.c1(m=3000, n=2500, k=40, p=10)
     A = _t(pr.A)
     Om = _t(W.omega(pr.n, pr.l, 6))
@@ -210,7 +211,7 @@ def test_factorizations_in_flight_on_several_streams_are_the_single_stream_one(R
         s.wait_stream(cur)
     for rep in range(2):
         for s in streams:
-            outs.append(R.rqlp(A, pr.k, pr.p, Om, stream=s, check=False, **kw))
+            outs.append(R.rqlp(A, pr.k, pr.p, Om, stream=s, check=False, in_flight=3, **kw))
     torch.cuda.synchronize()
     for o in outs:
         # the same status too (this spectrum makes the shifted pass run: a warning)
