@@ -430,7 +430,13 @@ k_chol_cluster(const double *__restrict__ G, int l, double rows, double *__restr
 // step), row j is scaled by its group and published in shared memory
 // (double-buffered by parity), and every thread applies it to its rows with
 // one broadcast row load per 4 rows.  Two barriers per column, no FP64 on
-// the chain; R and the block inverses are written in FP64.
+// the chain.  The column loop is bound by instruction issue (32 warps share
+// four schedulers), so the updates carry no per-entry tests: a warp with
+// nothing left (rows finished, columns finished or below the diagonal) skips
+// them, and the entries below the diagonal or beyond column l take updates
+// that are never read.  Conversions to and from FP64 use the integer pipe,
+// the diagonal blocks stay in shared memory for their inverses, and R and
+// the block inverses are written in FP64 (and in FP32 to `pack`).
 constexpr int kChol32MaxL = 128;
 __global__ void __launch_bounds__(1024)
 k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict__ R,
@@ -439,26 +445,39 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
   if (skip_unless && *reinterpret_cast<const volatile int *>(skip_unless) == 0) return;
   __shared__ __align__(16) float rowbuf[2][kChol32MaxL];
   __shared__ float s_thr[kChol32MaxL];
+  __shared__ float s_blk[kChol32MaxL / kB][kB][kB + 1];  // diagonal blocks of R
   __shared__ double red[32];
   __shared__ float s_rs;
   __shared__ int s_f;
   const int tid = threadIdx.x, c = tid & 127, g = tid >> 7;
   const int lane = tid & 31, warp = tid >> 5;
-  double tr = 0.0;
-  for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
-  tr = block_sum(tr, red);
   float v[16];
   int fail = 0;
   for (int att = 0; att < 2; ++att) {
-    const double shift = att ? 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr : 0.0;
+    double shift = 0.0;
+    if (att) {
+      double tr = 0.0;
+      for (int i = tid; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
+      tr = block_sum(tr, red);
+      shift = 11.0 * (rows * l + (double)l * (l + 1)) * eps * tr;
+    }
+    // eight loads in flight at a time (clamped indices, masked after)
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int a = 16 * g + i;
-      v[i] = (a < l && c >= a && c < l) ? (float)(G[(int64_t)a * l + c] + (c == a ? shift : 0.0))
-                                        : 0.0f;
+    for (int h = 0; h < 16; h += 8) {
+      double gv[8];
+      const int cl = min(c, l - 1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) gv[i] = G[(int64_t)min(16 * g + h + i, l - 1) * l + cl];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int a = 16 * g + h + i;
+        double x = gv[i];
+        if (att && c == a) x += shift;
+        v[h + i] = (a < l && c >= a && c < l) ? d2f_rn(x) : 0.0f;
+      }
     }
     for (int a = tid; a < l; a += blockDim.x)
-      s_thr[a] = (float)((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
+      s_thr[a] = d2f_rn((double)l * 2.0 * eps * (G[(int64_t)a * l + a] + shift));
     if (tid == 0) s_f = 0;
     __syncthreads();
     for (int jb = 0; jb * 16 < l; ++jb) {
@@ -478,28 +497,39 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
         }
         __syncthreads();
         if (s_f) { stop = true; break; }
-        if (g == jb && c >= j && c < l) {
-          const float y = v[ii] * s_rs;
-          rowbuf[buf][c] = y;
-          R[(int64_t)j * l + c] = (double)y;
-        }
-        if (pack && g == jb) {
-          // row j of R in FP32, padded to lpad columns, zeros left of the diagonal
-          const int lpad = (l + kB - 1) / kB * kB;
-          if (c < lpad) pack[(size_t)j * lpad + c] = (c >= j && c < l) ? v[ii] * s_rs : 0.0f;
+        if (g == jb) {
+          // row j of R (zeros left of the diagonal)
+          const float y = (c >= j && c < l) ? v[ii] * s_rs : 0.0f;
+          if (c >= j && c < l) rowbuf[buf][c] = y;
+          if (c < l) R[(int64_t)j * l + c] = f2d(y);
+          if (c >= j && c < 16 * jb + 16) s_blk[jb][ii][c - 16 * jb] = y;
+          if (pack && c < (l + kB - 1) / kB * kB) pack[(size_t)j * ((l + kB - 1) / kB * kB) + c] = y;  // padded to lpad columns
         }
         __syncthreads();
-        const float rjc = (c >= j && c < l) ? rowbuf[buf][c] : 0.0f;
-        const float4 *rb4 = reinterpret_cast<const float4 *>(&rowbuf[buf][16 * g]);
+        // this warp's columns are (c & ~31) .. (c | 31)
+        if (g >= jb && (c | 31) > j && (c | 31) >= 16 * g && (c & ~31) < l) {
+          const float rjc = rowbuf[buf][c];
+          const float4 *rb4 = reinterpret_cast<const float4 *>(&rowbuf[buf][16 * g]);
+          if (g > jb) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (16 * g + 4 * q + 3 <= j) continue;  // these four rows are finished
-          const float4 r4 = rb4[q];
-          const float ra[4] = {r4.x, r4.y, r4.z, r4.w};
+            for (int q = 0; q < 4; ++q) {
+              const float4 r4 = rb4[q];
+              v[4 * q] = fmaf(-r4.x, rjc, v[4 * q]);
+              v[4 * q + 1] = fmaf(-r4.y, rjc, v[4 * q + 1]);
+              v[4 * q + 2] = fmaf(-r4.z, rjc, v[4 * q + 2]);
+              v[4 * q + 3] = fmaf(-r4.w, rjc, v[4 * q + 3]);
+            }
+          } else {
+            // the group's own rows below row j (ii is known at compile time)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int i = 4 * q + k, a = 16 * g + i;
-            if (a > j && a <= c) v[i] = fmaf(-ra[k], rjc, v[i]);
+            for (int q = 0; q < 4; ++q) {
+              if (4 * q + 3 <= ii) continue;
+              const float4 r4 = rb4[q];
+              const float ra[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                if (4 * q + k > ii) v[4 * q + k] = fmaf(-ra[k], rjc, v[4 * q + k]);
+            }
           }
         }
       }
@@ -514,18 +544,12 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
     if (fail == 2) set_status(ctrl, RQLP_ERR_NONFINITE);
     else if (fail == 1) set_status(ctrl, RQLP_ERR_RANK_DEFICIENT);
   }
-  // zeros below the diagonal (rows were written above it)
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e / l, jj = e - i * l;
-    if (jj < i) R[e] = 0.0;
-  }
-  __syncthreads();
   // inverses of the 16 x 16 diagonal blocks in FP32, one warp per block
   const int nblk = (l + kB - 1) / kB;
   for (int bk = warp; bk < nblk; bk += (int)(blockDim.x >> 5)) {
     const int c0 = bk * kB, bs = min(kB, l - c0);
     const int cc = lane;
-    auto U = [&](int i, int t) { return (float)R[(int64_t)(c0 + i) * l + c0 + t]; };
+    auto U = [&](int i, int t) { return s_blk[bk][i][t]; };
     const float dl = (lane < bs) ? 1.0f / U(lane, lane) : 0.0f;
     float x[kB];
 #pragma unroll
@@ -544,7 +568,7 @@ k_chol_f32(const double *__restrict__ G, int l, double rows, double *__restrict_
     if (cc < bs)
 #pragma unroll
       for (int i = 0; i < kB; ++i)
-        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = (double)x[i];
+        if (i < bs) Dinv[(int64_t)(c0 + i) * l + c0 + cc] = f2d(x[i]);
     if (pack && cc < kB) {
       // the block inverse in FP32: rows c0 .. c0 + 15 of the [lpad][16] panel
       float *dp = pack + (size_t)l * ((l + kB - 1) / kB * kB) + (size_t)c0 * kB;
