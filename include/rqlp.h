@@ -110,8 +110,10 @@ typedef struct {
                            more, the column-pivoted QR of B, whose CTAs spend most of each
                            pivot step waiting on the grid-wide exchange, runs on half of the
                            SMs and leaves the others to the kernels of the other
-                           factorizations: a longer single factorization, more of them per
-                           second overall.  The results are identical bit for bit. */
+                           factorizations, and the FP64 Cholesky factorizations run on
+                           clusters of 8 CTAs instead of 16 (easier to place beside other
+                           kernels): a longer single factorization, more of them per second
+                           overall.  The results are identical bit for bit. */
 } rqlp_opts;
 
 /* Human-readable name of a status code. */

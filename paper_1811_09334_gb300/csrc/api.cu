@@ -587,10 +587,24 @@ int sum_squares(const void *X, int dtype, int64_t r, int64_t c, int64_t ld, doub
   return RQLP_OK;
 }
 
+// Launch shapes for a call with other factorizations in flight
+// (rqlp_opts.in_flight >= 2), for the duration of the call: the FP64
+// Cholesky on clusters of 8 CTAs, whose SMs are found sooner than 16 free
+// SMs of one GPC while other kernels run (the results do not change).  The
+// pivoted QR of B takes its half grid in qlp_stage.
+struct InFlightShapes {
+  Tuning saved;
+  explicit InFlightShapes(const rqlp_opts &o) : saved(tuning()) {
+    if (o.in_flight >= 2 && tuning().chol_ctas == 0) tuning().chol_ctas = 8;
+  }
+  ~InFlightShapes() { tuning() = saved; }
+};
+
 int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
              int32_t p, const double *Omega, int64_t ldo, const rqlp_opts &o, double *Q, double *L,
              double *Pout, double *Lvalues, int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
              cudaStream_t st) {
+  const InFlightShapes shapes(o);
   const int l = k + p;
   Plan P = carve(ws, m, n, l, o);
   if (P.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;

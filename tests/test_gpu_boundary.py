@@ -198,7 +198,8 @@ def test_autograd_of_a_bf16x3_forward_uses_its_pivots(R):
 def test_factorizations_in_flight_on_several_streams_are_the_single_stream_one(R, prec):
     # three problems at once on three streams (each its own workspace, the
     # count passed as in_flight: the pivoted QR of B then runs on half of the
-    # SMs): every output equals the single-stream factorization bit for bit
+    # SMs, the FP64 Cholesky on 8-CTA clusters): every output equals the
+    # single-stream factorization bit for bit
     pr = W.c1(m=3000, n=2500, k=40, p=10)
     A = _t(pr.A)
     Om = _t(W.omega(pr.n, pr.l, 6))
