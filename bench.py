@@ -49,11 +49,11 @@ _TRAFFIC = {
         # the kernel's launcher and its pivot-step loop (shared with the batch kernel)
         "source": ["paper_1811_09334_gb300/csrc/cpqr.cu",
                    "paper_1811_09334_gb300/csrc/cpqr_body.cuh"],
-        "sha256": "74b8706c6dc1f54b3668b5af0369e8922094a6fc13d1949e81a90321f9fb6212",
+        "sha256": "c637472d7c1c908bf7e457619b09619916af035ecd07d5b0eff41b0122e233ab",
         "profile": "profiles/k_cpqr_wide_b110x4096.md",
         # dram__bytes_read.sum + dram__bytes_write.sum at n = 4096 columns
-        # (3.719 MB + 7.9 KB), scaled by the columns processed
-        "bytes_per_column": (3.718656e6 + 7.936e3) / 4096,
+        # (3.718 MB + 2.8 KB), scaled by the columns processed
+        "bytes_per_column": (3.717632e6 + 2.816e3) / 4096,
     },
 }
 
@@ -925,7 +925,9 @@ def run_ours(args):
             return time.perf_counter() - t0
 
         # the host-to-device link bounds this path: a few problems in flight
-        # keep it busy; the best of 2, 3, 4 is timed
+        # keep it busy; the best of 2, 3, 4 is timed (after an untimed pass
+        # that loads the kernels the in-flight shapes use)
+        e2e_run(2, 4)
         e2e_sweep = {}
         for P in (2, 3, 4):
             e2e_sweep[P] = 3 * P / e2e_run(P, 3 * P)
