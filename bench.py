@@ -685,54 +685,73 @@ def _oracle_one_core(A_np, Om_np, budget_s=120.0):
 
 def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1, 2, 3, 4, 6, 8)):
     """Throughput with P independent factorizations in flight: P streams, each
-    with its own workspace and outputs, taking the steps round robin (the
-    latency-bound kernels of one factorization leave SMs and memory idle that
-    another one uses).  A short sweep over P = 1, 2, 3, 4, 6, 8 picks the count
-    with the most factorizations/s (a larger count only where it gains at
-    least 3 %); K steps of P factorizations (one per stream: a step is the
-    batch of P problems in flight) are then timed with it, with the clocks
-    sampled.  Each
-    call passes the count as rqlp_opts.in_flight, which runs the pivoted QR of
-    B on half of the SMs and the FP64 Cholesky on clusters of 8 CTAs (the
-    same results bit for bit)."""
+    with its own workspace and outputs, taking the factorizations round robin
+    (the latency-bound kernels of one factorization leave SMs and memory idle
+    that another one uses).  Every call passes the count as
+    rqlp_opts.in_flight, which runs the pivoted QR of B on half of the SMs and
+    the FP64 Cholesky on clusters of 8 CTAs (the same results bit for bit).
+    Two ways to issue a factorization are measured: a direct rqlp() call
+    (~110 kernel launches) and the replay of its recording (rqlp_graph_*, one
+    graph launch).  A short sweep over P = 1, 2, 3, 4, 6, 8 and both ways picks
+    the fastest (a larger P only where it gains at least 3 %); K steps of P
+    factorizations (one per stream: a step is the batch of P problems in
+    flight) are then timed with it, with the clocks sampled."""
     import torch.distributed as dist
     kw = dict(q=Q_POW, d=D_INNER, pivot2=False, prec=form)
     keys = ("Q", "L", "P", "Lvalues", "piv0", "piv1")
-    streams = [torch.cuda.Stream() for _ in range(max(counts))]
+    pmax = max(counts)
+    streams = [torch.cuda.Stream() for _ in range(pmax)]
     slots = []
     for s in streams:
         o = R.rqlp(A, pr.k, pr.p, Om, stream=s, rvalues=False, **kw)
         slots.append((o["ws"], {k: o[k] for k in keys}))
+    # recordings: one for a single stream (in_flight 0), pmax for P >= 2
+    g_one = R.Graph(A, pr.k, pr.p, Om, stream=streams[0], **kw)
+    g_many = [R.Graph(A, pr.k, pr.p, Om, stream=s, in_flight=pmax, **kw) for s in streams]
     torch.cuda.synchronize()
     cur = torch.cuda.current_stream()
 
-    def run(P, n):
+    def graphs_for(P):
+        return [g_one] if P == 1 else g_many[:P]
+
+    def run(P, n, mode):
         for s in streams[:P]:
             s.wait_stream(cur)
-        for i in range(n):
-            ws, buf = slots[i % P]
-            R.rqlp(A, pr.k, pr.p, Om, ws=ws, out=buf, check=False, stream=streams[i % P],
-                   in_flight=P, **kw)
+        if mode == "graph":
+            gs = graphs_for(P)
+            for i in range(n):
+                gs[i % P].launch(stream=streams[i % P])
+        else:
+            for i in range(n):
+                ws, buf = slots[i % P]
+                R.rqlp(A, pr.k, pr.p, Om, ws=ws, out=buf, check=False, stream=streams[i % P],
+                       in_flight=P, **kw)
         for s in streams[:P]:
             cur.wait_stream(s)
 
-    def timed(P, n):
+    def timed(P, n, mode):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(cur)
-        run(P, n)
+        run(P, n, mode)
         e1.record(cur)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    sweep = {}
-    for P in counts:
-        run(P, 2 * P)
-        sweep[P] = 4 * P / (timed(P, 4 * P) / 1e3)
-    best = counts[0]
-    for P in counts[1:]:
-        if sweep[P] > 1.03 * sweep[best]:
-            best = P
-    run(best, max(warmup, 1) * best)
+    sweep = {"direct": {}, "graph": {}}
+    for mode in ("direct", "graph"):
+        for P in counts:
+            run(P, 2 * P, mode)
+            sweep[mode][P] = 4 * P / (timed(P, 4 * P, mode) / 1e3)
+    # one factorization at a time from its recording, K replays
+    run(1, 2, "graph")
+    lat_graph = timed(1, steps, "graph") / steps
+    best, bmode = counts[0], "direct"
+    for mode in ("direct", "graph"):
+        for P in counts:
+            if sweep[mode][P] > 1.03 * sweep[bmode][best] or (
+                    P == best and sweep[mode][P] > sweep[bmode][best]):
+                best, bmode = P, mode
+    run(best, max(warmup, 1) * best, bmode)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -741,22 +760,30 @@ def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1
     clocks.start()
     n0 = R.launch_count()
     torch.cuda.nvtx.range_push("inflight_" + form)
-    ms = timed(best, steps * best)
+    ms = timed(best, steps * best, bmode)
     torch.cuda.nvtx.range_pop()
     launches = R.launch_count() - n0
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    status = min(R.read_status(ws) for ws, _ in slots[:best])
+    if bmode == "graph":
+        status = min(g.status() for g in graphs_for(best))
+        first = graphs_for(best)[0].out
+    else:
+        status = min(R.read_status(ws) for ws, _ in slots[:best])
+        first = slots[0][1]
     if status < 0:
         raise SystemExit("device status %d during the timed region" % status)
     t = torch.tensor([ms], device=A.device, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    out = dict(P=best, ms_total=float(t.item()), steps=steps, factorizations=steps * best,
-               launches=launches, clocks=clk,
-               sweep={str(k): v for k, v in sweep.items()},
-               outputs={k: v.clone() for k, v in slots[0][1].items()})
+    out = dict(P=best, mode=bmode, ms_total=float(t.item()), steps=steps,
+               factorizations=steps * best, launches=launches, clocks=clk,
+               sweep={m: {str(k): v for k, v in d.items()} for m, d in sweep.items()},
+               latency_ms_graph=lat_graph,
+               outputs={k: v.clone() for k, v in first.items()})
+    for g in [g_one] + g_many:
+        g.close()
     del slots
     torch.cuda.synchronize()
     return out
@@ -1021,8 +1048,10 @@ def run_ours(args):
                        "k": pr.k, "p": pr.p,
                        "q": Q_POW, "d": D_INNER, "l2": _l2_note(pr.m, pr.n),
                        "problems_in_flight": flight["P"],
-                       "step": "problems_in_flight factorizations, one per stream"},
+                       "step": "problems_in_flight factorizations, one per stream",
+                       "issue": flight["mode"]},
             "latency_ms_single_stream": latency_ms,
+            "latency_ms_single_stream_graph": flight["latency_ms_graph"],
             "in_flight_sweep": flight["sweep"],
             "in_flight_outputs_identical": same,
             "sketch_tflops": forms_out[args.prec]["sketch_tflops"],

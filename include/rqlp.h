@@ -120,7 +120,8 @@ typedef struct {
 const char *rqlp_status_string(int status);
 
 /* Library ABI version (major * 100 + minor); 200 added fixed_pivots, truncate_k,
- * rqlp_rvalues() and the pivot arguments of rqlp_backward(); 201 added in_flight. */
+ * rqlp_rvalues() and the pivot arguments of rqlp_backward(); 201 added in_flight and
+ * rqlp_graph_*. */
 int rqlp_version(void);
 
 /* Bytes of device workspace rqlp() needs for these sizes and options
@@ -399,6 +400,38 @@ int rqlp_batched_stage_times(rqlp_batch_t plan, rqlp_stream_t stream, double *bu
 
 /* Frees the graph (not the workspace, which the caller owns). */
 void rqlp_batched_destroy(rqlp_batch_t plan);
+
+/* ------------------------------------------------------------------------
+ * One factorization recorded once and replayed (a deployment feature the
+ * paper has no counterpart for).  rqlp() enqueues about 110 kernels; a
+ * replay of the recording is one CUDA graph launch.
+ * ---------------------------------------------------------------------- */
+typedef struct rqlp_graph *rqlp_graph_t;
+
+/* Arguments as for rqlp(), plus *graph [out].  The call first runs rqlp()
+ * once on `stream` (argument checks and one-time set-up; the outputs then
+ * hold that factorization) and synchronizes `stream`, then records the same
+ * call on a private stream into a graph.  The graph reads A, Omega (and the
+ * given pivots) and writes the outputs and the workspace at the addresses
+ * given here: to factor new data, write it to A (and Omega) in place and
+ * launch again.  The workspace belongs to the graph while it exists (one
+ * graph, or rqlp() call, at a time per workspace).  Returns rqlp()'s codes,
+ * or RQLP_ERR_CUDA if the recording fails (*graph is then NULL). */
+int rqlp_graph_create(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                      int32_t k, int32_t p, const double *Omega, int64_t ldo,
+                      const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+                      int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
+                      rqlp_stream_t stream, rqlp_graph_t *graph);
+
+/* Enqueues one replay on `stream` (any stream; replays of one graph must not
+ * overlap).  The device status is read with rqlp_read_status(ws, stream). */
+int rqlp_graph_launch(rqlp_graph_t graph, rqlp_stream_t stream);
+
+/* Library kernels one replay runs (what rqlp_launch_count() adds per launch). */
+int rqlp_graph_kernels(rqlp_graph_t graph);
+
+/* Frees the graph (not the workspace or the outputs). */
+void rqlp_graph_destroy(rqlp_graph_t graph);
 
 /*
  * rqlp_cpqr() for callers that cannot allocate device memory.  The paper has

@@ -1,5 +1,6 @@
 // Batched randomized QLP: many independent problems of uneven m, n, k in one
-// CUDA-graph launch, on one of two engines.
+// CUDA-graph launch, on one of two engines; and one factorization recorded
+// into a graph for replays (rqlp_graph_*, at the end).
 //
 // Persistent engine (persist.cu): one kernel of one CTA per SM takes
 // (problem, stage, tile) work items from an ordered device list; the graph
@@ -24,6 +25,12 @@
 #include "persist.cuh"
 
 using namespace rqk;
+
+struct rqlp_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;  // library kernels one replay runs
+};
 
 struct rqlp_batch {
   cudaGraph_t graph = nullptr;
@@ -310,6 +317,68 @@ void rqlp_batched_destroy(rqlp_batch_t plan) {
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
   delete plan;
+}
+
+// ---- one factorization recorded once, replayed with one launch -------------
+// rqlp() enqueues ~110 kernels; a replay of its recording costs one graph
+// launch and no host work per kernel.  The recording is made on a private
+// stream after one ordinary call on the caller's stream (which checks the
+// arguments and does every one-time set-up, none of which may happen inside a
+// capture); while recording, rqlp() keeps the Q0 work on the recorded stream
+// (no side stream), so the graph is one chain of kernels.
+int rqlp_graph_create(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                      int32_t k, int32_t p, const double *Omega, int64_t ldo,
+                      const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
+                      int32_t *piv0, int32_t *piv1, void *ws, size_t ws_bytes,
+                      rqlp_stream_t stream, rqlp_graph_t *out) {
+  if (!out) return RQLP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, opts, Q, L, P, Lvalues, piv0, piv1, ws,
+                ws_bytes, stream);
+  if (rc != RQLP_OK) return rc;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  cudaStream_t rec = nullptr;
+  if (cudaStreamCreateWithFlags(&rec, cudaStreamNonBlocking) != cudaSuccess) return RQLP_ERR_CUDA;
+  rqlp_graph *g = new rqlp_graph;
+  const long long n0 = launch_count();
+  if (cudaStreamBeginCapture(rec, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    rc = RQLP_ERR_CUDA;
+  } else {
+    rc = rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, opts, Q, L, P, Lvalues, piv0, piv1, ws,
+              ws_bytes, reinterpret_cast<rqlp_stream_t>(rec));
+    const cudaError_t ec = cudaStreamEndCapture(rec, &g->graph);
+    if (rc == RQLP_OK && ec != cudaSuccess) rc = RQLP_ERR_CUDA;
+  }
+  // the launches counted while recording ran nothing; each replay adds them
+  g->kernels = (int)(launch_count() - n0);
+  count_launch(-g->kernels);
+  if (rc == RQLP_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = RQLP_ERR_CUDA;
+  cudaStreamDestroy(rec);
+  if (rc != RQLP_OK) {
+    cudaGetLastError();
+    rqlp_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return RQLP_OK;
+}
+
+int rqlp_graph_launch(rqlp_graph_t graph, rqlp_stream_t stream) {
+  if (!graph || !graph->exec) return RQLP_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(graph->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  count_launch(graph->kernels);
+  return RQLP_OK;
+}
+
+int rqlp_graph_kernels(rqlp_graph_t graph) { return graph ? graph->kernels : 0; }
+
+void rqlp_graph_destroy(rqlp_graph_t graph) {
+  if (!graph) return;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  delete graph;
 }
 
 }  // extern "C"

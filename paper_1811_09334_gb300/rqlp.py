@@ -99,6 +99,12 @@ _SIGS = {
     "rqlp_batched_engine": (_c_i32, [_c_p, ctypes.POINTER(_c_i64)]),
     "rqlp_batched_stage_times": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "rqlp_batched_destroy": (None, [_c_p]),
+    "rqlp_graph_create": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p,
+                                   _c_i64, ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                   _c_p, _c_sz, _c_p, ctypes.POINTER(_c_p)]),
+    "rqlp_graph_launch": (_c_i32, [_c_p, _c_p]),
+    "rqlp_graph_kernels": (_c_i32, [_c_p]),
+    "rqlp_graph_destroy": (None, [_c_p]),
     "rqlp_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i32, _c_i32, ctypes.POINTER(Opts)]),
     "rqlp_backward": (_c_i32, [_c_p, _c_i32, _c_i64, _c_i64, _c_i64, _c_i32, _c_i32, _c_p, _c_i64,
                                ctypes.POINTER(Opts), _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i64,
@@ -614,6 +620,73 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().rqlp_batched_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """One factorization recorded into a CUDA graph and replayed
+    (rqlp_graph_create / launch / destroy).
+
+    Arguments as for rqlp() (no fixed pivots, no R-values).  The constructor
+    factors A once on `stream` and records the call; launch() replays it on
+    any stream with one graph launch.  The graph reads A and Omega and writes
+    self.out and self.ws at their current addresses: copy new data into A
+    (in place) and launch again.  status() reads the device status word.
+    """
+
+    def __init__(self, A, k: int, p: int, Omega, q: int = 0, d: int = 1, pivot2: bool = True,
+                 prec: str = "fp64", block_b: int = 0, stream=None, in_flight: int = 0,
+                 truncate_k: bool = False):
+        torch = _torch()
+        m, n = A.shape
+        l = k + p
+        lda = _row_major(A, "A")
+        ldo = _row_major(Omega, "Omega")
+        if Omega.dtype != torch.float64 or tuple(Omega.shape) != (n, l):
+            raise ValueError("Omega must be float64 of shape (n, k + p)")
+        self.opts = opts(q, d, pivot2, prec, block_b, truncate_k=truncate_k, in_flight=in_flight)
+        L_ = lib()
+        need = L_.rqlp_workspace_size(m, n, k, p, ctypes.byref(self.opts))
+        if need == 0:
+            raise RqlpError(-1, "rqlp_workspace_size")
+        dev = A.device
+        self.ws = workspace(need, dev)
+        w = k if truncate_k else l
+        self.out = dict(Q=torch.empty((m, w), dtype=torch.float64, device=dev),
+                        L=torch.empty((w, w), dtype=torch.float64, device=dev),
+                        P=torch.empty((n, w), dtype=torch.float64, device=dev),
+                        Lvalues=torch.empty((w,), dtype=torch.float64, device=dev),
+                        piv0=torch.empty((n,), dtype=torch.int32, device=dev),
+                        piv1=torch.empty((l,), dtype=torch.int32, device=dev))
+        self._keep = (A, Omega)
+        o = self.out
+        handle = _c_p()
+        _check(L_.rqlp_graph_create(_ptr(A), _dtype_code(A), m, n, lda, k, p, _ptr(Omega), ldo,
+                                    ctypes.byref(self.opts), _ptr(o["Q"]), _ptr(o["L"]),
+                                    _ptr(o["P"]), _ptr(o["Lvalues"]), _ptr(o["piv0"]),
+                                    _ptr(o["piv1"]), _ptr(self.ws), self.ws.numel(),
+                                    _stream(stream), ctypes.byref(handle)), "rqlp_graph_create")
+        self.handle = handle
+
+    @property
+    def kernels(self) -> int:
+        return int(lib().rqlp_graph_kernels(self.handle))
+
+    def launch(self, stream=None):
+        _check(lib().rqlp_graph_launch(self.handle, _stream(stream)), "rqlp_graph_launch")
+
+    def status(self, stream=None) -> int:
+        return read_status(self.ws, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rqlp_graph_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
