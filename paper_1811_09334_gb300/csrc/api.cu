@@ -365,11 +365,15 @@ struct SideStream {
   cudaEvent_t fork = nullptr, join = nullptr;
 };
 // One side stream per caller stream (and host thread), so that problems in
-// flight on different streams do not queue behind each other's Q0.
+// flight on different streams do not queue behind each other's Q0.  A
+// stream being recorded gets none (the batched graph records many problems
+// on many branches), unless the recording of one factorization asked for it
+// (t_side_in_capture) after creating it outside the capture.
+thread_local bool t_side_in_capture = false;
 SideStream *side_for(cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-    return nullptr;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return nullptr;
+  if (cs != cudaStreamCaptureStatusNone && !t_side_in_capture) return nullptr;
   struct Entry {
     cudaStream_t main;
     SideStream sd;
@@ -379,6 +383,7 @@ SideStream *side_for(cudaStream_t st) {
   for (Entry &e : table)
     if (e.main == st) return &e.sd;
   if (table.size() >= 64) return nullptr;  // many streams: Q0 stays on the caller's stream
+  if (cs != cudaStreamCaptureStatusNone) return nullptr;  // nothing is created while recording
   Entry e;
   e.main = st;
   if (cudaStreamCreateWithFlags(&e.sd.s, cudaStreamNonBlocking) != cudaSuccess ||
@@ -666,6 +671,11 @@ int run_rqlp(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda, 
 }
 
 }  // namespace
+
+namespace rqk {
+void side_stream_prepare(cudaStream_t st) { side_for(st); }
+void side_stream_in_capture(bool on) { t_side_in_capture = on; }
+}  // namespace rqk
 
 extern "C" {
 

@@ -324,8 +324,8 @@ void rqlp_batched_destroy(rqlp_batch_t plan) {
 // launch and no host work per kernel.  The recording is made on a private
 // stream after one ordinary call on the caller's stream (which checks the
 // arguments and does every one-time set-up, none of which may happen inside a
-// capture); while recording, rqlp() keeps the Q0 work on the recorded stream
-// (no side stream), so the graph is one chain of kernels.
+// capture); the private stream's side stream is created before the capture,
+// so that the explicit Q0 becomes a branch beside the QR of R0^T.
 int rqlp_graph_create(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t lda,
                       int32_t k, int32_t p, const double *Omega, int64_t ldo,
                       const rqlp_opts *opts, double *Q, double *L, double *P, double *Lvalues,
@@ -341,12 +341,15 @@ int rqlp_graph_create(const void *A, int32_t a_dtype, int64_t m, int64_t n, int6
   cudaStream_t rec = nullptr;
   if (cudaStreamCreateWithFlags(&rec, cudaStreamNonBlocking) != cudaSuccess) return RQLP_ERR_CUDA;
   rqlp_graph *g = new rqlp_graph;
+  side_stream_prepare(rec);
   const long long n0 = launch_count();
   if (cudaStreamBeginCapture(rec, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     rc = RQLP_ERR_CUDA;
   } else {
+    side_stream_in_capture(true);
     rc = rqlp(A, a_dtype, m, n, lda, k, p, Omega, ldo, opts, Q, L, P, Lvalues, piv0, piv1, ws,
               ws_bytes, reinterpret_cast<rqlp_stream_t>(rec));
+    side_stream_in_capture(false);
     const cudaError_t ec = cudaStreamEndCapture(rec, &g->graph);
     if (rc == RQLP_OK && ec != cudaSuccess) rc = RQLP_ERR_CUDA;
   }

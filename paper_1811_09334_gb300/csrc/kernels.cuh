@@ -60,6 +60,13 @@ struct Arena {
   }
 };
 
+// ---- api.cu: the side stream that runs Q0 beside the QR of R0^T ----------
+// For recording one factorization into a graph: create the side stream of
+// `st` now (outside a capture), and let rqlp() fork to it while `st` is
+// being recorded (the fork and the join become branches of the graph).
+void side_stream_prepare(cudaStream_t st);
+void side_stream_in_capture(bool on);
+
 // ---- gemm_f64.cu ---------------------------------------------------------
 int64_t gemm_f64_splits(int64_t M, int64_t N, int64_t K);
 size_t gemm_f64_part_bytes(int64_t M, int64_t N, int64_t K);
