@@ -953,13 +953,16 @@ def run_ours(args):
 
         # the host-to-device link bounds this path: a few problems in flight
         # keep it busy; the best of 2, 3, 4 is timed (after an untimed pass
-        # that loads the kernels the in-flight shapes use)
-        e2e_run(2, 4)
+        # that loads the kernels the in-flight shapes use).  Host-side
+        # hiccups show in regions this short, so each count takes the better
+        # of two runs of at least 12 factorizations
+        e2e_run(4, 8)
         e2e_sweep = {}
         for P in (2, 3, 4):
-            e2e_sweep[P] = 3 * P / e2e_run(P, 3 * P)
+            hs = max(12, 4 * P)
+            e2e_sweep[P] = max(hs / e2e_run(P, hs) for _ in range(2))
         pe = max(e2e_sweep, key=e2e_sweep.get)
-        hsteps = max(4, min(args.steps, 10), 2 * pe)
+        hsteps = max(16, 4 * pe, min(args.steps, 10))
         dt = e2e_run(pe, hsteps)
         l = pr.l
         h2d = A_h.numel() * A_h.element_size() + Om_h.numel() * 8
