@@ -683,6 +683,18 @@ def _oracle_one_core(A_np, Om_np, budget_s=120.0):
         os.unlink(opath)
 
 
+def _pick_in_flight(sweep, counts):
+    """(P, way) from the sweep {way: {P: factorizations/s}}: the count and
+    the way with the highest rate (ties to the fewer problems in flight, then
+    to direct calls)."""
+    best, bmode = counts[0], "direct"
+    for P in sorted(counts):
+        for mode in ("direct", "graph"):
+            if sweep[mode][P] > sweep[bmode][best]:
+                best, bmode = P, mode
+    return best, bmode
+
+
 def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1, 2, 3, 4, 6, 8)):
     """Throughput with P independent factorizations in flight: P streams, each
     with its own workspace and outputs, taking the factorizations round robin
@@ -693,7 +705,7 @@ def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1
     Two ways to issue a factorization are measured: a direct rqlp() call
     (~110 kernel launches) and the replay of its recording (rqlp_graph_*, one
     graph launch).  A short sweep over P = 1, 2, 3, 4, 6, 8 and both ways picks
-    the fastest (a larger P only where it gains at least 3 %); K steps of P
+    the fastest count and way; K steps of P
     factorizations (one per stream: a step is the batch of P problems in
     flight) are then timed with it, with the clocks sampled."""
     import torch.distributed as dist
@@ -745,12 +757,7 @@ def _in_flight(R, torch, A, pr, Om, form, steps, warmup, world, local, counts=(1
     # one factorization at a time from its recording, K replays
     run(1, 2, "graph")
     lat_graph = timed(1, steps, "graph") / steps
-    best, bmode = counts[0], "direct"
-    for mode in ("direct", "graph"):
-        for P in counts:
-            if sweep[mode][P] > 1.03 * sweep[bmode][best] or (
-                    P == best and sweep[mode][P] > sweep[bmode][best]):
-                best, bmode = P, mode
+    best, bmode = _pick_in_flight(sweep, counts)
     run(best, max(warmup, 1) * best, bmode)
     torch.cuda.synchronize()
     if world > 1:

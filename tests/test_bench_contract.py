@@ -70,3 +70,20 @@ def test_stage_roofline_arithmetic():
     sr64 = bench._stage_roofline("fp64", m, n, l, q, d, prof, 1, peaks)
     assert sr64["products_with_A"]["bound"] == "alu"
     assert "tensor_frac" not in sr64["products_with_A"]
+
+
+def test_in_flight_choice():
+    sys.path.insert(0, ROOT)
+    import bench
+    counts = (1, 2, 4, 8)
+    sweep = {"direct": {1: 350.0, 2: 500.0, 4: 700.0, 8: 715.0},
+             "graph": {1: 380.0, 2: 510.0, 4: 690.0, 8: 700.0}}
+    assert bench._pick_in_flight(sweep, counts) == (8, "direct")
+    # the faster way at the fastest count, whichever way comes first
+    sweep["graph"][8] = 716.0
+    assert bench._pick_in_flight(sweep, counts) == (8, "graph")
+    # ties go to fewer problems in flight, then to direct calls
+    sweep["direct"][4] = 716.0
+    assert bench._pick_in_flight(sweep, counts) == (4, "direct")
+    sweep["graph"][4] = 716.0
+    assert bench._pick_in_flight(sweep, counts) == (4, "direct")
