@@ -106,7 +106,8 @@ typedef struct {
                            L): Q m x k, L k x k, P n x k and k L-values, each with ld k
                            (Q[:, :k], L[:k, :k], P[:, :k] of the l-wide factorization) */
   int32_t in_flight;    /* how many factorizations the caller keeps running at once, each on its
-                           own stream with its own workspace (0 or 1: one at a time).  With 2 or
+                           own stream with its own workspace (0 or 1: one at a time; read by
+                           rqlp(), rqlp_host*(), rqlp_brqlp_tol() and rqlp_graph_create()).  With 2 or
                            more, the column-pivoted QR of B, whose CTAs spend most of each
                            pivot step waiting on the grid-wide exchange, runs on half of the
                            SMs and leaves the others to the kernels of the other

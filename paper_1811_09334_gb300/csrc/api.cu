@@ -737,6 +737,7 @@ int rqlp_brqlp_tol(const void *A, int32_t a_dtype, int64_t m, int64_t n, int64_t
   *l_used = 0;
   rqlp_opts o = *opts;
   o.block_b = b;
+  const InFlightShapes shapes(o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Plan W = carve(ws, m, n, l_max, o);
   if (W.bytes > ws_bytes) return RQLP_ERR_WORKSPACE;
